@@ -1,0 +1,122 @@
+"""Pins of the balancer oracle: the paper's own migration counts
+(Sec. VI-A Experiment A, Sec. VI-B Experiment C / Table V, Sec. VII) and
+scheduling-theory facts checked by brute force."""
+import itertools
+import random
+
+import pytest
+
+from oracle import balance as B
+
+
+def test_experiment_a_greedy_two_migrations():
+    """4 VPs on 2 processors, the heavy pair on processor 0: GreedyLB
+    migrates two threads, one each way (Sec. VI-A)."""
+    costs = [2.0, 2.0, 1.0, 1.0]
+    old = B.static_blocks(4, 2)
+    assert old == [0, 0, 1, 1]
+    new = B.greedy(costs, 2)
+    assert B.migrations(old, new) == 2
+    moved = [v for v in range(4) if old[v] != new[v]]
+    assert sorted(old[v] for v in moved) == [0, 1]       # one from each side
+    assert B.bin_loads(costs, new, 2) == [3.0, 3.0]
+
+
+def exp_c_first():
+    costs = [2.0] * 8 + [1.0] * 8          # VPs 0-7 heavy, 8-15 light
+    old = B.static_blocks(16, 4)           # 0000 1111 2222 3333
+    return costs, old
+
+
+def test_experiment_c_greedy_twelve_migrations():
+    """16 VPs on 4 processors: GreedyLB balances to 2 heavy + 2 light per
+    processor with 12 migrations although 8 would do (Table V, Sec. VII)."""
+    costs, old = exp_c_first()
+    assert old == [0] * 4 + [1] * 4 + [2] * 4 + [3] * 4
+    new = B.greedy(costs, 4)
+    assert B.migrations(old, new) == 12
+    for b in range(4):
+        vs = [v for v in range(16) if new[v] == b]
+        assert sum(costs[v] == 2.0 for v in vs) == 2 and len(vs) == 4
+    assert max(B.bin_loads(costs, new, 4)) == 6.0
+    # 8 moves suffice: minimum over all balanced placements, by counting
+    assert min_migrations_to_balance(costs, old, 4) == 8
+
+
+def min_migrations_to_balance(costs, old, nbins):
+    """Each bin needs 2 heavy + 2 light; a bin keeps at most 2 of its own
+    heavy and 2 of its own light VPs, so moves = 16 - kept."""
+    kept = 0
+    for b in range(nbins):
+        mine = [v for v in range(len(costs)) if old[v] == b]
+        kept += min(2, sum(costs[v] == 2.0 for v in mine))
+        kept += min(2, sum(costs[v] == 1.0 for v in mine))
+    return len(costs) - kept
+
+
+def test_experiment_c_refine_swap_after_redistribution():
+    """After the load moves, processors 0 and 2 hold 3 heavy + 1 light and 1
+    and 3 hold 1 heavy + 3 light (Sec. VI-B); RefineSwapLB restores balance
+    with at most the paper's 4 migrations."""
+    costs, old = exp_c_first()
+    a = B.greedy(costs, 4)
+    c2 = list(costs)
+    for b, make_heavy in ((0, True), (1, False), (2, True), (3, False)):
+        vs = [v for v in range(16) if a[v] == b]
+        if make_heavy:
+            light = [v for v in vs if c2[v] == 1.0]
+            c2[light[0]] = 2.0
+        else:
+            heavy = [v for v in vs if c2[v] == 2.0]
+            c2[heavy[0]] = 1.0
+    assert B.bin_loads(c2, a, 4) == [7.0, 5.0, 7.0, 5.0]
+    r = B.refine_swap(c2, a, 4)
+    assert B.max_over_mean(c2, r, 4) == 1.0
+    assert B.migrations(a, r) <= 4
+    assert B.migrations(a, r) == 2
+    # greedy from scratch would also balance but moves far more
+    assert B.migrations(a, B.greedy(c2, 4)) > 4
+
+
+def brute_force_makespan(costs, nbins):
+    best = float("inf")
+    for assign in itertools.product(range(nbins), repeat=len(costs)):
+        if assign[0] != 0:
+            continue
+        best = min(best, max(B.bin_loads(costs, assign, nbins)))
+    return best
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_greedy_lpt_bound_against_optimum(seed):
+    """Graham: LPT makespan <= (4/3 - 1/(3m)) OPT."""
+    rng = random.Random(seed)
+    m = rng.choice([2, 3])
+    n = rng.randint(m, 9 if m == 3 else 10)
+    costs = [float(rng.randint(1, 40)) for _ in range(n)]
+    a = B.greedy(costs, m)
+    opt = brute_force_makespan(costs, m)
+    assert max(B.bin_loads(costs, a, m)) <= (4 / 3 - 1 / (3 * m)) * opt + 1e-12
+
+
+@pytest.mark.parametrize("seed", range(30))
+def test_refine_never_increases_max_and_keeps_every_vp(seed):
+    rng = random.Random(100 + seed)
+    nb = rng.randint(2, 9)
+    nv = rng.randint(nb, 80)
+    costs = [rng.lognormvariate(0, 1) for _ in range(nv)]
+    a0 = [rng.randrange(nb) for _ in range(nv)]
+    r = B.refine_swap(costs, a0, nb)
+    assert len(r) == nv and all(0 <= b < nb for b in r)
+    assert max(B.bin_loads(costs, r, nb)) <= max(B.bin_loads(costs, a0, nb))
+
+
+def test_refine_is_idle_when_balanced():
+    costs = [1.0] * 12
+    a = B.static_blocks(12, 4)
+    assert B.refine_swap(costs, a, 4) == a
+
+
+def test_greedy_ties_break_by_id():
+    """Equal costs: VP v lands on bin v mod m (lowest-id tie rules)."""
+    assert B.greedy([1.0] * 7, 3) == [0, 1, 2, 0, 1, 2, 0]
