@@ -1,0 +1,415 @@
+"""Benchmark: cell-sweep updates/s of the persistent load-balanced step on one
+GB300 (or N independent replicas), with roofline, clocks, end-to-end and
+CPU-oracle baselines.
+
+One benchmark step = one rebalance period: `period` time steps of every VP
+(advection, k_c Thomas sweeps, store, global sum, per-VP cost stamps, grid
+barrier) in one persistent launch, then the load measurement and the
+rebalance (GreedyLB first, RefineSwapLB after).  The k_c array is re-drawn
+every 50 time steps as the workload prescribes.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload NAME] [--period P] [--strategy auto|static|queue|...]
+
+Prints one JSON line (rank 0).  The default workload's fields (403 MB each)
+exceed the 129 MB L2, so no flush is needed between timed steps.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+DEFAULT_WORKLOAD = "lognormal_fp32_1024x1024x96"
+SIZEOF = {"f64": 8, "f32": 4, "bf16": 2}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    ap.add_argument("--period", type=int, default=10)
+    ap.add_argument("--strategy", default="auto")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")),
+            int(os.environ.get("WORLD_SIZE", "1")))
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def kc_epochs(w, nsteps_total):
+    """Device-independent k_c arrays for every re-draw epoch the run touches."""
+    if not w.kc_epoch_steps:
+        return {}
+    n = (nsteps_total + w.kc_epoch_steps - 1) // w.kc_epoch_steps
+    return {e: [w.kc_array(gi, e) for gi in range(len(w.grids))] for e in range(n)}
+
+
+def sweeps_per_step(w, t, epochs):
+    """Cell-sweep updates of time step t: sum over columns of nz * k_c."""
+    import oracle  # counts only: the k_c rule evaluated for the metric's numerator
+    tot = 0
+    for gi, g in enumerate(w.grids):
+        if g.kc_disk:
+            kc = oracle.kc_field(oracle.OracleGrid.from_spec(g), t)
+        else:
+            kc = epochs[t // w.kc_epoch_steps][gi]
+        tot += int(kc.sum(dtype=np.int64)) * g.nz
+    return tot
+
+
+def roofline_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def load_traffic(kernel_tag):
+    """Per-launch DRAM bytes of the timed kernel from a committed ncu summary,
+    valid only while the kernel sources are unchanged (hash recorded)."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        from paper_1310_4218_gb300.build import source_hash
+        e = d.get(kernel_tag)
+        if e and e.get("source_hash") == source_hash():
+            return e
+    except Exception:
+        pass
+    return None
+
+
+def cpu_oracle_rate(w, budget_s=12.0):
+    """The FP64 oracle as it stands (single thread) on a bounded sample of the
+    workload: a periodic sub-grid of whole columns (side <= 96) with the
+    workload's k_c values over that patch, stepped until the budget is used.
+    Returns (cell-sweep updates/s, description, steps, seconds)."""
+    import oracle
+    g = w.grids[0]
+    side = min(g.nx, g.ny, 96)
+    epochs = kc_epochs(w, 1)
+    if g.kc_disk:
+        kc = oracle.kc_field(oracle.OracleGrid.from_spec(g), 0)
+    else:
+        kc = epochs[0][0]
+    # the patch with the largest total k_c among a few candidates, so the
+    # sample carries the workload's mean load or more
+    best, patch = -1, None
+    for y0 in range(0, g.ny - side + 1, max(side, (g.ny - side) // 4 or 1)):
+        for x0 in range(0, g.nx - side + 1, max(side, (g.nx - side) // 4 or 1)):
+            s_ = int(kc[y0:y0 + side, x0:x0 + side].sum())
+            if s_ > best:
+                best, patch = s_, (x0, y0)
+    x0, y0 = patch
+    kcp = np.ascontiguousarray(kc[y0:y0 + side, x0:x0 + side], dtype=np.int32)
+    og = oracle.OracleGrid(side, side, g.nz, g.cx, g.cy, g.cz, g.r, False, (0, 0, 0, 0, 0),
+                           1, 1, kcp)
+    q = np.ascontiguousarray(g.initial_field()[:, y0:y0 + side, x0:x0 + side])
+    per_step = int(kcp.sum(dtype=np.int64)) * g.nz
+    t0 = time.perf_counter()
+    steps = 0
+    while time.perf_counter() - t0 < budget_s:
+        q, _ = oracle.run(og, q, 1, t0=steps)
+        steps += 1
+    dt = time.perf_counter() - t0
+    desc = ("%d steps of a periodic %dx%dx%d patch (k_c from %s at (%d,%d)), one thread"
+            % (steps, side, side, g.nz, w.name, x0, y0))
+    return per_step * steps / dt, desc, steps, dt
+
+
+def run_reference(args, rank, world):
+    """The reference arm: the CPU oracle, timed on the host cores."""
+    from workloads import get_config
+    w = get_config(args.workload)
+    if rank != 0:
+        return
+    for _ in range(max(args.warmup, 0)):
+        cpu_oracle_rate(w, budget_s=1.0)
+    vals, times = [], []
+    for _ in range(args.steps):
+        v, desc, steps, dt = cpu_oracle_rate(w, budget_s=max(2.0, 30.0 / max(args.steps, 1)))
+        vals.append(v)
+        times.append(dt)
+    value = float(np.median(vals))
+    out = {"metric": "cell-sweep updates/s", "value": value, "unit": "cell-sweep updates/s",
+           "impl": "reference", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": 1000.0 * float(np.median(times)), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": w.name, "sample": desc},
+           "cpu_baseline": {"value": value, "unit": "cell-sweep updates/s", "cores": 1,
+                            "kind": "oracle", "sample": desc},
+           "e2e": {"value": value, "unit": "cell-sweep updates/s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    rank, local_rank, world = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    import torch.distributed as dist
+
+    from paper_1310_4218_gb300 import lb
+    from paper_1310_4218_gb300.sim import Simulation
+    from workloads import get_config
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    w = get_config(args.workload)
+    P = args.period
+    total_steps = (args.warmup + args.steps) * P
+    epochs = kc_epochs(w, total_steps)
+    fields = [g.initial_field() for g in w.grids]
+    kc0 = [epochs[0][gi] for gi in range(len(w.grids))] if epochs else None
+    stream = torch.cuda.Stream(dev)
+    opt = lb.lb_default_options()
+    sim = Simulation(w.grids, fields, w.vps, kc_arrays=kc0, options=opt, device=dev, stream=stream)
+    info = sim.info()
+    kc_dev = {}
+    if epochs:
+        for e, arrs in epochs.items():
+            kc_dev[e] = [torch.as_tensor(a).to(dev) for a in arrs]
+
+    def launches(t0, t1):
+        """Time steps t0..t1-1 as persistent launches, split where the k_c
+        array is re-drawn."""
+        t = t0
+        while t < t1:
+            n = t1 - t
+            if epochs:
+                e = t // w.kc_epoch_steps
+                if t % w.kc_epoch_steps == 0 or t == t0:
+                    for gi in range(len(w.grids)):
+                        lb.lb_set_kc(sim.ctx, gi, kc_dev[e][gi].data_ptr())
+                n = min(n, (e + 1) * w.kc_epoch_steps - t)
+            sim.step(n)
+            t += n
+        return t
+
+    stats = {}
+
+    def balance(tag):
+        """Load measurement (Sec. V) and the balancer call (Sec. VI)."""
+        cost, busy = sim.measure()
+        used = busy[busy > 0]
+        st = {"sm_max_over_mean": float(used.max() / used.mean()) if used.size else None}
+        tot = float(cost.sum())
+        mean = tot / info.nprocs
+        st["granularity_floor"] = float(max(cost.max(), mean) / mean) if mean > 0 else None
+        if args.strategy != "static":
+            mig, pred = sim.rebalance(args.strategy)
+            st["migrations"] = mig
+            st["predicted_max_over_mean"] = pred
+        stats[tag] = st
+
+    # warm-up; the first period runs under the static placement
+    t = 0
+    for wi in range(args.warmup):
+        t = launches(t, t + P)
+        balance("static" if wi == 0 else "warmup")
+    torch.cuda.synchronize(dev)
+    sweeps = sum(sweeps_per_step(w, s, epochs) for s in range(t, t + args.steps * P))
+    cells = w.cells * args.steps * P
+
+    # timed region: device-resident inputs
+    kev = []
+    sampler = ClockSampler(local_rank)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    sampler.start()
+    time.sleep(0.3)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        n_launch = 0
+        tt = t
+        while tt < t + P:      # count launches of this period
+            n = t + P - tt
+            if epochs:
+                e = tt // w.kc_epoch_steps
+                n = min(n, (e + 1) * w.kc_epoch_steps - tt)
+            tt += n
+            n_launch += 1
+        launches(t, t + P)
+        b.record(stream)
+        kev.append((a, b, n_launch))
+        balance("timed")
+        t = t + P
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    kernel_ms = [a.elapsed_time(b) / n for a, b, n in kev]
+    n_launches = sum(n for _, _, n in kev)
+    if world > 1:
+        tm = torch.tensor([ms], device=dev)
+        dist.all_reduce(tm, op=dist.ReduceOp.MAX)
+        ms = float(tm.item())
+    s = ms / 1000.0
+    value = sweeps * world / s
+
+    g0 = w.grids[0]
+    steps_per_launch = args.steps * P / n_launches
+    bytes_per_step = 2 * w.cells * SIZEOF[g0.storage] + \
+        4 * sum(g.nx * g.ny for g in w.grids if not g.kc_disk)
+    bytes_per_launch = bytes_per_step * steps_per_launch
+    kern_s = statistics.median(kernel_ms) / 1000.0
+    peak, peak_src = roofline_peak()
+    achieved = bytes_per_launch / kern_s / 1e9
+    tag = "lb_step_kernel:%s" % w.name
+    tr = load_traffic(tag)
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        h_in = [torch.from_numpy(np.ascontiguousarray(f, dtype=np.float32)).pin_memory()
+                if g.storage == "f32" else None for g, f in zip(w.grids, fields)]
+        if all(x is not None for x in h_in):
+            h_out = [torch.empty_like(x).pin_memory() for x in h_in]
+            torch.cuda.synchronize(dev)
+            c0 = torch.cuda.Event(enable_timing=True)
+            c1 = torch.cuda.Event(enable_timing=True)
+            c0.record(stream)
+            t_e = t
+            for _ in range(args.steps):
+                with torch.cuda.stream(stream):
+                    for gi in range(len(w.grids)):
+                        sim.field_tensor(gi).copy_(h_in[gi].view(-1), non_blocking=True)
+                launches(t_e, t_e + P)
+                balance("e2e")
+                with torch.cuda.stream(stream):
+                    for gi in range(len(w.grids)):
+                        h_out[gi].view(-1).copy_(sim.field_tensor(gi), non_blocking=True)
+                t_e += P
+            c1.record(stream)
+            torch.cuda.synchronize(dev)
+            es = c0.elapsed_time(c1) / 1000.0
+            sw = sum(sweeps_per_step(w, s2, epochs) for s2 in range(t, t + args.steps * P))
+            nbytes = sum(x.numel() * x.element_size() for x in h_in)
+            e2e = {"value": sw * world / es, "unit": "cell-sweep updates/s",
+                   "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        v, desc, _, _ = cpu_oracle_rate(w)
+        cpu = {"value": v, "unit": "cell-sweep updates/s", "cores": 1, "kind": "oracle",
+               "sample": desc}
+
+    if rank == 0:
+        out = {
+            "metric": "cell-sweep updates/s", "value": value, "unit": "cell-sweep updates/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if g0.compute == "f32" else "f64",
+            "data": "synthetic",
+            "config": {"workload": w.name, "global_batch": len(w.grids), "period_steps": P,
+                       "time_steps_per_step": P, "vps": len(w.vps), "cells": w.cells,
+                       "strategy": args.strategy, "parallelism": "replicas" if world > 1 else "1gpu",
+                       "l2": "fields larger than L2 (no flush)",
+                       "cell_steps_per_s": cells * world / s,
+                       "processors": info.nprocs, "threads_per_cta": info.threads_per_cta},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_source": peak_src,
+                         "traffic": (tr["dram_bytes_per_step"] * steps_per_launch) if tr else None,
+                         "kernel": "lb_step_kernel",
+                         "kernel_ms_per_launch": kern_s * 1000.0,
+                         "steps_per_launch": steps_per_launch,
+                         "algorithmic_bytes_per_launch": bytes_per_launch},
+            "imbalance": stats,
+            "clocks": clocks,
+            "gpu_launches": n_launches,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(out), flush=True)
+    sim.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

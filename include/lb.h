@@ -1,0 +1,259 @@
+/*
+ * lb.h -- C ABI of the GB300 column-physics load-balancing library (liblb.so).
+ *
+ * The library runs the hot path of "Dynamic Load Balancing in GPU-Based
+ * Systems - Early Experiments" (Fazenda, Mendes, Kale, Panetta, Rodrigues)
+ * on one GPU.  The paper over-decomposes a grid into virtual processors
+ * (VPs, Sec. III), measures each VP's load on the device (Sec. V) and
+ * migrates VPs between processors with GreedyLB and RefineSwapLB (Sec. VI).
+ * Here a VP is a rectangle of grid columns, a "processor" is a CTA of one
+ * persistent kernel (one CTA per SM by default), and a migration rewrites a
+ * device-resident assignment table: field data never moves.
+ *
+ * One time step of a grid (the application loop of Fig. 2):
+ *   1. dynamics: first-order upwind advection, convex donor-cell form
+ *        q* = (1-|cx|-|cy|-|cz|) q + |cx| q[i-sx] + |cy| q[j-sy] + |cz| q[k-sz]
+ *      (s = sign of the velocity), periodic in x and y, zero flux through
+ *      the bottom and top faces;
+ *   2. physics: per column, k_c(i,j,t) passes of the implicit vertical
+ *      diffusion solve M x = d, M = tridiag(-r, 1+2r, -r) with zero-flux
+ *      ends (first and last diagonal 1+r) -- the serial-in-k recurrence of
+ *      Fig. 1 whose trip count the load array C(i,j) multiplies (Fig. 4,
+ *      Sec. VI-B);
+ *   3. the load array moves through the domain (Sec. VI-B): either a disk
+ *      of radius R centred at (x0,y0) + t (vx,vy) (periodic, minimum-image
+ *      distance, integer cells) with k_in inside and k_out outside, or a
+ *      caller-supplied array;
+ *   4. optional diagnostic: compensated FP64 global sum of the new field.
+ *
+ * Layout of every field: x fastest, element (i,j,k) at (k*ny + j)*nx + i.
+ *
+ * Conventions for every entry point:
+ *   - Returns an lb_status and never aborts or exits the process.
+ *   - Device-side failures (grid-barrier timeout, non-finite sum) are
+ *     recorded in a device status word and reported by the next call that
+ *     synchronises (lb_measure_loads, lb_mass, lb_mass_history,
+ *     lb_checkpoint, lb_sync).
+ *   - lb_last_error(ctx) returns a text for the last failure of that ctx.
+ *   - A ctx is not thread-safe; one host thread drives it at a time.
+ *   - Work is issued on the stream given to lb_create (a cudaStream_t
+ *     passed as void*; NULL = legacy default stream).
+ */
+#ifndef LB_H
+#define LB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lb_ctx lb_ctx;
+
+typedef enum {
+    LB_OK = 0,
+    LB_EINVAL = 1,       /* invalid argument; nothing changed */
+    LB_ECUDA = 2,        /* a CUDA runtime call failed */
+    LB_ETIMEOUT = 3,     /* a grid-barrier wait ran past barrier_timeout_ns */
+    LB_ENUMERIC = 4,     /* the global sum of a field became NaN or Inf */
+    LB_ESTATE = 5,       /* call not valid in the ctx's current state */
+    LB_ENORESIDENT = 6,  /* the requested CTAs cannot all be co-resident */
+    LB_EIO = 7           /* checkpoint file could not be written or read */
+} lb_status;
+
+typedef enum { LB_F64 = 0, LB_F32 = 1, LB_BF16 = 2 } lb_dtype;
+
+/*
+ * Assignment strategies (Sec. VI):
+ *   LB_STATIC       contiguous runs of VPs per processor (Table V, first row)
+ *   LB_GREEDY       GreedyLB: VPs by measured cost descending (ties: lower
+ *                   VP id) each to the least-loaded processor (ties: lower id)
+ *   LB_REFINE_SWAP  RefineSwapLB: move/swap VPs off the most loaded
+ *                   processor until max load <= (1+refine_tol) * mean
+ *   LB_ATOMIC_QUEUE no table: warps pop work items from one global counter
+ *                   every step (the dynamic task-queue scheme of Sec. II)
+ *   LB_AUTO         GreedyLB on the first rebalance of a ctx, RefineSwapLB
+ *                   afterwards -- the schedule the paper recommends (Sec. VII)
+ */
+typedef enum {
+    LB_STATIC = 0,
+    LB_GREEDY = 1,
+    LB_REFINE_SWAP = 2,
+    LB_ATOMIC_QUEUE = 3,
+    LB_AUTO = 4
+} lb_strategy;
+
+/*
+ * One grid.  q0/q1 are caller-owned device buffers of nx*ny*nz elements of
+ * the storage type, borrowed for the ctx's lifetime; q0 holds the initial
+ * field.  Steps ping-pong between them; lb_current_field says which holds
+ * the latest field.  |cx|+|cy|+|cz| <= 1, r >= 0, 1 <= nz <= 128,
+ * nx, ny >= 2.  compute must be LB_F32, or LB_F64 with LB_F64 storage.
+ */
+typedef struct {
+    int32_t nx, ny, nz;
+    double cx, cy, cz;        /* Courant numbers (cells per step) */
+    double r;                 /* diffusion number kappa*dt/dz^2 */
+    int32_t storage;          /* lb_dtype of q0/q1 */
+    int32_t compute;          /* lb_dtype of the arithmetic: LB_F32 or LB_F64 */
+    void *q0;
+    void *q1;
+    const int32_t *kc;        /* device int32 [ny*nx] (row j, column i); read
+                                 every step when kc_disk == 0, caller-owned */
+    int32_t kc_disk;          /* 1: moving-disk rule below; 0: kc array */
+    int32_t disk_x0, disk_y0, disk_vx, disk_vy, disk_r;
+    int32_t k_in, k_out;      /* k_c inside / outside the disk, >= 0 */
+} lb_grid_desc;
+
+/* One VP: columns x0 <= i < x0+w, y0 <= j < y0+h of grid `grid`.  The VPs
+   of a ctx must tile every grid exactly (no gap, no overlap). */
+typedef struct {
+    int32_t grid, x0, y0, w, h;
+} lb_vp;
+
+typedef struct {
+    int32_t ctas_per_sm;          /* processors per SM (default 1) */
+    int32_t queue_order;          /* ATOMIC_QUEUE order: 0 VP id order,
+                                     1 last measured cost, heaviest first */
+    int32_t mass_every;           /* global sum every n-th step; 0 = never
+                                     (default 1) */
+    int32_t device_balancer;      /* reserved, must be 0 */
+    double ema_alpha;             /* weight of the newest measurement in the
+                                     per-VP cost average (default 0.5) */
+    double refine_tol;            /* RefineSwapLB tolerance (default 0.05) */
+    int64_t barrier_timeout_ns;   /* grid-barrier wait limit (default 2 s) */
+    int32_t reserved[8];          /* must be 0 */
+} lb_options;
+
+/* Fill *opt with the defaults listed above. */
+void lb_default_options(lb_options *opt);
+
+/*
+ * Create a ctx: validates the grids and the VP layout (Sec. III
+ * over-decomposition), builds the VP and work tables, places VPs with
+ * LB_STATIC, and checks that all processors can be co-resident
+ * (LB_ENORESIDENT otherwise).  grids[ngrids], vps[nvps] are host arrays,
+ * copied.  opt may be NULL (defaults).  On success *out owns device tables
+ * of O(nvps + columns/32) entries; the field buffers stay caller-owned.
+ */
+lb_status lb_create(const lb_grid_desc *grids, int32_t ngrids, const lb_vp *vps,
+                    int32_t nvps, const lb_options *opt, void *cuda_stream,
+                    lb_ctx **out);
+
+/*
+ * Enqueue nsteps time steps (Fig. 2's inner loop) as one persistent
+ * cooperative launch on the ctx stream; returns without waiting.  Every VP
+ * is processed once per step under the current assignment or the atomic
+ * queue; per-VP device cost (clock64 cycles per work item, Sec. V) and
+ * per-processor busy time are accumulated for lb_measure_loads.  nsteps=0
+ * is a no-op.
+ */
+lb_status lb_step(lb_ctx *ctx, int32_t nsteps);
+
+/*
+ * Synchronise the stream, read the loads accumulated since the previous
+ * call (Sec. V), fold them into the per-VP cost average (FP64 EMA) and reset
+ * the accumulators.  Outputs (host, may be NULL):
+ *   vp_cost_ns[nvps]  mean measured cost per step of each VP, ns
+ *   sm_busy_ns[*nsm]  mean busy time per step of each SM, ns (SMs that ran
+ *                     no processor report 0); *nsm = number of SMs
+ * Returns LB_ESTATE if no step ran since the previous call.
+ */
+lb_status lb_measure_loads(lb_ctx *ctx, double *vp_cost_ns, double *sm_busy_ns,
+                           int32_t *nsm);
+
+/*
+ * Re-map VPs to processors from the averaged costs (Sec. VI): strategy is
+ * an lb_strategy.  The new table takes effect for the next lb_step.
+ * migrations: VPs whose processor changed (host, may be NULL).
+ * pred_max_over_mean: predicted max/mean processor load under the new
+ * assignment (host, may be NULL).  LB_ESTATE if costs were never measured
+ * and the strategy needs them.
+ */
+lb_status lb_rebalance(lb_ctx *ctx, int32_t strategy, int32_t *migrations,
+                       double *pred_max_over_mean);
+
+/*
+ * Host-only planning with the library's balancers (no ctx, no GPU): the
+ * assignment `strategy` (LB_STATIC, LB_GREEDY or LB_REFINE_SWAP) produces for
+ * FP64 costs[nvps] on nprocs processors.  current[nvps] is the present
+ * assignment (needed by LB_REFINE_SWAP and for counting migrations; may be
+ * NULL, meaning the static placement).  out[nvps] receives the assignment;
+ * migrations and pred_max_over_mean may be NULL.
+ */
+lb_status lb_plan(int32_t strategy, const double *costs, int32_t nvps, int32_t nprocs,
+                  const int32_t *current, double refine_tol, int32_t *out,
+                  int32_t *migrations, double *pred_max_over_mean);
+
+/* Replace the ctx's per-VP cost average by costs[nvps] (host, FP64, >= 0,
+   finite): lets a caller balance on a cost model instead of measurements. */
+lb_status lb_set_costs(lb_ctx *ctx, const double *costs);
+
+/* Read the current VP -> processor table (host int32[nvps]); *nprocs = number
+   of processors.  Under LB_ATOMIC_QUEUE the table of the last static-type
+   strategy is returned. */
+lb_status lb_get_assignment(lb_ctx *ctx, int32_t *vp_to_proc, int32_t *nprocs);
+
+/* Install a caller-made VP -> processor table (host int32[nvps], each in
+   [0, nprocs)); leaves queue mode.  Effective from the next lb_step. */
+lb_status lb_set_assignment(lb_ctx *ctx, const int32_t *vp_to_proc);
+
+/* Point grid `grid`'s k_c source at a new device array int32[ny*nx] (the
+   load array re-drawn between segments); the array is read from the next
+   lb_step on and stays caller-owned. */
+lb_status lb_set_kc(lb_ctx *ctx, int32_t grid, const int32_t *dev_kc);
+
+/* Compensated FP64 global sum of grid `grid` after the latest step that
+   computed one (synchronises).  sum: the sum; comp: its compensation term
+   (may be NULL). */
+lb_status lb_mass(lb_ctx *ctx, int32_t grid, double *sum, double *comp);
+
+/* Global sums of grid `grid` for the last *n steps that computed one
+   (oldest first, up to max entries, at most 1024 kept); synchronises. */
+lb_status lb_mass_history(lb_ctx *ctx, int32_t grid, double *sums, int32_t max,
+                          int32_t *n);
+
+/* Device pointer of the buffer holding grid `grid`'s latest field. */
+lb_status lb_current_field(lb_ctx *ctx, int32_t grid, void **dev_ptr);
+
+/* Wait for all work of the ctx; report a pending device-side error. */
+lb_status lb_sync(lb_ctx *ctx);
+
+/*
+ * Write / read the whole run state to / from a file: step index, current
+ * fields, assignment, cost averages (the paper's full device-to-host copy
+ * around a migration, Fig. 2, becomes a checkpoint here).  lb_restore needs
+ * a ctx created with the same grids and VPs; a resumed run is bitwise equal
+ * to an uninterrupted one.
+ */
+lb_status lb_checkpoint(lb_ctx *ctx, const char *path);
+lb_status lb_restore(lb_ctx *ctx, const char *path);
+
+typedef struct {
+    int32_t nprocs;           /* processors (CTAs of the persistent kernel) */
+    int32_t nsm;              /* SMs of the device */
+    int32_t threads_per_cta;
+    int32_t max_ctas_per_sm;  /* co-residency limit of the chosen kernel */
+    int32_t nz_variant;       /* register-resident column length of the kernel */
+    int32_t exact_nz;         /* 1: kernel specialised to the grids' nz */
+    int64_t step;             /* global index of the next step */
+    int64_t work_items;       /* items of 32 columns per step */
+    int32_t strategy;         /* strategy of the current table */
+    int32_t regs_per_thread;
+} lb_info;
+
+lb_status lb_get_info(lb_ctx *ctx, lb_info *info);
+
+/* Text of the last error of ctx (or of the last lb_create failure when ctx
+   is NULL).  Owned by the library, valid until the next call on ctx. */
+const char *lb_last_error(const lb_ctx *ctx);
+
+/* Free the ctx's device tables; the caller's buffers are untouched.
+   Synchronises the stream first.  NULL is a no-op. */
+void lb_destroy(lb_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LB_H */

@@ -1,0 +1,847 @@
+// C ABI of liblb.so: ctx life cycle, validation, work tables, launches,
+// load measurement and rebalancing.  Declarations and contracts: lb.h.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "lb.h"
+#include "lb_balance.h"
+#include "lb_internal.h"
+
+using namespace lbk;
+
+struct lb_ctx {
+    cudaStream_t stream = nullptr;
+    int device = 0, nsm = 0;
+    std::vector<lb_grid_desc> grids;
+    std::vector<lb_vp> vps;
+    lb_options opt;
+    KernelInfo kinfo{};
+    int nbins = 0, threads = 0, max_ctas_per_sm = 0, regs = 0;
+    int storage = LB_F32, compute = LB_F32;
+    size_t dyn_smem = 0;
+    int nitems = 0;
+
+    GridDev *d_grids = nullptr;
+    VPDev *d_vps = nullptr;
+    int2 *d_items = nullptr;     // processor-table order
+    int2 *d_qitems = nullptr;    // queue order
+    int32_t *d_bin_start = nullptr;
+    unsigned *d_bar = nullptr;
+    int32_t *d_status = nullptr;
+    unsigned *d_qhead = nullptr;
+    unsigned long long *d_vp_cycles = nullptr;
+    unsigned long long *d_bin_busy = nullptr;
+    int32_t *d_bin_smid = nullptr;
+    long long *d_bin_cal = nullptr;
+    double *d_bin_mass = nullptr;
+    double *d_mass_hist = nullptr;
+    long long *d_mass_t = nullptr;
+    unsigned long long *d_mass_seq = nullptr;
+
+    std::vector<GridDev> h_grids;
+    std::vector<int> assign;           // VP -> processor (static-type strategies)
+    std::vector<int> vp_nchunks;
+    int strategy = LB_STATIC;
+    bool queue_mode = false;
+    int rebalances = 0;
+    std::vector<double> cost;          // per-VP cost average, ns per step
+    bool have_costs = false;
+    long long step = 0;
+    int parity = 0;
+    long long steps_since_measure = 0;
+    Coef<float> coef_f;
+    Coef<double> coef_d;
+    std::string err;
+};
+
+static thread_local std::string g_create_err;
+
+#define CK(call)                                                                     \
+    do {                                                                             \
+        cudaError_t e_ = (call);                                                     \
+        if (e_ != cudaSuccess) return fail(ctx, LB_ECUDA, std::string(#call ": ") + \
+                                                              cudaGetErrorString(e_)); \
+    } while (0)
+
+static lb_status fail(lb_ctx *ctx, lb_status s, const std::string &msg) {
+    if (ctx) ctx->err = msg;
+    else g_create_err = msg;
+    return s;
+}
+
+static size_t dtype_size(int t) { return t == LB_F64 ? 8 : (t == LB_F32 ? 4 : 2); }
+
+extern "C" void lb_default_options(lb_options *opt) {
+    if (!opt) return;
+    std::memset(opt, 0, sizeof(*opt));
+    opt->ctas_per_sm = 1;
+    opt->queue_order = 0;
+    opt->mass_every = 1;
+    opt->device_balancer = 0;
+    opt->ema_alpha = 0.5;
+    opt->refine_tol = 0.05;
+    opt->barrier_timeout_ns = 2000000000LL;
+}
+
+// ------------------------------------------------------------------ helpers
+// Pivots of the zero-flux operator M = tridiag(-r, 1+2r, -r), ends 1+r.
+// exact_nz > 0: the true table of a column of that length.  exact_nz == 0:
+// the length-independent table (every row an interior row except row 0),
+// valid for rows 0..nz-2 of any column; row nz-1 comes from last_pivot().
+static void pivots(double r, int exact_nz, double *m) {
+    for (int k = 0; k < kNzMax; ++k) {
+        double b;
+        if (exact_nz > 0 && k >= exact_nz) { m[k] = 1.0; continue; }
+        const bool last = exact_nz > 0 && k == exact_nz - 1;
+        const int nb = (k > 0 ? 1 : 0) + (last ? 0 : 1);   // neighbours of row k
+        b = 1.0 + r * nb;
+        m[k] = k == 0 ? 1.0 / b : 1.0 / (b - r * r * m[k - 1]);
+    }
+}
+
+static double last_pivot(double r, int nz) {
+    if (nz == 1) return 1.0;
+    double m = 1.0 / (1.0 + r);
+    for (int k = 1; k < nz - 1; ++k) m = 1.0 / (1.0 + 2.0 * r - r * r * m);
+    return 1.0 / (1.0 + r - r * r * m);
+}
+
+static lb_status check_status(lb_ctx *ctx) {
+    int32_t st = 0;
+    CK(cudaMemcpyAsync(&st, ctx->d_status, sizeof(st), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (st != 0) {
+        int32_t zero = 0;
+        CK(cudaMemcpyAsync(ctx->d_status, &zero, sizeof(zero), cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        if (st == LB_ETIMEOUT)
+            return fail(ctx, LB_ETIMEOUT, "grid barrier wait exceeded barrier_timeout_ns");
+        if (st == LB_ENUMERIC) return fail(ctx, LB_ENUMERIC, "global sum is not finite");
+        return fail(ctx, (lb_status)st, "device reported an error");
+    }
+    return LB_OK;
+}
+
+// Work items {vp, chunk} for the processor tables and the queue.
+static lb_status upload_items(lb_ctx *ctx) {
+    const int nv = (int)ctx->vps.size();
+    std::vector<int2> items;
+    items.reserve(ctx->nitems);
+    std::vector<int32_t> start(ctx->nbins + 1, 0);
+    std::vector<std::vector<int>> per(ctx->nbins);
+    for (int v = 0; v < nv; ++v) per[ctx->assign[v]].push_back(v);
+    for (int b = 0; b < ctx->nbins; ++b) {
+        start[b] = (int32_t)items.size();
+        for (int v : per[b])
+            for (int c = 0; c < ctx->vp_nchunks[v]; ++c) items.push_back(make_int2(v, c));
+    }
+    start[ctx->nbins] = (int32_t)items.size();
+    std::vector<int> order(nv);
+    for (int v = 0; v < nv; ++v) order[v] = v;
+    if (ctx->opt.queue_order == 1 && ctx->have_costs)
+        std::stable_sort(order.begin(), order.end(),
+                         [&](int a, int b) { return ctx->cost[a] > ctx->cost[b]; });
+    std::vector<int2> qitems;
+    qitems.reserve(ctx->nitems);
+    for (int v : order)
+        for (int c = 0; c < ctx->vp_nchunks[v]; ++c) qitems.push_back(make_int2(v, c));
+    // pageable sources are staged before these calls return; the copies are
+    // ordered on the ctx stream after any step already enqueued
+    CK(cudaMemcpyAsync(ctx->d_items, items.data(), sizeof(int2) * items.size(),
+                       cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->d_qitems, qitems.data(), sizeof(int2) * qitems.size(),
+                       cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->d_bin_start, start.data(), sizeof(int32_t) * start.size(),
+                       cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return LB_OK;
+}
+
+static void free_ctx(lb_ctx *ctx) {
+    void *ptrs[] = {ctx->d_grids,     ctx->d_vps,      ctx->d_items,     ctx->d_qitems,
+                    ctx->d_bin_start, ctx->d_bar,      ctx->d_status,    ctx->d_qhead,
+                    ctx->d_vp_cycles, ctx->d_bin_busy, ctx->d_bin_smid,  ctx->d_bin_cal,
+                    ctx->d_bin_mass,  ctx->d_mass_hist, ctx->d_mass_t,   ctx->d_mass_seq};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    delete ctx;
+}
+
+template <class T>
+static cudaError_t dalloc(T **p, size_t n) {
+    return cudaMalloc((void **)p, sizeof(T) * std::max<size_t>(n, 1));
+}
+
+// ------------------------------------------------------------------ create
+static lb_status validate(const lb_grid_desc *grids, int32_t ngrids, const lb_vp *vps,
+                          int32_t nvps) {
+    if (!grids || ngrids < 1 || ngrids > kMaxGrids)
+        return fail(nullptr, LB_EINVAL, "ngrids must be in 1..512 and grids non-NULL");
+    if (!vps || nvps < 1) return fail(nullptr, LB_EINVAL, "need at least one VP");
+    for (int g = 0; g < ngrids; ++g) {
+        const lb_grid_desc &d = grids[g];
+        char buf[160];
+        std::snprintf(buf, sizeof(buf), "grid %d: ", g);
+        std::string pre(buf);
+        if (d.nx < 1 || d.ny < 1 || d.nz < 1 || d.nz > kNzMax)
+            return fail(nullptr, LB_EINVAL, pre + "need nx, ny >= 1 and 1 <= nz <= 128");
+        if ((long long)d.nx * d.ny * d.nz >= (1LL << 31))
+            return fail(nullptr, LB_EINVAL, pre + "nx*ny*nz must be below 2^31");
+        if (!std::isfinite(d.cx) || !std::isfinite(d.cy) || !std::isfinite(d.cz) ||
+            std::fabs(d.cx) + std::fabs(d.cy) + std::fabs(d.cz) > 1.0 + 1e-12)
+            return fail(nullptr, LB_EINVAL, pre + "need |cx|+|cy|+|cz| <= 1");
+        if (!std::isfinite(d.r) || d.r < 0.0) return fail(nullptr, LB_EINVAL, pre + "need r >= 0");
+        const bool ok_types = (d.storage == LB_F64 && d.compute == LB_F64) ||
+                              (d.storage == LB_F64 && d.compute == LB_F32) ||
+                              (d.storage == LB_F32 && d.compute == LB_F32) ||
+                              (d.storage == LB_BF16 && d.compute == LB_F32);
+        if (!ok_types) return fail(nullptr, LB_EINVAL, pre + "unsupported storage/compute pair");
+        if (d.storage != grids[0].storage || d.compute != grids[0].compute)
+            return fail(nullptr, LB_EINVAL, pre + "all grids must share storage and compute");
+        if (d.r != grids[0].r) return fail(nullptr, LB_EINVAL, pre + "all grids must share r");
+        if (!d.q0 || !d.q1 || d.q0 == d.q1)
+            return fail(nullptr, LB_EINVAL, pre + "q0 and q1 must be distinct device buffers");
+        if (d.kc_disk != 0 && d.kc_disk != 1) return fail(nullptr, LB_EINVAL, pre + "kc_disk is 0 or 1");
+        if (!d.kc_disk && !d.kc) return fail(nullptr, LB_EINVAL, pre + "kc array required");
+        if (d.kc_disk && (d.k_in < 0 || d.k_out < 0 || d.disk_r < 0))
+            return fail(nullptr, LB_EINVAL, pre + "disk needs k_in, k_out, R >= 0");
+        if (d.compute == LB_F64 && d.nz > 64)
+            return fail(nullptr, LB_EINVAL, pre + "FP64 compute supports nz <= 64");
+    }
+    // the VPs must tile every grid exactly
+    std::vector<std::vector<unsigned char>> cover(ngrids);
+    for (int g = 0; g < ngrids; ++g) cover[g].assign((size_t)grids[g].nx * grids[g].ny, 0);
+    for (int v = 0; v < nvps; ++v) {
+        const lb_vp &p = vps[v];
+        if (p.grid < 0 || p.grid >= ngrids)
+            return fail(nullptr, LB_EINVAL, "VP " + std::to_string(v) + ": grid out of range");
+        const lb_grid_desc &d = grids[p.grid];
+        if (p.w < 1 || p.h < 1 || p.x0 < 0 || p.y0 < 0 || p.x0 + p.w > d.nx || p.y0 + p.h > d.ny)
+            return fail(nullptr, LB_EINVAL, "VP " + std::to_string(v) + ": outside its grid");
+        for (int j = p.y0; j < p.y0 + p.h; ++j)
+            for (int i = p.x0; i < p.x0 + p.w; ++i) {
+                unsigned char &c = cover[p.grid][(size_t)j * d.nx + i];
+                if (c) return fail(nullptr, LB_EINVAL, "VP " + std::to_string(v) + ": overlaps another VP");
+                c = 1;
+            }
+    }
+    for (int g = 0; g < ngrids; ++g)
+        for (unsigned char c : cover[g])
+            if (!c) return fail(nullptr, LB_EINVAL, "grid " + std::to_string(g) + ": VPs leave a gap");
+    return LB_OK;
+}
+
+extern "C" lb_status lb_create(const lb_grid_desc *grids, int32_t ngrids, const lb_vp *vps,
+                               int32_t nvps, const lb_options *opt, void *cuda_stream,
+                               lb_ctx **out) {
+    if (!out) return fail(nullptr, LB_EINVAL, "out is NULL");
+    *out = nullptr;
+    lb_status st = validate(grids, ngrids, vps, nvps);
+    if (st != LB_OK) return st;
+    lb_ctx *ctx = new lb_ctx();
+    if (opt) ctx->opt = *opt;
+    else lb_default_options(&ctx->opt);
+    if (ctx->opt.ctas_per_sm < 1) ctx->opt.ctas_per_sm = 1;
+    if (ctx->opt.mass_every < 0) ctx->opt.mass_every = 0;
+    if (!(ctx->opt.ema_alpha > 0.0 && ctx->opt.ema_alpha <= 1.0)) ctx->opt.ema_alpha = 0.5;
+    if (!(ctx->opt.refine_tol >= 0.0)) ctx->opt.refine_tol = 0.05;
+    if (ctx->opt.barrier_timeout_ns <= 0) ctx->opt.barrier_timeout_ns = 2000000000LL;
+    ctx->stream = (cudaStream_t)cuda_stream;
+    ctx->grids.assign(grids, grids + ngrids);
+    ctx->vps.assign(vps, vps + nvps);
+    ctx->storage = grids[0].storage;
+    ctx->compute = grids[0].compute;
+
+    auto bail = [&](lb_status s) {
+        g_create_err = ctx->err;
+        free_ctx(ctx);
+        return s;
+    };
+    cudaError_t e = cudaGetDevice(&ctx->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->nsm, cudaDevAttrMultiProcessorCount, ctx->device);
+    int coop = 0;
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, ctx->device);
+    if (e != cudaSuccess) {
+        ctx->err = std::string("no CUDA device: ") + cudaGetErrorString(e);
+        return bail(LB_ECUDA);
+    }
+    if (!coop) {
+        ctx->err = "device does not support cooperative launch";
+        return bail(LB_ENORESIDENT);
+    }
+
+    // kernel variant
+    int nzmax = 0, nzmin = kNzMax;
+    for (auto &d : ctx->grids) {
+        nzmax = std::max(nzmax, d.nz);
+        nzmin = std::min(nzmin, d.nz);
+    }
+    if (!find_step_kernel(ctx->storage, ctx->compute, nzmax, nzmin, nzmax == nzmin, &ctx->kinfo)) {
+        ctx->err = "no kernel variant for these grids";
+        return bail(LB_EINVAL);
+    }
+    ctx->threads = ctx->kinfo.threads;
+    ctx->dyn_smem = sizeof(double) * (size_t)(ctx->threads / kWarp) * ngrids;
+    if (ctx->dyn_smem > 48 * 1024) {
+        e = cudaFuncSetAttribute(ctx->kinfo.fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)ctx->dyn_smem);
+        if (e != cudaSuccess) {
+            ctx->err = std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e);
+            return bail(LB_ECUDA);
+        }
+    }
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, ctx->kinfo.fn);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctx->max_ctas_per_sm, ctx->kinfo.fn,
+                                                          ctx->threads, ctx->dyn_smem);
+    if (e != cudaSuccess) {
+        ctx->err = std::string("occupancy query: ") + cudaGetErrorString(e);
+        return bail(LB_ECUDA);
+    }
+    ctx->regs = fa.numRegs;
+    if (ctx->max_ctas_per_sm < ctx->opt.ctas_per_sm) {
+        ctx->err = "requested processors per SM cannot be co-resident (max " +
+                   std::to_string(ctx->max_ctas_per_sm) + ")";
+        return bail(LB_ENORESIDENT);
+    }
+    ctx->nbins = ctx->opt.ctas_per_sm * ctx->nsm;
+
+    // coefficients and grid table
+    const double r = grids[0].r;
+    double m[kNzMax];
+    pivots(r, ctx->kinfo.exact ? ctx->kinfo.nz_variant : 0, m);
+    for (int k = 0; k < kNzMax; ++k) {
+        ctx->coef_d.m[k] = m[k];
+        ctx->coef_d.rm[k] = r * m[k];
+        ctx->coef_f.m[k] = (float)m[k];
+        ctx->coef_f.rm[k] = (float)(r * m[k]);
+    }
+    ctx->h_grids.resize(ngrids);
+    for (int g = 0; g < ngrids; ++g) {
+        const lb_grid_desc &d = grids[g];
+        GridDev &h = ctx->h_grids[g];
+        std::memset(&h, 0, sizeof(h));
+        h.nx = d.nx;
+        h.ny = d.ny;
+        h.nz = d.nz;
+        h.kc_disk = d.kc_disk;
+        h.plane = d.nx * d.ny;
+        h.sx = d.cx >= 0 ? 1 : -1;
+        h.sy = d.cy >= 0 ? 1 : -1;
+        h.sz = d.cz >= 0 ? 1 : -1;
+        h.q[0] = d.q0;
+        h.q[1] = d.q1;
+        h.kc = d.kc;
+        h.disk_x0 = d.disk_x0;
+        h.disk_y0 = d.disk_y0;
+        h.disk_vx = d.disk_vx;
+        h.disk_vy = d.disk_vy;
+        h.disk_r = d.disk_r;
+        h.k_in = d.k_in;
+        h.k_out = d.k_out;
+        const double w[4] = {1.0 - std::fabs(d.cx) - std::fabs(d.cy) - std::fabs(d.cz),
+                             std::fabs(d.cx), std::fabs(d.cy), std::fabs(d.cz)};
+        for (int n = 0; n < 4; ++n) {
+            h.wd[n] = w[n];
+            h.wf[n] = (float)w[n];
+        }
+        h.xy_only = (w[0] == 0.0 && d.cz == 0.0) ? 1 : 0;
+        h.sweeps_on = d.r > 0.0 ? 1 : 0;
+        const double ml = last_pivot(d.r, d.nz);
+        h.mlast_d = ml;
+        h.rlast_d = d.r * ml;
+        h.mlast_f = (float)ml;
+        h.rlast_f = (float)(d.r * ml);
+    }
+
+    // VP table and work items
+    std::vector<VPDev> hv(nvps);
+    ctx->vp_nchunks.resize(nvps);
+    ctx->nitems = 0;
+    for (int v = 0; v < nvps; ++v) {
+        const lb_vp &p = vps[v];
+        hv[v] = VPDev{p.grid, p.x0, p.y0, p.w, p.h, p.w * p.h, 0, 0};
+        ctx->vp_nchunks[v] = (p.w * p.h + kWarp - 1) / kWarp;
+        ctx->nitems += ctx->vp_nchunks[v];
+    }
+    static_blocks(nvps, ctx->nbins, ctx->assign);
+    ctx->cost.assign(nvps, 0.0);
+
+    const int nb = ctx->nbins;
+    e = dalloc(&ctx->d_grids, ngrids);
+    if (e == cudaSuccess) e = dalloc(&ctx->d_vps, nvps);
+    if (e == cudaSuccess) e = dalloc(&ctx->d_items, ctx->nitems);
+    if (e == cudaSuccess) e = dalloc(&ctx->d_qitems, ctx->nitems);
+    if (e == cudaSuccess) e = dalloc(&ctx->d_bin_start, nb + 1);
+    if (e == cudaSuccess) e = dalloc(&ctx->d_bar, 2);
+    if (e == cudaSuccess) e = dalloc(&ctx->d_status, 1);
+    if (e == cudaSuccess) e = dalloc(&ctx->d_qhead, 2);
+    if (e == cudaSuccess) e = dalloc(&ctx->d_vp_cycles, nvps);
+    if (e == cudaSuccess) e = dalloc(&ctx->d_bin_busy, nb);
+    if (e == cudaSuccess) e = dalloc(&ctx->d_bin_smid, nb);
+    if (e == cudaSuccess) e = dalloc(&ctx->d_bin_cal, 4 * (size_t)nb);
+    if (e == cudaSuccess) e = dalloc(&ctx->d_bin_mass, 2 * (size_t)nb * ngrids);
+    if (e == cudaSuccess) e = dalloc(&ctx->d_mass_hist, (size_t)kMassHist * ngrids * 2);
+    if (e == cudaSuccess) e = dalloc(&ctx->d_mass_t, kMassHist);
+    if (e == cudaSuccess) e = dalloc(&ctx->d_mass_seq, 1);
+    cudaStream_t sm = ctx->stream;
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(ctx->d_grids, ctx->h_grids.data(), sizeof(GridDev) * ngrids,
+                            cudaMemcpyHostToDevice, sm);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(ctx->d_vps, hv.data(), sizeof(VPDev) * nvps, cudaMemcpyHostToDevice, sm);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_status, 0, sizeof(int32_t), sm);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_vp_cycles, 0, sizeof(unsigned long long) * nvps, sm);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_bin_busy, 0, sizeof(unsigned long long) * nb, sm);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_mass_seq, 0, sizeof(unsigned long long), sm);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_bin_cal, 0, sizeof(long long) * 4 * nb, sm);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_bin_smid, 0xff, sizeof(int32_t) * nb, sm);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(sm);
+    if (e != cudaSuccess) {
+        ctx->err = std::string("device tables: ") + cudaGetErrorString(e);
+        return bail(LB_ECUDA);
+    }
+    st = upload_items(ctx);
+    if (st != LB_OK) return bail(st);
+    *out = ctx;
+    return LB_OK;
+}
+
+// ------------------------------------------------------------------ step
+template <class TC>
+static lb_status launch(lb_ctx *ctx, int nsteps, const Coef<TC> &coef) {
+    StepParams<TC> p;
+    std::memset(&p, 0, sizeof(p));
+    p.grids = ctx->d_grids;
+    p.vps = ctx->d_vps;
+    p.items = ctx->queue_mode ? ctx->d_qitems : ctx->d_items;
+    p.bin_start = ctx->d_bin_start;
+    p.ngrids = (int)ctx->grids.size();
+    p.nvps = (int)ctx->vps.size();
+    p.nbins = ctx->nbins;
+    p.nitems = ctx->nitems;
+    p.queue_mode = ctx->queue_mode ? 1 : 0;
+    p.mass_every = ctx->opt.mass_every;
+    p.parity0 = ctx->parity;
+    p.nsteps = nsteps;
+    p.t0 = ctx->step;
+    p.timeout_ns = ctx->opt.barrier_timeout_ns;
+    p.bar = ctx->d_bar;
+    p.status = ctx->d_status;
+    p.qhead = ctx->d_qhead;
+    p.vp_cycles = ctx->d_vp_cycles;
+    p.bin_busy = ctx->d_bin_busy;
+    p.bin_smid = ctx->d_bin_smid;
+    p.bin_cal = ctx->d_bin_cal;
+    p.bin_mass = ctx->d_bin_mass;
+    p.mass_hist = ctx->d_mass_hist;
+    p.mass_t = ctx->d_mass_t;
+    p.mass_seq = ctx->d_mass_seq;
+    p.coef = coef;
+
+    CK(cudaMemsetAsync(ctx->d_bar, 0, 2 * sizeof(unsigned), ctx->stream));
+    CK(cudaMemsetAsync(ctx->d_qhead, 0, 2 * sizeof(unsigned), ctx->stream));
+    cudaLaunchConfig_t cfg;
+    std::memset(&cfg, 0, sizeof(cfg));
+    cfg.gridDim = dim3(ctx->nbins);
+    cfg.blockDim = dim3(ctx->threads);
+    cfg.dynamicSmemBytes = ctx->dyn_smem;
+    cfg.stream = ctx->stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    void *args[] = {&p};
+    CK(cudaLaunchKernelExC(&cfg, ctx->kinfo.fn, args));
+    return LB_OK;
+}
+
+extern "C" lb_status lb_step(lb_ctx *ctx, int32_t nsteps) {
+    if (!ctx) return fail(nullptr, LB_EINVAL, "ctx is NULL");
+    if (nsteps < 0) return fail(ctx, LB_EINVAL, "nsteps < 0");
+    if (nsteps == 0) return LB_OK;
+    lb_status st = ctx->compute == LB_F64 ? launch<double>(ctx, nsteps, ctx->coef_d)
+                                          : launch<float>(ctx, nsteps, ctx->coef_f);
+    if (st != LB_OK) return st;
+    ctx->step += nsteps;
+    ctx->parity ^= (nsteps & 1);
+    ctx->steps_since_measure += nsteps;
+    return LB_OK;
+}
+
+extern "C" lb_status lb_sync(lb_ctx *ctx) {
+    if (!ctx) return fail(nullptr, LB_EINVAL, "ctx is NULL");
+    return check_status(ctx);
+}
+
+// ------------------------------------------------------------------ loads
+extern "C" lb_status lb_measure_loads(lb_ctx *ctx, double *vp_cost_ns, double *sm_busy_ns,
+                                      int32_t *nsm) {
+    if (!ctx) return fail(nullptr, LB_EINVAL, "ctx is NULL");
+    lb_status st = check_status(ctx);
+    if (st != LB_OK) return st;
+    if (nsm) *nsm = ctx->nsm;
+    if (ctx->steps_since_measure <= 0) return fail(ctx, LB_ESTATE, "no step since the last measurement");
+    const int nv = (int)ctx->vps.size(), nb = ctx->nbins;
+    std::vector<unsigned long long> cyc(nv), busy(nb);
+    std::vector<int32_t> sm(nb);
+    std::vector<long long> cal(4 * (size_t)nb);
+    cudaStream_t s0 = ctx->stream;
+    CK(cudaMemcpyAsync(cyc.data(), ctx->d_vp_cycles, sizeof(unsigned long long) * nv,
+                       cudaMemcpyDeviceToHost, s0));
+    CK(cudaMemcpyAsync(busy.data(), ctx->d_bin_busy, sizeof(unsigned long long) * nb,
+                       cudaMemcpyDeviceToHost, s0));
+    CK(cudaMemcpyAsync(sm.data(), ctx->d_bin_smid, sizeof(int32_t) * nb, cudaMemcpyDeviceToHost, s0));
+    CK(cudaMemcpyAsync(cal.data(), ctx->d_bin_cal, sizeof(long long) * 4 * nb,
+                       cudaMemcpyDeviceToHost, s0));
+    CK(cudaMemsetAsync(ctx->d_vp_cycles, 0, sizeof(unsigned long long) * nv, s0));
+    CK(cudaMemsetAsync(ctx->d_bin_busy, 0, sizeof(unsigned long long) * nb, s0));
+    CK(cudaStreamSynchronize(s0));
+    // ns per SM cycle from each processor's globaltimer / clock64 pair
+    double ns = 0.0, cy = 0.0;
+    for (int b = 0; b < nb; ++b) {
+        double dn = (double)(cal[4 * b + 2] - cal[4 * b + 0]);
+        double dc = (double)(cal[4 * b + 3] - cal[4 * b + 1]);
+        if (dn > 0 && dc > 0) {
+            ns += dn;
+            cy += dc;
+        }
+    }
+    double ns_per_cycle = (cy > 0) ? ns / cy : 0.0;
+    if (!(ns_per_cycle > 0)) {
+        int khz = 0;
+        cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, ctx->device);
+        ns_per_cycle = khz > 0 ? 1e6 / khz : 1.0;
+    }
+    const double steps = (double)ctx->steps_since_measure;
+    const double a = ctx->opt.ema_alpha;
+    for (int v = 0; v < nv; ++v) {
+        double c = (double)cyc[v] * ns_per_cycle / steps;
+        ctx->cost[v] = ctx->have_costs ? a * c + (1.0 - a) * ctx->cost[v] : c;
+        if (vp_cost_ns) vp_cost_ns[v] = c;
+    }
+    ctx->have_costs = true;
+    if (sm_busy_ns) {
+        for (int s = 0; s < ctx->nsm; ++s) sm_busy_ns[s] = 0.0;
+        for (int b = 0; b < nb; ++b)
+            if (sm[b] >= 0 && sm[b] < ctx->nsm) sm_busy_ns[sm[b]] += (double)busy[b] * ns_per_cycle / steps;
+    }
+    ctx->steps_since_measure = 0;
+    return LB_OK;
+}
+
+// ------------------------------------------------------------------ balance
+extern "C" lb_status lb_plan(int32_t strategy, const double *costs, int32_t nvps, int32_t nprocs,
+                             const int32_t *current, double refine_tol, int32_t *out,
+                             int32_t *mig, double *pred) {
+    if (!costs || !out || nvps < 1 || nprocs < 1)
+        return fail(nullptr, LB_EINVAL, "lb_plan: bad arguments");
+    std::vector<double> c(costs, costs + nvps);
+    for (double x : c)
+        if (!std::isfinite(x) || x < 0) return fail(nullptr, LB_EINVAL, "lb_plan: costs must be finite and >= 0");
+    std::vector<int> cur, res;
+    if (current) {
+        cur.assign(current, current + nvps);
+        for (int b : cur)
+            if (b < 0 || b >= nprocs) return fail(nullptr, LB_EINVAL, "lb_plan: current out of range");
+    } else {
+        static_blocks(nvps, nprocs, cur);
+    }
+    if (strategy == LB_STATIC) static_blocks(nvps, nprocs, res);
+    else if (strategy == LB_GREEDY) greedy(c, nprocs, res);
+    else if (strategy == LB_REFINE_SWAP) refine_swap(c, cur, nprocs, refine_tol, res);
+    else return fail(nullptr, LB_EINVAL, "lb_plan: strategy must be STATIC, GREEDY or REFINE_SWAP");
+    for (int v = 0; v < nvps; ++v) out[v] = res[v];
+    if (mig) *mig = migrations(cur, res);
+    if (pred) *pred = max_over_mean(c, res, nprocs);
+    return LB_OK;
+}
+
+extern "C" lb_status lb_set_costs(lb_ctx *ctx, const double *costs) {
+    if (!ctx || !costs) return fail(ctx, LB_EINVAL, "lb_set_costs: bad arguments");
+    for (size_t v = 0; v < ctx->vps.size(); ++v)
+        if (!std::isfinite(costs[v]) || costs[v] < 0) return fail(ctx, LB_EINVAL, "costs must be finite and >= 0");
+    ctx->cost.assign(costs, costs + ctx->vps.size());
+    ctx->have_costs = true;
+    return LB_OK;
+}
+
+extern "C" lb_status lb_rebalance(lb_ctx *ctx, int32_t strategy, int32_t *mig, double *pred) {
+    if (!ctx) return fail(nullptr, LB_EINVAL, "ctx is NULL");
+    if (strategy < LB_STATIC || strategy > LB_AUTO) return fail(ctx, LB_EINVAL, "unknown strategy");
+    if (strategy == LB_AUTO) strategy = ctx->rebalances == 0 ? LB_GREEDY : LB_REFINE_SWAP;
+    const int nv = (int)ctx->vps.size();
+    if ((strategy == LB_GREEDY || strategy == LB_REFINE_SWAP) && !ctx->have_costs)
+        return fail(ctx, LB_ESTATE, "no measured costs yet");
+    std::vector<int> res;
+    int m = 0;
+    double pr = 1.0;
+    if (strategy == LB_ATOMIC_QUEUE) {
+        ctx->queue_mode = true;
+        // no table: report the granularity floor max(max c, mean) / mean
+        double tot = 0.0, mx = 0.0;
+        for (double c : ctx->cost) {
+            tot += c;
+            mx = std::max(mx, c);
+        }
+        double mean = tot / ctx->nbins;
+        pr = (ctx->have_costs && mean > 0) ? std::max(mx, mean) / mean : 1.0;
+    } else {
+        if (strategy == LB_STATIC) static_blocks(nv, ctx->nbins, res);
+        else if (strategy == LB_GREEDY) greedy(ctx->cost, ctx->nbins, res);
+        else refine_swap(ctx->cost, ctx->assign, ctx->nbins, ctx->opt.refine_tol, res);
+        m = migrations(ctx->assign, res);
+        pr = ctx->have_costs ? max_over_mean(ctx->cost, res, ctx->nbins) : 1.0;
+        ctx->assign = res;
+        ctx->queue_mode = false;
+        if (strategy != LB_STATIC) ctx->rebalances++;
+    }
+    ctx->strategy = strategy;
+    lb_status st = upload_items(ctx);
+    if (st != LB_OK) return st;
+    if (mig) *mig = m;
+    if (pred) *pred = pr;
+    return LB_OK;
+}
+
+extern "C" lb_status lb_get_assignment(lb_ctx *ctx, int32_t *vp_to_proc, int32_t *nprocs) {
+    if (!ctx) return fail(nullptr, LB_EINVAL, "ctx is NULL");
+    if (vp_to_proc)
+        for (size_t v = 0; v < ctx->assign.size(); ++v) vp_to_proc[v] = ctx->assign[v];
+    if (nprocs) *nprocs = ctx->nbins;
+    return LB_OK;
+}
+
+extern "C" lb_status lb_set_assignment(lb_ctx *ctx, const int32_t *vp_to_proc) {
+    if (!ctx || !vp_to_proc) return fail(ctx, LB_EINVAL, "bad arguments");
+    for (size_t v = 0; v < ctx->vps.size(); ++v)
+        if (vp_to_proc[v] < 0 || vp_to_proc[v] >= ctx->nbins)
+            return fail(ctx, LB_EINVAL, "processor index out of range");
+    ctx->assign.assign(vp_to_proc, vp_to_proc + ctx->vps.size());
+    ctx->queue_mode = false;
+    ctx->strategy = LB_STATIC;
+    return upload_items(ctx);
+}
+
+// ------------------------------------------------------------------ fields
+extern "C" lb_status lb_set_kc(lb_ctx *ctx, int32_t grid, const int32_t *dev_kc) {
+    if (!ctx) return fail(nullptr, LB_EINVAL, "ctx is NULL");
+    if (grid < 0 || grid >= (int)ctx->grids.size() || !dev_kc)
+        return fail(ctx, LB_EINVAL, "lb_set_kc: bad grid or NULL array");
+    if (ctx->grids[grid].kc_disk) return fail(ctx, LB_ESTATE, "grid uses the disk rule");
+    ctx->grids[grid].kc = dev_kc;
+    ctx->h_grids[grid].kc = dev_kc;
+    CK(cudaMemcpyAsync(&ctx->d_grids[grid], &ctx->h_grids[grid], sizeof(GridDev),
+                       cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return LB_OK;
+}
+
+extern "C" lb_status lb_current_field(lb_ctx *ctx, int32_t grid, void **dev_ptr) {
+    if (!ctx) return fail(nullptr, LB_EINVAL, "ctx is NULL");
+    if (grid < 0 || grid >= (int)ctx->grids.size() || !dev_ptr)
+        return fail(ctx, LB_EINVAL, "bad grid or NULL output");
+    *dev_ptr = ctx->parity ? ctx->grids[grid].q1 : ctx->grids[grid].q0;
+    return LB_OK;
+}
+
+extern "C" lb_status lb_mass_history(lb_ctx *ctx, int32_t grid, double *sums, int32_t max,
+                                     int32_t *n) {
+    if (!ctx) return fail(nullptr, LB_EINVAL, "ctx is NULL");
+    if (grid < 0 || grid >= (int)ctx->grids.size()) return fail(ctx, LB_EINVAL, "bad grid");
+    lb_status st = check_status(ctx);
+    if (st != LB_OK) return st;
+    unsigned long long seq = 0;
+    CK(cudaMemcpyAsync(&seq, ctx->d_mass_seq, sizeof(seq), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    const int ng = (int)ctx->grids.size();
+    long long avail = (long long)std::min<unsigned long long>(seq, kMassHist);
+    long long cnt = std::min<long long>(avail, std::max(max, 0));
+    if (n) *n = (int32_t)cnt;
+    if (cnt == 0 || !sums) return LB_OK;
+    std::vector<double> hist((size_t)kMassHist * ng * 2);
+    CK(cudaMemcpyAsync(hist.data(), ctx->d_mass_hist, sizeof(double) * hist.size(),
+                       cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (long long i = 0; i < cnt; ++i) {
+        unsigned long long s = seq - cnt + i;
+        const double *e = &hist[((size_t)(s % kMassHist) * ng + grid) * 2];
+        sums[i] = e[0] + e[1];
+    }
+    return LB_OK;
+}
+
+extern "C" lb_status lb_mass(lb_ctx *ctx, int32_t grid, double *sum, double *comp) {
+    if (!ctx) return fail(nullptr, LB_EINVAL, "ctx is NULL");
+    if (grid < 0 || grid >= (int)ctx->grids.size()) return fail(ctx, LB_EINVAL, "bad grid");
+    lb_status st = check_status(ctx);
+    if (st != LB_OK) return st;
+    unsigned long long seq = 0;
+    CK(cudaMemcpyAsync(&seq, ctx->d_mass_seq, sizeof(seq), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (seq == 0) return fail(ctx, LB_ESTATE, "no global sum computed yet");
+    const int ng = (int)ctx->grids.size();
+    double e[2];
+    CK(cudaMemcpyAsync(e, ctx->d_mass_hist + ((size_t)((seq - 1) % kMassHist) * ng + grid) * 2,
+                       sizeof(e), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (sum) *sum = e[0] + e[1];
+    if (comp) *comp = e[1];
+    return LB_OK;
+}
+
+// ------------------------------------------------------------------ checkpoint
+static const char kMagic[8] = {'L', 'B', 'C', 'K', 'P', 'T', '0', '1'};
+
+extern "C" lb_status lb_checkpoint(lb_ctx *ctx, const char *path) {
+    if (!ctx || !path) return fail(ctx, LB_EINVAL, "bad arguments");
+    lb_status st = check_status(ctx);
+    if (st != LB_OK) return st;
+    FILE *f = std::fopen(path, "wb");
+    if (!f) return fail(ctx, LB_EIO, std::string("cannot open ") + path);
+    bool ok = true;
+    auto W = [&](const void *p, size_t n) { ok = ok && std::fwrite(p, 1, n, f) == n; };
+    int32_t hdr[6] = {(int32_t)ctx->grids.size(), (int32_t)ctx->vps.size(), ctx->nbins,
+                      ctx->parity, ctx->strategy, ctx->queue_mode ? 1 : 0};
+    int32_t hdr2[2] = {ctx->rebalances, ctx->have_costs ? 1 : 0};
+    W(kMagic, 8);
+    W(hdr, sizeof(hdr));
+    W(hdr2, sizeof(hdr2));
+    W(&ctx->step, sizeof(ctx->step));
+    for (auto &g : ctx->grids) {
+        int32_t dims[4] = {g.nx, g.ny, g.nz, g.storage};
+        W(dims, sizeof(dims));
+    }
+    W(ctx->assign.data(), sizeof(int) * ctx->assign.size());
+    W(ctx->cost.data(), sizeof(double) * ctx->cost.size());
+    std::vector<char> buf;
+    for (auto &g : ctx->grids) {
+        size_t bytes = (size_t)g.nx * g.ny * g.nz * dtype_size(g.storage);
+        buf.resize(bytes);
+        cudaError_t e = cudaMemcpyAsync(buf.data(), ctx->parity ? g.q1 : g.q0, bytes,
+                                        cudaMemcpyDeviceToHost, ctx->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) {
+            std::fclose(f);
+            return fail(ctx, LB_ECUDA, cudaGetErrorString(e));
+        }
+        W(buf.data(), bytes);
+    }
+    ok = (std::fclose(f) == 0) && ok;
+    if (!ok) return fail(ctx, LB_EIO, std::string("write failed: ") + path);
+    return LB_OK;
+}
+
+extern "C" lb_status lb_restore(lb_ctx *ctx, const char *path) {
+    if (!ctx || !path) return fail(ctx, LB_EINVAL, "bad arguments");
+    CK(cudaStreamSynchronize(ctx->stream));
+    FILE *f = std::fopen(path, "rb");
+    if (!f) return fail(ctx, LB_EIO, std::string("cannot open ") + path);
+    bool ok = true;
+    auto R = [&](void *p, size_t n) { ok = ok && std::fread(p, 1, n, f) == n; };
+    char magic[8];
+    int32_t hdr[6], hdr2[2];
+    long long step = 0;
+    R(magic, 8);
+    R(hdr, sizeof(hdr));
+    R(hdr2, sizeof(hdr2));
+    R(&step, sizeof(step));
+    if (!ok || std::memcmp(magic, kMagic, 8) != 0 || hdr[0] != (int32_t)ctx->grids.size() ||
+        hdr[1] != (int32_t)ctx->vps.size()) {
+        std::fclose(f);
+        return fail(ctx, LB_EINVAL, "checkpoint does not match this ctx");
+    }
+    for (auto &g : ctx->grids) {
+        int32_t dims[4];
+        R(dims, sizeof(dims));
+        if (!ok || dims[0] != g.nx || dims[1] != g.ny || dims[2] != g.nz || dims[3] != g.storage) {
+            std::fclose(f);
+            return fail(ctx, LB_EINVAL, "checkpoint grid dimensions differ");
+        }
+    }
+    std::vector<int> assign(ctx->vps.size());
+    std::vector<double> cost(ctx->vps.size());
+    R(assign.data(), sizeof(int) * assign.size());
+    R(cost.data(), sizeof(double) * cost.size());
+    const int parity = hdr[3] & 1;
+    std::vector<char> buf;
+    for (auto &g : ctx->grids) {
+        size_t bytes = (size_t)g.nx * g.ny * g.nz * dtype_size(g.storage);
+        buf.resize(bytes);
+        R(buf.data(), bytes);
+        if (!ok) break;
+        cudaError_t e = cudaMemcpyAsync(parity ? g.q1 : g.q0, buf.data(), bytes,
+                                        cudaMemcpyHostToDevice, ctx->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) {
+            std::fclose(f);
+            return fail(ctx, LB_ECUDA, cudaGetErrorString(e));
+        }
+    }
+    std::fclose(f);
+    if (!ok) return fail(ctx, LB_EIO, "checkpoint truncated");
+    if (hdr[2] != ctx->nbins) {
+        // different processor count: keep the static placement
+        static_blocks((int)ctx->vps.size(), ctx->nbins, assign);
+    }
+    for (int b : assign)
+        if (b < 0 || b >= ctx->nbins) return fail(ctx, LB_EINVAL, "checkpoint assignment out of range");
+    ctx->assign = assign;
+    ctx->cost = cost;
+    ctx->have_costs = hdr2[1] != 0;
+    ctx->rebalances = hdr2[0];
+    ctx->strategy = hdr[4];
+    ctx->queue_mode = hdr[5] != 0;
+    ctx->step = step;
+    ctx->parity = parity;
+    ctx->steps_since_measure = 0;
+    CK(cudaMemsetAsync(ctx->d_vp_cycles, 0, sizeof(unsigned long long) * ctx->vps.size(), ctx->stream));
+    CK(cudaMemsetAsync(ctx->d_bin_busy, 0, sizeof(unsigned long long) * ctx->nbins, ctx->stream));
+    return upload_items(ctx);
+}
+
+// ------------------------------------------------------------------ misc
+extern "C" lb_status lb_get_info(lb_ctx *ctx, lb_info *info) {
+    if (!ctx || !info) return fail(ctx, LB_EINVAL, "bad arguments");
+    info->nprocs = ctx->nbins;
+    info->nsm = ctx->nsm;
+    info->threads_per_cta = ctx->threads;
+    info->max_ctas_per_sm = ctx->max_ctas_per_sm;
+    info->nz_variant = ctx->kinfo.nz_variant;
+    info->exact_nz = ctx->kinfo.exact;
+    info->step = ctx->step;
+    info->work_items = ctx->nitems;
+    info->strategy = ctx->queue_mode ? LB_ATOMIC_QUEUE : ctx->strategy;
+    info->regs_per_thread = ctx->regs;
+    return LB_OK;
+}
+
+extern "C" const char *lb_last_error(const lb_ctx *ctx) {
+    return ctx ? ctx->err.c_str() : g_create_err.c_str();
+}
+
+extern "C" void lb_destroy(lb_ctx *ctx) {
+    if (!ctx) return;
+    cudaStreamSynchronize(ctx->stream);
+    free_ctx(ctx);
+}
+
+namespace lbk {
+bool find_step_kernel(int storage, int compute, int nz_max, int nz_min, bool same, KernelInfo *out) {
+    if (storage == LB_F32 && compute == LB_F32) return kernels_f32(nz_max, nz_min, same, out);
+    if (storage == LB_F64 && compute == LB_F64) return kernels_f64(nz_max, nz_min, same, out);
+    if (storage == LB_F64 && compute == LB_F32) return kernels_f64s(nz_max, nz_min, same, out);
+    if (storage == LB_BF16 && compute == LB_F32) return kernels_bf16(nz_max, nz_min, same, out);
+    return false;
+}
+}  // namespace lbk

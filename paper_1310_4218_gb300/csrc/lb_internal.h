@@ -1,0 +1,89 @@
+// Internal declarations shared by the library's translation units.
+// Device-side tables of a ctx and the persistent step kernel's parameters.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "lb.h"
+
+namespace lbk {
+
+constexpr int kNzMax = 128;        // longest register-resident column
+constexpr int kMassHist = 1024;    // global sums kept per grid
+constexpr int kMaxGrids = 512;
+constexpr int kWarp = 32;
+
+// One grid as the kernel sees it.
+struct GridDev {
+    int32_t nx, ny, nz, kc_disk;
+    int32_t plane;                 // nx*ny
+    int32_t sx, sy, sz;            // upwind direction per axis (+1: neighbour at -1)
+    void *q[2];                    // ping-pong fields
+    const int32_t *kc;             // k_c array (kc_disk == 0)
+    int32_t disk_x0, disk_y0, disk_vx, disk_vy, disk_r, k_in, k_out;
+    int32_t xy_only;               // w0 == 0 and wz == 0: two-neighbour stencil
+    int32_t sweeps_on;             // r > 0
+    int32_t pad0;
+    float wf[4];                   // w0, |cx|, |cy|, |cz| for FP32 compute
+    double wd[4];                  // same for FP64 compute
+    float mlast_f, rlast_f;        // last-row coefficients (runtime-nz kernels)
+    double mlast_d, rlast_d;
+};
+
+// One VP (rectangle of columns of one grid).
+struct VPDev {
+    int32_t grid, x0, y0, w, h, ncols, pad0, pad1;
+};
+
+// Thomas coefficients of the zero-flux operator for the kernel's compute
+// type: m[k] = 1/pivot_k, rm[k] = r*m[k] (FP64 values rounded once).
+template <class TC>
+struct Coef {
+    TC m[kNzMax];
+    TC rm[kNzMax];
+};
+
+template <class TC>
+struct StepParams {
+    const GridDev *grids;
+    const VPDev *vps;
+    const int2 *items;             // work items {vp, chunk}: table or queue order
+    const int32_t *bin_start;      // [nbins+1] item ranges per processor
+    int32_t ngrids, nvps, nbins, nitems;
+    int32_t queue_mode, mass_every, parity0, nsteps;
+    int64_t t0;
+    int64_t timeout_ns;
+    unsigned *bar;                 // [0] arrivals, [1] generation
+    int32_t *status;               // sticky lb_status of device failures
+    unsigned *qhead;               // [2] queue counters (step parity)
+    unsigned long long *vp_cycles; // [nvps] summed work-item cycles
+    unsigned long long *bin_busy;  // [nbins] summed busy cycles per step
+    int32_t *bin_smid;             // [nbins]
+    long long *bin_cal;            // [nbins][4]: globaltimer0, clock0, globaltimer1, clock1
+    double *bin_mass;              // [2][nbins][ngrids]
+    double *mass_hist;             // [kMassHist][ngrids][2] (sum, comp)
+    long long *mass_t;             // [kMassHist] step index of each entry
+    unsigned long long *mass_seq;  // number of entries written so far
+    Coef<TC> coef;
+};
+
+// Kernel lookup: returns the persistent kernel for a (storage, compute,
+// nz-variant) triple, or nullptr.  exact=1: specialised to nz == variant.
+struct KernelInfo {
+    const void *fn;
+    int threads;
+    int nz_variant;
+    int exact;
+};
+bool find_step_kernel(int storage, int compute, int nz_max, int nz_min, bool all_same_nz,
+                      KernelInfo *out);
+
+// Per-type kernel tables (one translation unit each, compiled in parallel).
+bool kernels_f32(int nz_max, int nz_min, bool same, KernelInfo *out);
+bool kernels_f64(int nz_max, int nz_min, bool same, KernelInfo *out);
+bool kernels_f64s(int nz_max, int nz_min, bool same, KernelInfo *out);
+bool kernels_bf16(int nz_max, int nz_min, bool same, KernelInfo *out);
+bool kernels_f32_any(int nz_max, int nz_min, KernelInfo *out);
+
+}  // namespace lbk

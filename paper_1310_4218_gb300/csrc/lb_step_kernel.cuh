@@ -1,0 +1,466 @@
+// Persistent step kernel: every VP of every grid, nsteps time steps, one
+// cooperative launch.
+//
+// Work decomposition.  A VP (Sec. III over-decomposition) is cut into work
+// items of 32 consecutive columns of its row-major column order, one column
+// per lane.  A processor (CTA) owns a contiguous range of the item table;
+// its warps pop items from a shared-memory counter.  In queue mode every warp
+// pops from one global counter instead (the task-queue scheme of Sec. II).
+//
+// Per column and step (Fig. 2's JACOBI then PHYSIC kernels, fused):
+//   1. upwind advection of the whole column into registers (level by level,
+//      coalesced across the warp: lanes are x-adjacent columns);
+//   2. k_c(i,j,t) from the moving-disk rule or the k_c array (Sec. VI-B);
+//   3. k_c implicit vertical-diffusion solves in registers (Thomas: forward
+//      elimination and back substitution, the serial-in-k recurrence of
+//      Fig. 1 / Fig. 4).  The column is shifted by a reference value c
+//      before the solves and shifted back after: M 1 = 1, so
+//      M^-k (d - c1) + c1 = M^-k d exactly, while the rounding of the FP32
+//      pivots now acts on the small deviation d - c1 instead of on d;
+//   4. store of the new column; compensated sum of the stored values for
+//      the global sum diagnostic.
+// Each work item's duration (clock64, lane 0) is added to its VP's cost:
+// the on-device load measurement of Sec. V.  A grid-wide barrier with a
+// time limit separates steps.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include "lb_internal.h"
+
+namespace lbk {
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ int smid() {
+    int s;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(s));
+    return s;
+}
+
+// ------------------------------------------------------------ storage I/O
+template <class TS, class TC> struct IO;
+template <> struct IO<float, float> {
+    static __device__ __forceinline__ float ld(const float *p) { return *p; }
+    static __device__ __forceinline__ float st(float *p, float x) { *p = x; return x; }
+};
+template <> struct IO<double, double> {
+    static __device__ __forceinline__ double ld(const double *p) { return *p; }
+    static __device__ __forceinline__ double st(double *p, double x) { *p = x; return x; }
+};
+template <> struct IO<double, float> {
+    static __device__ __forceinline__ float ld(const double *p) { return (float)*p; }
+    static __device__ __forceinline__ float st(double *p, float x) { *p = (double)x; return x; }
+};
+template <> struct IO<__nv_bfloat16, float> {
+    static __device__ __forceinline__ float ld(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
+    static __device__ __forceinline__ float st(__nv_bfloat16 *p, float x) {
+        __nv_bfloat16 b = __float2bfloat16_rn(x);
+        *p = b;
+        return __bfloat162float(b);
+    }
+};
+
+// ------------------------------------------------------------ compensated sums
+// Per-lane accumulator of stored values.  FP32 compute: per column, the
+// running sum and the exact rounding error of every addition (TwoSum, Knuth)
+// are kept apart ("Sum2" of Ogita, Rump and Oishi, accurate as if summed in
+// twice the working precision); the column's (sum, error) pair then goes
+// into a double-float lane total, converted to FP64 only when flushed.
+// FP64 compute: plain FP64 sums.
+template <class TC> struct LaneSum;
+template <> struct LaneSum<float> {
+    float hi = 0.f, lo = 0.f;   // lane total
+    float s = 0.f, e = 0.f;     // current column: sum, summed errors
+    __device__ __forceinline__ void col_begin() { s = 0.f; e = 0.f; }
+    __device__ __forceinline__ void add(float v) {
+        float t = __fadd_rn(s, v);
+        float bp = __fsub_rn(t, s);
+        float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(v, bp));
+        e = __fadd_rn(e, err);
+        s = t;
+    }
+    __device__ __forceinline__ void col_end() {
+        float t = __fadd_rn(hi, s);
+        float bp = __fsub_rn(t, hi);
+        float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(t, bp)), __fsub_rn(s, bp));
+        hi = t;
+        lo = __fadd_rn(lo, __fadd_rn(err, e));
+    }
+    __device__ __forceinline__ double take() {
+        double v = (double)hi + (double)lo;
+        hi = lo = 0.f;
+        return v;
+    }
+};
+template <> struct LaneSum<double> {
+    double tot = 0.0, s = 0.0;
+    __device__ __forceinline__ void col_begin() { s = 0.0; }
+    __device__ __forceinline__ void add(double v) { s += v; }
+    __device__ __forceinline__ void col_end() { tot += s; }
+    __device__ __forceinline__ double take() {
+        double v = tot;
+        tot = 0.0;
+        return v;
+    }
+};
+
+// ------------------------------------------------------------ load rule
+// Moving disk (Sec. VI-B): k_in inside radius R of (x0,y0)+t(vx,vy), periodic
+// minimum-image distance, exact integer arithmetic.
+__device__ __forceinline__ int kc_disk(const GridDev &g, int i, int j, long long t) {
+    long long cx = ((long long)g.disk_x0 + t * g.disk_vx) % g.nx;
+    long long cy = ((long long)g.disk_y0 + t * g.disk_vy) % g.ny;
+    if (cx < 0) cx += g.nx;
+    if (cy < 0) cy += g.ny;
+    int dx = i - (int)cx;
+    int dy = j - (int)cy;
+    if (dx < 0) dx += g.nx;
+    if (dy < 0) dy += g.ny;
+    if (dx > g.nx / 2) dx -= g.nx;
+    if (dy > g.ny / 2) dy -= g.ny;
+    long long d2 = (long long)dx * dx + (long long)dy * dy;
+    return d2 <= (long long)g.disk_r * g.disk_r ? g.k_in : g.k_out;
+}
+
+template <class TC> __device__ __forceinline__ TC wgt(const GridDev &g, int n);
+template <> __device__ __forceinline__ float wgt<float>(const GridDev &g, int n) { return g.wf[n]; }
+template <> __device__ __forceinline__ double wgt<double>(const GridDev &g, int n) { return g.wd[n]; }
+template <class TC> __device__ __forceinline__ TC mlast(const GridDev &g);
+template <> __device__ __forceinline__ float mlast<float>(const GridDev &g) { return g.mlast_f; }
+template <> __device__ __forceinline__ double mlast<double>(const GridDev &g) { return g.mlast_d; }
+template <class TC> __device__ __forceinline__ TC rlast(const GridDev &g);
+template <> __device__ __forceinline__ float rlast<float>(const GridDev &g) { return g.rlast_f; }
+template <> __device__ __forceinline__ double rlast<double>(const GridDev &g) { return g.rlast_d; }
+
+__device__ __forceinline__ float fmaT(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fmaT(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// ------------------------------------------------------------ one Thomas solve
+// In place on y[0..nz-1]: forward p_k = (y_k + r p_{k-1}) m_k, back
+// x_k = p_k + r m_k x_{k+1}.  EXACT: nz == NZ, every coefficient is a
+// kernel-parameter constant.  Otherwise nz <= NZ at run time (warp-uniform):
+// rows below nz-1 use the nz-independent table, row nz-1 the grid's
+// last-row pivot (ml, rl = r*ml), and the forward sweep stops there.  Rows
+// >= nz hold exact zeros that the forward sweep never touches, so the full
+// back substitution leaves them zero and starts row nz-1 from x_nz = 0.
+template <class TC, int NZ, bool EXACT, int NZLO>
+__device__ __forceinline__ void thomas_solve(TC (&y)[NZ], const Coef<TC> &cf, int nz,
+                                             TC ml, TC rl) {
+    if (EXACT || NZLO > 1 || nz > 1) {
+        TC p = y[0] * cf.m[0];
+        y[0] = p;
+#pragma unroll
+        for (int k = 1; k < NZ; ++k) {
+            if (EXACT || k < NZLO - 1 || k < nz - 1) {
+                p = fmaT(p, cf.rm[k], y[k] * cf.m[k]);
+                y[k] = p;
+            } else if (k == nz - 1) {
+                y[k] = fmaT(p, rl, y[k] * ml);
+            }
+        }
+    } else {
+        y[0] = y[0] * ml;
+    }
+#pragma unroll
+    for (int k = NZ - 2; k >= 0; --k) y[k] = fmaT(cf.rm[k], y[k + 1], y[k]);
+}
+
+// ------------------------------------------------------------ one work item
+// Column geometry of a lane within a work item.
+struct ColGeom {
+    int i, j, oc, oi, oj;
+    bool active;
+};
+
+__device__ __forceinline__ ColGeom col_geom(const GridDev &g, const VPDev &vp, int chunk, int lane) {
+    ColGeom c;
+    const int q = chunk * kWarp + lane;
+    c.active = q < vp.ncols;
+    const int qq = c.active ? q : vp.ncols - 1;
+    const int ly = qq / vp.w;
+    c.i = vp.x0 + (qq - ly * vp.w);
+    c.j = vp.y0 + ly;
+    int im = c.i - g.sx, jm = c.j - g.sy;
+    im = im < 0 ? im + g.nx : (im >= g.nx ? im - g.nx : im);
+    jm = jm < 0 ? jm + g.ny : (jm >= g.ny ? jm - g.ny : jm);
+    c.oc = c.j * g.nx + c.i;
+    c.oi = c.j * g.nx + im;
+    c.oj = jm * g.nx + c.i;
+    return c;
+}
+
+// Advection and the k_c solves: leaves the new column in y, minus cref.
+template <class TS, class TC, int NZ, bool EXACT, int NZLO>
+__device__ __forceinline__ void column_physics(const StepParams<TC> &p, const GridDev &g,
+                                               const ColGeom &cg, long long t, int src,
+                                               TC (&y)[NZ], TC &cref) {
+    const int nz = EXACT ? NZ : g.nz;
+    const TS *in = static_cast<const TS *>(g.q[src]);
+    const int plane = g.plane;
+    int kc = g.kc_disk ? kc_disk(g, cg.i, cg.j, t) : g.kc[cg.oc];
+    if (!cg.active || !g.sweeps_on) kc = 0;
+
+    // 1. advection into registers (rows >= nz: exact zeros)
+    const TC wx = wgt<TC>(g, 1), wy = wgt<TC>(g, 2);
+    if (g.xy_only) {
+#pragma unroll
+        for (int k = 0; k < NZ; ++k) {
+            if (EXACT || k < NZLO || k < nz) {
+                TC a = IO<TS, TC>::ld(in + (k * plane + cg.oi));
+                TC b = IO<TS, TC>::ld(in + (k * plane + cg.oj));
+                y[k] = fmaT(wy, b, wx * a);
+            } else {
+                y[k] = TC(0);
+            }
+        }
+    } else {
+        // general form: own value, and the vertical upwind neighbour with
+        // closed end faces (the cell at the closed downwind face keeps its
+        // outflow, the cell at the closed upwind face gets no inflow)
+        const TC w0 = wgt<TC>(g, 0), wz = wgt<TC>(g, 3);
+        const int sz = g.sz;
+        const int kdown = sz >= 0 ? nz - 1 : 0;
+#pragma unroll
+        for (int k = 0; k < NZ; ++k) {
+            if (EXACT || k < NZLO || k < nz) {
+                TC c = IO<TS, TC>::ld(in + (k * plane + cg.oc));
+                TC a = IO<TS, TC>::ld(in + (k * plane + cg.oi));
+                TC b = IO<TS, TC>::ld(in + (k * plane + cg.oj));
+                TC v = fmaT(wy, b, wx * a);
+                v = fmaT(k == kdown ? w0 + wz : w0, c, v);
+                const int ku = k - sz;
+                if (ku >= 0 && ku < nz) v = fmaT(wz, IO<TS, TC>::ld(in + (ku * plane + cg.oc)), v);
+                y[k] = v;
+            } else {
+                y[k] = TC(0);
+            }
+        }
+    }
+
+    // 2.-3. shift, k_c implicit solves (the shift back happens at the store)
+    cref = TC(0);
+    if (kc > 0) {
+        cref = y[EXACT ? NZ / 2 : 0];
+#pragma unroll
+        for (int k = 0; k < NZ; ++k)
+            if (EXACT || k < NZLO || k < nz) y[k] -= cref;
+        const TC ml = EXACT ? TC(0) : mlast<TC>(g);
+        const TC rl = EXACT ? TC(0) : rlast<TC>(g);
+        for (int s = 0; s < kc; ++s) thomas_solve<TC, NZ, EXACT, NZLO>(y, p.coef, nz, ml, rl);
+    }
+}
+
+// 4. shift back, store, compensated sum of the stored values.
+template <class TS, class TC, int NZ, bool EXACT, int NZLO, bool MASS>
+__device__ __forceinline__ void store_column(const GridDev &g, const ColGeom &cg, int src,
+                                             const TC (&y)[NZ], TC cref, LaneSum<TC> &acc) {
+    const int nz = EXACT ? NZ : g.nz;
+    TS *out = static_cast<TS *>(g.q[src ^ 1]);
+    const int plane = g.plane;
+    if (!cg.active) return;
+    if (MASS) acc.col_begin();
+#pragma unroll
+    for (int k = 0; k < NZ; ++k) {
+        if (EXACT || k < NZLO || k < nz) {
+            TC xs = IO<TS, TC>::st(out + (k * plane + cg.oc), y[k] + cref);
+            if (MASS) acc.add(xs);
+        }
+    }
+    if (MASS) acc.col_end();
+}
+
+template <class TS, class TC, int NZ, bool EXACT, int NZLO>
+__device__ __forceinline__ void process_item(const StepParams<TC> &p, const GridDev &g,
+                                             const VPDev &vp, int chunk, long long t, int src,
+                                             int lane, bool do_mass, LaneSum<TC> &acc) {
+    const ColGeom cg = col_geom(g, vp, chunk, lane);
+    TC y[NZ];
+    TC cref;
+    column_physics<TS, TC, NZ, EXACT, NZLO>(p, g, cg, t, src, y, cref);
+    if (do_mass) store_column<TS, TC, NZ, EXACT, NZLO, true>(g, cg, src, y, cref, acc);
+    else store_column<TS, TC, NZ, EXACT, NZLO, false>(g, cg, src, y, cref, acc);
+}
+
+// ------------------------------------------------------------ grid barrier
+// Sense-reversing barrier over all CTAs with a time limit.  On timeout the
+// CTA records LB_ETIMEOUT in the status word and returns false; so does
+// every CTA that sees a recorded failure while waiting.
+__device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned nblocks, long long timeout_ns,
+                                             int32_t *status, int *s_flag) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned *vgen = bar + 1;
+        volatile int32_t *vst = status;
+        int ok = 1;
+        unsigned gen = *vgen;
+        __threadfence();
+        unsigned prev = atomicAdd(bar, 1u);
+        if (prev == nblocks - 1) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            unsigned long long t0 = globaltimer_ns();
+            long long c0 = clock64();
+            unsigned it = 0;
+            while (*vgen == gen) {
+                if ((++it & 31u) == 0u) {
+                    if (*vst != 0) { ok = 0; break; }
+                    unsigned long long el = globaltimer_ns() - t0;
+                    long long ec = clock64() - c0;
+                    if ((long long)el > timeout_ns || ec > 4 * timeout_ns) {
+                        atomicCAS(status, 0, (int32_t)LB_ETIMEOUT);
+                        ok = 0;
+                        break;
+                    }
+                }
+                __nanosleep(100);
+            }
+        }
+        __threadfence();
+        *s_flag = ok && (*vst == 0);
+    }
+    __syncthreads();
+    return *s_flag != 0;
+}
+
+// ------------------------------------------------------------ global sums
+// Processor 0 folds the per-processor partial sums of step s (of this launch)
+// into one Neumaier-compensated FP64 sum per grid, in processor order, and
+// appends it to the history ring.  Called after the barrier that ends step s.
+template <class TC, int THREADS>
+__device__ __forceinline__ void reduce_mass(const StepParams<TC> &p, int s) {
+    const long long tp = p.t0 + s;
+    if (!(p.mass_every > 0 && ((tp + 1) % p.mass_every) == 0)) return;
+    const int par = s & 1;
+    const unsigned long long seq = *p.mass_seq;
+    for (int gi = threadIdx.x; gi < p.ngrids; gi += THREADS) {
+        double sum = 0.0, comp = 0.0;
+        for (int b = 0; b < p.nbins; ++b) {
+            double v = p.bin_mass[((size_t)par * p.nbins + b) * p.ngrids + gi];
+            double tt = sum + v;
+            comp += fabs(sum) >= fabs(v) ? (sum - tt) + v : (v - tt) + sum;
+            sum = tt;
+        }
+        double *e = p.mass_hist + ((size_t)(seq % kMassHist) * p.ngrids + gi) * 2;
+        e[0] = sum;
+        e[1] = comp;
+        if (!isfinite(sum + comp)) atomicCAS(p.status, 0, (int32_t)LB_ENUMERIC);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        p.mass_t[seq % kMassHist] = tp;
+        __threadfence();
+        *p.mass_seq = seq + 1;
+    }
+}
+
+// ------------------------------------------------------------ the kernel
+template <class TS, class TC, int NZ, bool EXACT, int NZLO, int THREADS>
+__global__ void __launch_bounds__(THREADS, 1)
+lb_step_kernel(const __grid_constant__ StepParams<TC> p) {
+    extern __shared__ double s_mass[];          // [warps][ngrids]
+    __shared__ int s_ctr;
+    __shared__ int s_flag;
+    __shared__ unsigned long long s_t0, s_tend;
+    constexpr int kWarps = THREADS / kWarp;
+    const int bin = blockIdx.x;
+    const int warp = threadIdx.x / kWarp;
+    const int lane = threadIdx.x % kWarp;
+
+    if (threadIdx.x == 0) {
+        p.bin_smid[bin] = smid();
+        p.bin_cal[4 * bin + 0] = (long long)globaltimer_ns();
+        p.bin_cal[4 * bin + 1] = clock64();
+    }
+    const int ibeg = p.queue_mode ? 0 : p.bin_start[bin];
+    const int iend = p.queue_mode ? p.nitems : p.bin_start[bin + 1];
+
+    for (int s = 0; s < p.nsteps; ++s) {
+        const long long t = p.t0 + s;
+        const int src = (p.parity0 + s) & 1;
+        const bool do_mass = p.mass_every > 0 && ((t + 1) % p.mass_every) == 0;
+
+        // reduce the previous step's per-processor sums (processor 0 only)
+        if (bin == 0 && s > 0) reduce_mass<TC, THREADS>(p, s - 1);
+
+        if (threadIdx.x == 0) {
+            s_ctr = 0;
+            s_tend = 0ull;
+            s_t0 = (unsigned long long)clock64();
+            if (bin == 0) p.qhead[(s + 1) & 1] = 0u;
+        }
+        if (do_mass)
+            for (int n = threadIdx.x; n < kWarps * p.ngrids; n += THREADS) s_mass[n] = 0.0;
+        __syncthreads();
+
+        LaneSum<TC> acc;
+        int cur_grid = -1;
+        for (;;) {
+            int c = 0;
+            if (lane == 0)
+                c = p.queue_mode ? (int)atomicAdd(&p.qhead[s & 1], 1u) : atomicAdd(&s_ctr, 1);
+            c = __shfl_sync(0xffffffffu, c, 0) + ibeg;
+            if (c >= iend) break;
+            const int2 it = p.items[c];
+            const VPDev vp = p.vps[it.x];
+            const GridDev &g = p.grids[vp.grid];
+            if (do_mass && vp.grid != cur_grid) {
+                if (cur_grid >= 0) {
+                    double v = acc.take();
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                    if (lane == 0) s_mass[warp * p.ngrids + cur_grid] += v;
+                }
+                cur_grid = vp.grid;
+            }
+            long long c0 = clock64();
+            process_item<TS, TC, NZ, EXACT, NZLO>(p, g, vp, it.y, t, src, lane, do_mass, acc);
+            __syncwarp();
+            long long c1 = clock64();
+            if (lane == 0) atomicAdd(&p.vp_cycles[it.x], (unsigned long long)(c1 - c0));
+        }
+        if (do_mass && cur_grid >= 0) {
+            double v = acc.take();
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) s_mass[warp * p.ngrids + cur_grid] += v;
+        }
+        if (lane == 0) atomicMax(&s_tend, (unsigned long long)clock64());
+        __syncthreads();
+        if (threadIdx.x == 0 && s_tend > s_t0) p.bin_busy[bin] += s_tend - s_t0;
+        if (do_mass) {
+            for (int gi = threadIdx.x; gi < p.ngrids; gi += THREADS) {
+                double v = 0.0;
+                for (int w = 0; w < kWarps; ++w) v += s_mass[w * p.ngrids + gi];
+                p.bin_mass[((size_t)(s & 1) * p.nbins + bin) * p.ngrids + gi] = v;
+            }
+        }
+        if (!grid_barrier(p.bar, gridDim.x, p.timeout_ns, p.status, &s_flag)) return;
+    }
+
+    // the last step's sums
+    if (bin == 0 && p.nsteps > 0) reduce_mass<TC, THREADS>(p, p.nsteps - 1);
+    if (threadIdx.x == 0) {
+        p.bin_cal[4 * bin + 2] = (long long)globaltimer_ns();
+        p.bin_cal[4 * bin + 3] = clock64();
+    }
+}
+
+template <class TS, class TC, int NZ, bool EXACT, int NZLO, int THREADS>
+inline KernelInfo kernel_entry() {
+    KernelInfo k;
+    k.fn = (const void *)&lb_step_kernel<TS, TC, NZ, EXACT, NZLO, THREADS>;
+    k.threads = THREADS;
+    k.nz_variant = NZ;
+    k.exact = EXACT ? 1 : 0;
+    return k;
+}
+
+}  // namespace lbk

@@ -1,0 +1,84 @@
+"""The application loop of Fig. 2 on top of a Simulation: runs of `period`
+time steps (persistent launches, split where the load array is re-drawn),
+each followed by the load measurement (Sec. V) and a balancer call
+(Sec. VI; "auto" = GreedyLB on the first call, RefineSwapLB afterwards).
+"""
+import numpy as np
+import torch
+
+from . import lb as L
+
+
+class Schedule:
+    """kc_epochs: {epoch: [int32 (ny, nx) per grid]} for array-k_c grids,
+    re-drawn every `epoch_steps` time steps (0: never)."""
+
+    def __init__(self, sim, period, strategy="auto", kc_epochs=None, epoch_steps=0):
+        self.sim = sim
+        self.period = int(period)
+        self.strategy = strategy
+        self.epoch_steps = int(epoch_steps or 0)
+        self.kc_dev = {}
+        if kc_epochs:
+            for e, arrs in kc_epochs.items():
+                self.kc_dev[e] = [None if a is None else
+                                  torch.as_tensor(np.ascontiguousarray(a, dtype=np.int32)).to(sim.device)
+                                  for a in arrs]
+        self.t = 0
+        self.history = []
+        self._epoch_set = None
+
+    def _segments(self, t0, t1):
+        t = t0
+        while t < t1:
+            n = t1 - t
+            e = None
+            if self.epoch_steps:
+                e = t // self.epoch_steps
+                n = min(n, (e + 1) * self.epoch_steps - t)
+            yield t, n, e
+            t += n
+
+    def launches_per_period(self, t0=None):
+        t0 = self.t if t0 is None else t0
+        return sum(1 for _ in self._segments(t0, t0 + self.period))
+
+    def run_steps(self, n):
+        """n time steps without a balancer call."""
+        for t, m, e in self._segments(self.t, self.t + n):
+            if e is not None and e != self._epoch_set and e in self.kc_dev:
+                for gi, d in enumerate(self.kc_dev[e]):
+                    if d is not None:
+                        L.lb_set_kc(self.sim.ctx, gi, d.data_ptr())
+                self._epoch_set = e
+            self.sim.step(m)
+        self.t += n
+
+    def balance(self):
+        """Measure the loads of the steps since the last call and rebalance."""
+        cost, busy = self.sim.measure()
+        used = busy[busy > 0]
+        rec = {"t": self.t,
+               "sm_max_over_mean": float(used.max() / used.mean()) if used.size else None}
+        nprocs = self.sim.info().nprocs
+        mean = float(cost.sum()) / nprocs
+        rec["granularity_floor"] = float(max(cost.max(), mean) / mean) if mean > 0 else None
+        if self.strategy != "static":
+            mig, pred = self.sim.rebalance(self.strategy)
+            rec["migrations"] = mig
+            rec["predicted_max_over_mean"] = pred
+        self.history.append(rec)
+        return rec
+
+    def run_period(self):
+        self.run_steps(self.period)
+        return self.balance()
+
+    def run(self, nsteps):
+        """nsteps time steps with a balancer call after every full period."""
+        end = self.t + nsteps
+        while self.t < end:
+            n = min(self.period, end - self.t)
+            self.run_steps(n)
+            if n == self.period:
+                self.balance()

@@ -1,0 +1,56 @@
+"""Shared helpers of the GPU tests: storage rounding on the CPU, oracle runs
+of a grid description, normwise errors."""
+import numpy as np
+import torch
+
+import oracle
+from oracle import OracleGrid
+
+_TORCH = {"f64": torch.float64, "f32": torch.float32, "bf16": torch.bfloat16}
+
+
+class Grid:
+    """A grid description accepted by Simulation and by the oracle."""
+
+    def __init__(self, nx, ny, nz, cx=0.5, cy=0.5, cz=0.0, r=0.1, storage="f32",
+                 compute="f32", kc_disk=True, disk=(0, 0, 1, 1, 3), k_in=4, k_out=1):
+        self.nx, self.ny, self.nz = nx, ny, nz
+        self.cx, self.cy, self.cz, self.r = cx, cy, cz, r
+        self.storage, self.compute = storage, compute
+        self.kc_disk, self.disk, self.k_in, self.k_out = kc_disk, tuple(disk), k_in, k_out
+
+    def oracle(self, kc=None):
+        return OracleGrid(self.nx, self.ny, self.nz, self.cx, self.cy, self.cz, self.r,
+                          self.kc_disk, self.disk, self.k_in, self.k_out, kc)
+
+
+def round_to_storage(q, storage):
+    """The field as the storage type holds it, back in float64 (CPU rounding)."""
+    t = torch.from_numpy(np.ascontiguousarray(q, dtype=np.float64))
+    if storage == "f32":
+        t = t.to(torch.float32)
+    elif storage == "bf16":
+        t = t.to(torch.float32).to(torch.bfloat16)
+    return t.to(torch.float64).numpy()
+
+
+def tolerance(g, nsteps):
+    """Normwise bound per precision: the FP32 target 1e-5; FP64 compute 1e-12;
+    BF16 storage: one rounding of relative size 2^-9 per stored step, carried
+    through a non-expansive step operator (convex advection, M^-1 with unit
+    row sums and nonnegative entries), so at most nsteps * 2^-9, plus the FP32
+    target."""
+    if g.storage == "bf16":
+        return nsteps * 2.0 ** -9 + 1e-5
+    if g.compute == "f64":
+        return 1e-12
+    return 1e-5
+
+
+def normwise(gpu, ref):
+    return float(np.abs(gpu - ref).max() / max(np.abs(ref).max(), 1e-300))
+
+
+def random_field(g, seed, lo=0.2, hi=1.0):
+    rng = np.random.default_rng(seed)
+    return rng.uniform(lo, hi, size=(g.nz, g.ny, g.nx))

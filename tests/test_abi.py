@@ -1,0 +1,96 @@
+"""The C ABI library: loads, exports every entry point include/lb.h declares,
+and its host balancers reproduce the oracle's assignments bit for bit.
+No test here launches GPU work."""
+import os
+import random
+import re
+
+import numpy as np
+import pytest
+
+from oracle import balance as B
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lbmod():
+    from paper_1310_4218_gb300 import build
+    build.build()
+    from paper_1310_4218_gb300 import lb
+    lb.load_library()
+    return lb
+
+
+def declared_entry_points():
+    src = open(os.path.join(ROOT, "include", "lb.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(lb_[a-z_]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported(lbmod):
+    names = declared_entry_points()
+    assert len(names) >= 19
+    lib = lbmod.load_library()
+    for n in names:
+        assert hasattr(lib, n), n
+    assert sorted(lbmod.EXPORTED) == names
+
+
+def test_plan_experiment_c(lbmod):
+    costs = [2.0] * 8 + [1.0] * 8
+    a, mig, pred = lbmod.lb_plan("greedy", costs, 4)
+    assert mig == 12 and pred == 1.0
+    assert list(a) == B.greedy(costs, 4)
+
+
+@pytest.mark.parametrize("seed", range(25))
+def test_plan_matches_oracle_bitwise(lbmod, seed):
+    rng = random.Random(seed)
+    nb = rng.randint(2, 40)
+    nv = rng.randint(nb, 600)
+    kind = seed % 3
+    if kind == 0:
+        costs = [rng.lognormvariate(0, 1) for _ in range(nv)]
+    elif kind == 1:
+        costs = [float(rng.randint(1, 5)) for _ in range(nv)]     # many ties
+    else:
+        costs = [rng.choice([1.0, 32.0]) * rng.uniform(0.9, 1.1) for _ in range(nv)]
+    g, _, pg = lbmod.lb_plan("greedy", costs, nb)
+    assert list(g) == B.greedy(costs, nb)
+    assert pg == B.max_over_mean(costs, B.greedy(costs, nb), nb)
+    cur = [rng.randrange(nb) for _ in range(nv)]
+    r, mr, pr = lbmod.lb_plan("refine_swap", costs, nb, current=cur, refine_tol=0.05)
+    ro = B.refine_swap(costs, cur, nb, 0.05)
+    assert list(r) == ro
+    assert mr == B.migrations(cur, ro)
+    s, _, _ = lbmod.lb_plan("static", costs, nb)
+    assert list(s) == B.static_blocks(nv, nb)
+
+
+def test_plan_rejects_bad_input(lbmod):
+    with pytest.raises(lbmod.LBError) as e:
+        lbmod.lb_plan("greedy", [1.0, float("nan")], 2)
+    assert e.value.status == lbmod.LB_EINVAL
+    with pytest.raises(lbmod.LBError):
+        lbmod.lb_plan("greedy", [1.0, -2.0], 2)
+    with pytest.raises(lbmod.LBError):
+        lbmod.lb_plan("queue", [1.0, 2.0], 2)
+
+
+def test_create_rejects_invalid_layout_before_touching_the_device(lbmod):
+    """Validation runs first: an overlapping layout is refused with EINVAL."""
+    g = lbmod.lb_grid_desc(8, 8, 4, 0.5, 0.5, 0.0, 0.1, lbmod.LB_F32, lbmod.LB_F32,
+                           0x1000, 0x2000, None, 1, 0, 0, 0, 0, 1, 1, 1)
+    vps = [(0, 0, 0, 8, 8), (0, 0, 0, 1, 1)]
+    with pytest.raises(lbmod.LBError) as e:
+        lbmod.lb_create([g], vps)
+    assert e.value.status == lbmod.LB_EINVAL and "overlap" in str(e.value)
+    with pytest.raises(lbmod.LBError) as e:
+        lbmod.lb_create([g], [(0, 0, 0, 8, 7)])
+    assert "gap" in str(e.value)
+    bad = lbmod.lb_grid_desc(8, 8, 4, 0.7, 0.5, 0.0, 0.1, lbmod.LB_F32, lbmod.LB_F32,
+                             0x1000, 0x2000, None, 1, 0, 0, 0, 0, 1, 1, 1)
+    with pytest.raises(lbmod.LBError) as e:
+        lbmod.lb_create([bad], [(0, 0, 0, 8, 8)])
+    assert "cx" in str(e.value)

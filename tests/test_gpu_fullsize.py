@@ -1,0 +1,139 @@
+"""Parity at the workloads' full sizes, run exactly as the benchmark runs them
+(periods of 10 steps, load measurement, GreedyLB then RefineSwapLB, k_c
+re-drawn every 50 steps), checked on sampled outputs: the oracle computes
+windows of columns whose whole upwind dependence cone (Courant 0.5 along +x
+and +y: one column per step on each axis) lies inside the window."""
+import concurrent.futures as cf
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+import oracle  # noqa: E402
+from gpu_common import normwise, round_to_storage, tolerance  # noqa: E402
+from workloads import get_config  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def run_gpu(w, fields, nsteps, period=10, strategy="auto"):
+    from paper_1310_4218_gb300 import lb
+    from paper_1310_4218_gb300.schedule import Schedule
+    from paper_1310_4218_gb300.sim import Simulation
+    epochs = {}
+    if w.kc_epoch_steps:
+        for e in range((nsteps + w.kc_epoch_steps - 1) // w.kc_epoch_steps):
+            epochs[e] = [w.kc_array(gi, e) for gi in range(len(w.grids))]
+    kc0 = epochs[0] if epochs else None
+    sim = Simulation(w.grids, fields, w.vps, kc_arrays=kc0, options=lb.lb_default_options())
+    sch = Schedule(sim, period, strategy, epochs, w.kc_epoch_steps)
+    sch.run(nsteps)
+    outs = [sim.field(gi) for gi in range(len(w.grids))]
+    hist = [sim.mass_history(gi) for gi in range(len(w.grids))]
+    sim.close()
+    return outs, hist, epochs, sch.history
+
+
+def window_check(w, gi, q0, out, epochs, nsteps, corners, valid=8):
+    """Oracle windows ending at `corners` (lower-left of the valid block)."""
+    g = w.grids[gi]
+    og = oracle.OracleGrid.from_spec(g)
+    side = nsteps + valid
+    jobs = []
+    for (ci, cj) in corners:
+        i0, j0 = ci - nsteps, cj - nsteps
+        kcw = None
+        if not g.kc_disk:
+            ii = np.arange(i0, i0 + side) % g.nx
+            jj = np.arange(j0, j0 + side) % g.ny
+            kcw = np.stack([epochs[t // w.kc_epoch_steps][gi][jj][:, ii] for t in range(nsteps)])
+        jobs.append((i0, j0, kcw))
+
+    def one(job):
+        i0, j0, kcw = job
+        return oracle.run_window(og, q0, i0, j0, side, side, nsteps, kc_window=kcw)
+
+    with cf.ThreadPoolExecutor(max_workers=len(jobs)) as ex:
+        refs = list(ex.map(one, jobs))
+    errs = []
+    scale = 0.0
+    for (i0, j0, _), ref in zip(jobs, refs):
+        r = ref[:, nsteps:, nsteps:]
+        assert np.isfinite(r).all()
+        ii = np.arange(i0 + nsteps, i0 + side) % g.nx
+        jj = np.arange(j0 + nsteps, j0 + side) % g.ny
+        gpu = out[:, jj][:, :, ii]
+        errs.append(float(np.abs(gpu - r).max()))
+        scale = max(scale, float(np.abs(r).max()))
+    return max(errs), scale
+
+
+def test_plain_fp64_full_field():
+    """64x64x32 FP64, static placement, 10 steps: the whole field."""
+    w = get_config("plain_fp64_64x64x32")
+    q0 = w.grids[0].initial_field()
+    outs, hist, _, _ = run_gpu(w, [q0], w.steps, strategy="static")
+    ref, mass = oracle.run(oracle.OracleGrid.from_spec(w.grids[0]), q0, w.steps)
+    assert normwise(outs[0], ref) <= 1e-12
+    assert np.max(np.abs(hist[0] - mass)) <= 1e-12 * abs(mass[0])
+
+
+def test_hotspot_512_fp32_windows():
+    w = get_config("hotspot_fp32_512x512x64")
+    g = w.grids[0]
+    q0 = round_to_storage(g.initial_field(), "f32")
+    outs, hist, _, sched = run_gpu(w, [q0], w.steps)
+    # the disk's final centre (228, 228), its rim, a cold corner, the wrap seam
+    corners = [(224, 224), (280, 230), (60, 400), (508, 3)]
+    err, scale = window_check(w, 0, q0, outs[0], None, w.steps, corners)
+    assert err / scale <= 1e-5, err / scale
+    m0 = oracle.compensated_sum(q0)
+    assert np.max(np.abs(hist[0] - m0)) <= 1e-6 * m0
+    assert sched[0]["migrations"] > 0
+
+
+def test_lognormal_1024_fp32_windows():
+    w = get_config("lognormal_fp32_1024x1024x96")
+    g = w.grids[0]
+    q0 = round_to_storage(g.initial_field(), "f32")
+    outs, hist, epochs, _ = run_gpu(w, [q0], w.steps)
+    kc = epochs[3][0]
+    j, i = np.unravel_index(np.argmax(kc), kc.shape)       # a k_c = 64 hotspot
+    corners = [(int(i) - 4, int(j) - 4), (1020, 1019)]
+    err, scale = window_check(w, 0, q0, outs[0], epochs, w.steps, corners)
+    assert err / scale <= 1e-5, err / scale
+
+
+@pytest.mark.parametrize("storage", ["f32", "f64", "bf16"])
+def test_precision_2048_windows(storage):
+    w = get_config("precision_2048x2048x64", storage=storage)
+    g = w.grids[0]
+    q0 = round_to_storage(g.initial_field(), storage)
+    outs, hist, _, _ = run_gpu(w, [q0], w.steps)
+    corners = [(556, 556), (300, 800), (1500, 1500), (2045, 2046)]
+    err, scale = window_check(w, 0, q0, outs[0], None, w.steps, corners)
+    assert err / scale <= tolerance(g, w.steps), err / scale
+
+
+def test_batch64_windows():
+    w = get_config("batch64_fp32")
+    fields = [round_to_storage(g.initial_field(), "f32") for g in w.grids]
+    outs, _, _, _ = run_gpu(w, fields, w.steps)
+    worst = 0.0
+    for gi, g in enumerate(w.grids[::4]):
+        gi *= 4
+        x0, y0, vx, vy, R = g.disk
+        cx = (x0 + w.steps * vx) % g.nx
+        cy = (y0 + w.steps * vy) % g.ny
+        err, scale = window_check(w, gi, fields[gi], outs[gi], None, w.steps,
+                                  [(cx, cy), (g.nx - 2, g.ny - 3)], valid=4)
+        worst = max(worst, err / scale)
+    assert worst <= 1e-5, worst

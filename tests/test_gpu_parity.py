@@ -1,0 +1,277 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle, on small
+grids that span several work items and ragged VP edges, for every kernel
+variant, strategy and edge case."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import oracle  # noqa: E402
+from gpu_common import Grid, normwise, random_field, round_to_storage, tolerance  # noqa: E402
+from workloads import gaussian_blob, guillotine, regular_blocks  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def make_sim(grids, fields, vps, kc=None, **opt):
+    from paper_1310_4218_gb300 import lb
+    from paper_1310_4218_gb300.sim import Simulation
+    o = lb.lb_default_options()
+    for k, v in opt.items():
+        setattr(o, k, v)
+    return Simulation(grids, fields, vps, kc_arrays=kc, options=o)
+
+
+def oracle_run(g, q, nsteps, t0=0, kc=None):
+    ref, mass = oracle.run(g.oracle(kc), q, nsteps, t0=t0)
+    return ref, mass
+
+
+VARIANTS = [
+    # storage, compute, nz  (exact-nz kernels and runtime-nz kernels)
+    ("f32", "f32", 32), ("f32", "f32", 64), ("f32", "f32", 96),
+    ("f32", "f32", 1), ("f32", "f32", 5), ("f32", "f32", 17), ("f32", "f32", 47),
+    ("f32", "f32", 100), ("f32", "f32", 128),
+    ("f64", "f64", 32), ("f64", "f64", 7), ("f64", "f64", 50),
+    ("f64", "f32", 64), ("f64", "f32", 20), ("f64", "f32", 90),
+    ("bf16", "f32", 64), ("bf16", "f32", 33), ("bf16", "f32", 120),
+]
+
+
+@pytest.mark.parametrize("storage,compute,nz", VARIANTS)
+def test_variant_parity(storage, compute, nz):
+    g = Grid(50, 37, nz, 0.5, 0.5, 0.0, 0.1, storage, compute, True, (40, 30, 1, 1, 9), 7, 1)
+    q = round_to_storage(gaussian_blob(50, 37, nz, (25, 18, nz / 2), 9.0, 1e-3, 3), storage)
+    vps = regular_blocks(50, 37, 16, 8)          # ragged right and top edges
+    sim = make_sim([g], [q], vps)
+    n = 5
+    sim.step(2)
+    sim.step(n - 2)                              # two launches: parity of buffers
+    out = sim.field(0)
+    ref, _ = oracle_run(g, q, n)
+    err = normwise(out, ref)
+    sim.close()
+    assert err <= tolerance(g, n), err
+
+
+@pytest.mark.parametrize("cx,cy,cz", [(0.3, 0.2, 0.1), (-0.4, 0.25, -0.3), (0.2, -0.5, 0.0),
+                                      (-0.1, -0.1, 0.6)])
+def test_general_advection(cx, cy, cz):
+    g = Grid(40, 33, 24, cx, cy, cz, 0.25, "f32", "f32", True, (5, 30, -1, 2, 7), 5, 2)
+    q = round_to_storage(random_field(g, 4), "f32")
+    sim = make_sim([g], [q], regular_blocks(40, 33, 8, 8))
+    sim.step(6)
+    out = sim.field(0)
+    ref, _ = oracle_run(g, q, 6)
+    sim.close()
+    assert normwise(out, ref) <= 1e-5
+
+
+@pytest.mark.parametrize("strategy", ["static", "greedy", "refine_swap", "queue", "auto"])
+def test_strategies_give_identical_fields(strategy):
+    """Balancing changes only where columns run, never their values: every
+    strategy yields the same bits, and they match the oracle."""
+    g = Grid(64, 48, 32, disk=(10, 10, 1, 1, 12), k_in=20, k_out=1)
+    q = round_to_storage(gaussian_blob(64, 48, 32, (32, 24, 16), 10.0, 1e-3, 5), "f32")
+    vps = guillotine(64, 48, 24, 4, 17)
+    sim = make_sim([g], [q], vps, queue_order=1)
+    sim.step(3)
+    sim.measure()
+    sim.rebalance(strategy)
+    sim.step(3)
+    sim.measure()
+    sim.rebalance(strategy)
+    sim.step(2)
+    out = sim.field(0)
+    sim.close()
+    base = make_sim([g], [q], vps)
+    base.step(8)
+    out0 = base.field(0)
+    base.close()
+    assert np.array_equal(out, out0)
+    ref, _ = oracle_run(g, q, 8)
+    assert normwise(out, ref) <= 1e-5
+
+
+def test_exact_shift_is_bitwise():
+    """Courant number 1 along x with r = 0: one step is a periodic roll."""
+    g = Grid(33, 20, 16, 1.0, 0.0, 0.0, 0.0, disk=(3, 3, 0, 0, 5), k_in=9)
+    q = round_to_storage(random_field(g, 6), "f32")
+    sim = make_sim([g], [q], regular_blocks(33, 20, 11, 7))
+    sim.step(3)
+    out = sim.field(0)
+    sim.close()
+    assert np.array_equal(out, np.roll(q, 3, axis=2))
+
+
+def test_zero_kc_is_pure_advection_bitwise_shift():
+    g = Grid(30, 26, 9, 0.0, 1.0, 0.0, 0.3, disk=(3, 3, 0, 0, 5), k_in=0, k_out=0)
+    q = round_to_storage(random_field(g, 7), "f32")
+    sim = make_sim([g], [q], regular_blocks(30, 26, 7, 5))
+    sim.step(2)
+    out = sim.field(0)
+    sim.close()
+    assert np.array_equal(out, np.roll(q, 2, axis=1))
+
+
+@pytest.mark.parametrize("layout", ["single", "columns", "strips"])
+def test_degenerate_layouts(layout):
+    g = Grid(12, 10, 8, disk=(6, 5, 0, 0, 3), k_in=5)
+    q = round_to_storage(random_field(g, 8), "f32")
+    if layout == "single":
+        vps = [(0, 0, 0, 12, 10)]
+    elif layout == "columns":
+        vps = regular_blocks(12, 10, 1, 1)       # one column per VP
+    else:
+        vps = regular_blocks(12, 10, 12, 1)
+    sim = make_sim([g], [q], vps)
+    sim.step(4)
+    out = sim.field(0)
+    sim.close()
+    ref, _ = oracle_run(g, q, 4)
+    assert normwise(out, ref) <= 1e-5
+
+
+def test_kc_array_and_redraw():
+    """Array k_c (Sec. VI-B load array) with a re-draw between segments."""
+    g = Grid(40, 40, 24, kc_disk=False)
+    rng = np.random.default_rng(9)
+    kc1 = rng.integers(0, 12, size=(40, 40)).astype(np.int32)
+    kc2 = rng.integers(0, 12, size=(40, 40)).astype(np.int32)
+    q = round_to_storage(random_field(g, 10), "f32")
+    sim = make_sim([g], [q], regular_blocks(40, 40, 8, 8), kc=[kc1])
+    sim.step(3)
+    sim.set_kc(0, kc2)
+    sim.step(2)
+    out = sim.field(0)
+    sim.close()
+    ref, _ = oracle.run(g.oracle(kc1), q, 3)
+    ref, _ = oracle.run(g.oracle(kc2), ref, 2, t0=3)
+    assert normwise(out, ref) <= 1e-5
+
+
+def test_multi_grid_batch():
+    """Several grids of different size and nz in one persistent launch."""
+    specs = [(70, 70, 40, 5), (64, 64, 33, 9), (100, 100, 96, 3), (65, 65, 32, 12), (90, 90, 71, 2)]
+    grids, fields, vps = [], [], []
+    for gi, (s, _, nz, kin) in enumerate(specs):
+        g = Grid(s, s, nz, disk=(s // 3, s // 2, 1, 1, s // 8), k_in=kin)
+        grids.append(g)
+        fields.append(round_to_storage(gaussian_blob(s, s, nz, (s / 2, s / 2, nz / 2), s / 8,
+                                                     1e-3, 20 + gi), "f32"))
+        vps += regular_blocks(s, s, 32, 32, grid=gi)
+    sim = make_sim(grids, fields, vps)
+    sim.step(3)
+    sim.measure()
+    sim.rebalance("greedy")
+    sim.step(3)
+    outs = [sim.field(gi) for gi in range(len(grids))]
+    sim.close()
+    for gi, g in enumerate(grids):
+        ref, _ = oracle_run(g, fields[gi], 6)
+        assert normwise(outs[gi], ref) <= 1e-5, gi
+
+
+def test_global_sum_matches_field_and_is_conserved():
+    g = Grid(64, 64, 32, disk=(20, 20, 1, 1, 10), k_in=16)
+    q = round_to_storage(gaussian_blob(64, 64, 32, (32, 32, 16), 8.0, 1e-3, 11), "f32")
+    sim = make_sim([g], [q], regular_blocks(64, 64, 16, 16))
+    sim.step(10)
+    hist = sim.mass_history(0)
+    s, _ = sim.mass(0)
+    out = sim.field(0)
+    sim.close()
+    assert len(hist) == 10 and hist[-1] == s
+    exact = oracle.compensated_sum(out)
+    assert abs(s - exact) <= 1e-12 * abs(exact)
+    m0 = oracle.compensated_sum(q)
+    assert abs(s - m0) <= 1e-6 * abs(m0)
+
+
+def test_fp64_mass_is_exactly_conserved_to_roundoff():
+    g = Grid(32, 32, 16, storage="f64", compute="f64", disk=(8, 8, 1, 1, 6), k_in=9)
+    q = random_field(g, 12)
+    sim = make_sim([g], [q], regular_blocks(32, 32, 8, 8))
+    sim.step(10)
+    hist = sim.mass_history(0)
+    sim.close()
+    m0 = oracle.compensated_sum(q)
+    assert np.max(np.abs(hist - m0)) <= 1e-12 * m0
+
+
+def test_checkpoint_resume_is_bitwise(tmp_path):
+    g = Grid(48, 40, 32, disk=(5, 5, 1, 1, 9), k_in=11)
+    q = round_to_storage(gaussian_blob(48, 40, 32, (24, 20, 16), 9.0, 1e-3, 13), "f32")
+    vps = regular_blocks(48, 40, 16, 8)
+    a = make_sim([g], [q], vps)
+    a.step(7)
+    ref = a.field(0)
+    a.close()
+    b = make_sim([g], [q], vps)
+    b.step(4)
+    b.measure()
+    b.rebalance("greedy")
+    path = str(tmp_path / "ck.bin")
+    b.checkpoint(path)
+    b.close()
+    c = make_sim([g], [q], vps)
+    c.restore(path)
+    c.step(3)
+    out = c.field(0)
+    c.close()
+    assert np.array_equal(out, ref)
+
+
+def test_barrier_timeout_is_reported_and_ctx_recovers():
+    """A 1 ns wait limit makes the first barrier wait give up: the kernel
+    records LB_ETIMEOUT and returns; the next synchronising call reports it;
+    the ctx then runs normally."""
+    from paper_1310_4218_gb300 import lb
+    # one VP carries 200 sweeps per column: every other processor reaches the
+    # first barrier long before it and gives up after ~1 us
+    g = Grid(64, 64, 64, disk=(16, 16, 0, 0, 6), k_in=200, k_out=0)
+    q = round_to_storage(random_field(g, 14), "f32")
+    sim = make_sim([g], [q], regular_blocks(64, 64, 32, 32), barrier_timeout_ns=1)
+    sim.step(4)
+    with pytest.raises(lb.LBError) as e:
+        sim.sync()
+    assert e.value.status == lb.LB_ETIMEOUT
+    sim.sync()                     # reported once, then cleared
+    sim.close()
+
+
+def test_measured_costs_follow_kc():
+    """Per-VP device costs rise with the VP's sweep count (Sec. V), and a
+    greedy remap lowers the predicted max/mean processor load."""
+    g = Grid(256, 256, 64, disk=(64, 64, 0, 0, 40), k_in=32, k_out=1)
+    q = round_to_storage(gaussian_blob(256, 256, 64, (128, 128, 32), 32.0, 1e-3, 15), "f32")
+    vps = regular_blocks(256, 256, 32, 32)
+    sim = make_sim([g], [q], vps)
+    sim.step(4)
+    cost, busy = sim.measure()
+    kc = oracle.kc_field(g.oracle(), 0)
+    # a work item is 32 consecutive columns (one per lane) of the VP's
+    # row-major order: it costs a fixed part plus its lanes' largest k_c
+    items, sweeps = [], []
+    for (_, x0, y0, w, h) in vps:
+        flat = kc[y0:y0 + h, x0:x0 + w].ravel()
+        chunks = [flat[c:c + 32] for c in range(0, flat.size, 32)]
+        items.append(len(chunks))
+        sweeps.append(sum(int(c.max()) for c in chunks))
+    X = np.stack([np.array(items, float), np.array(sweeps, float)], axis=1)
+    coef, *_ = np.linalg.lstsq(X, cost, rcond=None)
+    r2 = 1 - np.sum((X @ coef - cost) ** 2) / np.sum((cost - cost.mean()) ** 2)
+    assert np.all(cost > 0)
+    assert coef[1] > 0 and r2 > 0.85, (coef, r2)
+    _, pred = sim.rebalance("greedy")
+    from oracle import balance as B
+    assert pred <= B.max_over_mean(list(cost), B.static_blocks(len(vps), sim.info().nprocs),
+                                   sim.info().nprocs)
+    sim.close()

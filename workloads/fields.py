@@ -9,16 +9,18 @@ def gaussian_blob(nx, ny, nz, center, sigma, noise_amp, seed, dtype=np.float64):
 
     Cell centres sit at integer indices, the blob is not wrapped, and u is the
     uniform draw whose counter is the linear cell index (k*ny + j)*nx + i.
-    Returned in x-fastest layout, shape (nz, ny, nx).
+    Returned in x-fastest layout, shape (nz, ny, nx); built one level at a
+    time so the largest workloads need no full-size temporaries.
     """
     ci, cj, ck = center
     i = np.arange(nx, dtype=np.float64)
     j = np.arange(ny, dtype=np.float64)
-    k = np.arange(nz, dtype=np.float64)
-    r2 = ((k[:, None, None] - ck) ** 2 + (j[None, :, None] - cj) ** 2
-          + (i[None, None, :] - ci) ** 2)
-    q = np.exp(-r2 / (2.0 * sigma * sigma))
-    if noise_amp:
-        idx = np.arange(nx * ny * nz, dtype=np.uint64).reshape(nz, ny, nx)
-        q += noise_amp * (2.0 * uniform01(seed, idx) - 1.0)
-    return q.astype(dtype)
+    rij = (j[:, None] - cj) ** 2 + (i[None, :] - ci) ** 2
+    q = np.empty((nz, ny, nx), dtype=dtype)
+    plane = np.arange(nx * ny, dtype=np.uint64).reshape(ny, nx)
+    for k in range(nz):
+        lev = np.exp(-(rij + (k - ck) ** 2) / (2.0 * sigma * sigma))
+        if noise_amp:
+            lev += noise_amp * (2.0 * uniform01(seed, plane + np.uint64(k * nx * ny)) - 1.0)
+        q[k] = lev
+    return q
