@@ -87,7 +87,7 @@ class OracleGrid:
 
     def _c(self):
         kc = None
-        if not self.kc_disk:
+        if not self.kc_disk and self.kc is not None:    # window runs bring their own
             self._kc_keep = np.ascontiguousarray(self.kc, dtype=np.int32)
             kc = self._kc_keep.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
         x0, y0, vx, vy, R = self.disk
