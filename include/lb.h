@@ -252,6 +252,43 @@ const char *lb_last_error(const lb_ctx *ctx);
    Synchronises the stream first.  NULL is a no-op. */
 void lb_destroy(lb_ctx *ctx);
 
+/*
+ * lb_step_noalloc -- nsteps time steps of one grid without allocating any
+ * memory.  (This entry point has no counterpart in the paper.)
+ *
+ * For callers that cannot call cudaMalloc: programs whose device memory is
+ * owned by another allocator (a framework's caching allocator that has
+ * already reserved the GPU, a fixed-budget pool in an embedded or real-time
+ * service), where a library allocation could fail, fragment the pool, or
+ * synchronise the device at a moment the caller does not control.  lb_create
+ * allocates tables; this call keeps all of the step kernel's tables and
+ * scratch in one fixed device array compiled into the library
+ * (LB_NOALLOC_SCRATCH_BYTES, under 2 MiB), which every GPU that loads the
+ * library holds until the process exits.
+ *
+ * Arguments: grid (host struct; q0 holds the input field, q1 is the other
+ * ping-pong buffer; after the call the result is in q0 when nsteps is even,
+ * in q1 when odd), vps[nvps] (host, grid index 0, must tile the grid),
+ * t0 (global index of the first step: moves the k_c disk), nsteps, the
+ * stream, and mass_out (host, may be NULL): the compensated global sum after
+ * the last step.  VPs are placed statically, contiguous runs per SM, and
+ * every step runs exactly like lb_step's.
+ *
+ * Limits: nvps <= LB_NOALLOC_MAX_VPS, work items (ceil(w*h/32) summed over
+ * VPs) <= LB_NOALLOC_MAX_ITEMS; larger inputs return LB_EINVAL, with the
+ * reason in lb_last_error(NULL).  The call synchronises the stream before
+ * returning.  The first call on a device looks up the array's device
+ * address with that device current; make it before any stream capture.
+ * Every call reuses the same array and clears the parts that must start at
+ * zero; calls whose GPU work overlaps (two streams, two host threads on one
+ * device) race on the array -- serialise them.
+ */
+#define LB_NOALLOC_MAX_VPS 8192
+#define LB_NOALLOC_MAX_ITEMS 65536
+#define LB_NOALLOC_SCRATCH_BYTES (2u * 1024u * 1024u)
+lb_status lb_step_noalloc(const lb_grid_desc *grid, const lb_vp *vps, int32_t nvps, int64_t t0,
+                          int32_t nsteps, void *cuda_stream, double *mass_out);
+
 #ifdef __cplusplus
 }
 #endif

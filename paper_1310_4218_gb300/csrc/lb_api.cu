@@ -71,6 +71,8 @@ static thread_local std::string g_create_err;
                                                               cudaGetErrorString(e_)); \
     } while (0)
 
+void lbk::set_ctxless_error(const char *msg) { g_create_err = msg; }
+
 static lb_status fail(lb_ctx *ctx, lb_status s, const std::string &msg) {
     if (ctx) ctx->err = msg;
     else g_create_err = msg;

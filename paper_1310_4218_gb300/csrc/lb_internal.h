@@ -86,4 +86,7 @@ bool kernels_f64s(int nz_max, int nz_min, bool same, KernelInfo *out);
 bool kernels_bf16(int nz_max, int nz_min, bool same, KernelInfo *out);
 bool kernels_f32_any(int nz_max, int nz_min, KernelInfo *out);
 
+// Text returned by lb_last_error(NULL) (calls without a ctx).
+void set_ctxless_error(const char *msg);
+
 }  // namespace lbk

@@ -85,6 +85,8 @@ _SIG = {
     "lb_get_info": (_I32, [_P, ctypes.POINTER(lb_info)]),
     "lb_last_error": (ctypes.c_char_p, [_P]),
     "lb_destroy": (None, [_P]),
+    "lb_step_noalloc": (_I32, [ctypes.POINTER(lb_grid_desc), ctypes.POINTER(lb_vp), _I32,
+                               ctypes.c_int64, _I32, _P, _P]),
 }
 EXPORTED = tuple(_SIG)
 
@@ -242,3 +244,16 @@ def lb_last_error(ctx=None):
 def lb_destroy(ctx):
     if ctx:
         load_library().lb_destroy(ctx)
+
+
+def lb_step_noalloc(grid, vps, t0, nsteps, stream=0, want_mass=True):
+    """nsteps steps of one grid with no memory allocation in the library (a
+    fixed device array inside liblb.so holds every table); returns the global
+    sum after the last step, or None."""
+    L = load_library()
+    va = (lb_vp * len(vps))(*[lb_vp(*map(int, v)) for v in vps])
+    m = ctypes.c_double(0.0)
+    st = L.lb_step_noalloc(ctypes.byref(grid), va, len(vps), int(t0), int(nsteps),
+                           _P(stream or 0), ctypes.addressof(m) if want_mass else None)
+    _check(st, None)
+    return m.value if want_mass else None
