@@ -44,6 +44,9 @@ def parse():
     ap.add_argument("--strategy", default="auto")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--threads", type=int, default=0, help="threads per processor (0: default)")
+    ap.add_argument("--no-compare", action="store_true",
+                    help="skip the side-by-side runs of the other strategies")
     return ap.parse_args()
 
 
@@ -112,19 +115,6 @@ def kc_epochs(w, nsteps_total):
         return {}
     n = (nsteps_total + w.kc_epoch_steps - 1) // w.kc_epoch_steps
     return {e: [w.kc_array(gi, e) for gi in range(len(w.grids))] for e in range(n)}
-
-
-def sweeps_per_step(w, t, epochs):
-    """Cell-sweep updates of time step t: sum over columns of nz * k_c."""
-    import oracle  # counts only: the k_c rule evaluated for the metric's numerator
-    tot = 0
-    for gi, g in enumerate(w.grids):
-        if g.kc_disk:
-            kc = oracle.kc_field(oracle.OracleGrid.from_spec(g), t)
-        else:
-            kc = epochs[t // w.kc_epoch_steps][gi]
-        tot += int(kc.sum(dtype=np.int64)) * g.nz
-    return tot
 
 
 def roofline_peak():
@@ -215,6 +205,131 @@ def run_reference(args, rank, world):
     print(json.dumps(out), flush=True)
 
 
+class StrategyRun:
+    """One ctx on the workload, driven period by period with one strategy."""
+
+    def __init__(self, w, fields, epochs, kc_dev, args, dev, stream, strategy):
+        from paper_1310_4218_gb300 import lb
+        from paper_1310_4218_gb300.sim import Simulation
+        self.lb, self.w, self.epochs, self.kc_dev = lb, w, epochs, kc_dev
+        self.P, self.strategy, self.dev, self.stream = args.period, strategy, dev, stream
+        opt = lb.lb_default_options()
+        opt.threads_hint = args.threads
+        opt.queue_order = 0
+        kc0 = [epochs[0][gi] for gi in range(len(w.grids))] if epochs else None
+        self.sim = Simulation(w.grids, fields, w.vps, kc_arrays=kc0, options=opt, device=dev,
+                              stream=stream)
+        self.info = self.sim.info()
+        self.t = 0
+        self.stats = {}
+
+    def launches(self, t0, t1):
+        """Time steps t0..t1-1 as persistent launches, split where the k_c
+        array is re-drawn.  Returns the number of launches."""
+        t, n_launch = t0, 0
+        w = self.w
+        while t < t1:
+            n = t1 - t
+            if self.epochs:
+                e = t // w.kc_epoch_steps
+                if t % w.kc_epoch_steps == 0 or t == t0:
+                    for gi in range(len(w.grids)):
+                        self.lb.lb_set_kc(self.sim.ctx, gi, self.kc_dev[e][gi].data_ptr())
+                n = min(n, (e + 1) * w.kc_epoch_steps - t)
+            self.sim.step(n)
+            t += n
+            n_launch += 1
+        return n_launch
+
+    def balance(self, tag):
+        """Load measurement (Sec. V) and the balancer call (Sec. VI)."""
+        cost, busy = self.sim.measure()
+        used = busy[busy > 0]
+        st = {"sm_max_over_mean": float(used.max() / used.mean()) if used.size else None}
+        mean = float(cost.sum()) / self.info.nprocs
+        st["granularity_floor"] = float(max(cost.max(), mean) / mean) if mean > 0 else None
+        if self.strategy != "static":
+            mig, pred = self.sim.rebalance(self.strategy)
+            st["migrations"] = mig
+            st["predicted_max_over_mean"] = pred
+        self.stats[tag] = st
+
+    def warmup(self, nper):
+        import torch
+        for wi in range(nper):
+            self.launches(self.t, self.t + self.P)
+            self.t += self.P
+            self.balance("first" if wi == 0 else "warmup")
+        torch.cuda.synchronize(self.dev)
+
+    def timed(self, nper, sampler=None):
+        """nper periods between CUDA events; returns the measurement."""
+        import torch
+        lb, stream = self.lb, self.stream
+        sw0, cs0 = lb.lb_work_done(self.sim.ctx)
+        torch.cuda.synchronize(self.dev)
+        if sampler:
+            sampler.start()
+            time.sleep(0.3)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        kev = []
+        e0.record(stream)
+        for _ in range(nper):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            nl = self.launches(self.t, self.t + self.P)
+            b.record(stream)
+            kev.append((a, b, nl))
+            self.balance("timed")
+            self.t += self.P
+        e1.record(stream)
+        torch.cuda.synchronize(self.dev)
+        clocks = sampler.stop() if sampler else None
+        sw1, cs1 = lb.lb_work_done(self.sim.ctx)
+        return {"ms": e0.elapsed_time(e1), "sweeps": sw1 - sw0, "cells": cs1 - cs0,
+                "kernel_ms": [a.elapsed_time(b) / n for a, b, n in kev],
+                "launches": sum(n for _, _, n in kev), "clocks": clocks}
+
+    def end_to_end(self, fields, nper):
+        """The same periods through the public API with host buffers: every
+        period copies its input field host -> device (pinned) and its
+        result device -> host inside the timed region."""
+        import torch
+        if not all(g.storage == "f32" for g in self.w.grids):
+            return None
+        lb, sim, stream = self.lb, self.sim, self.stream
+        h_in = [torch.from_numpy(np.ascontiguousarray(f, dtype=np.float32)).pin_memory()
+                for f in fields]
+        h_out = [torch.empty_like(x).pin_memory() for x in h_in]
+        torch.cuda.synchronize(self.dev)
+        s0, _ = lb.lb_work_done(sim.ctx)
+        c0 = torch.cuda.Event(enable_timing=True)
+        c1 = torch.cuda.Event(enable_timing=True)
+        c0.record(stream)
+        for _ in range(nper):
+            with torch.cuda.stream(stream):
+                for gi in range(len(self.w.grids)):
+                    sim.field_tensor(gi).view(-1).copy_(h_in[gi].view(-1), non_blocking=True)
+            self.launches(self.t, self.t + self.P)
+            self.balance("e2e")
+            self.t += self.P
+            with torch.cuda.stream(stream):
+                for gi in range(len(self.w.grids)):
+                    h_out[gi].view(-1).copy_(sim.field_tensor(gi).view(-1), non_blocking=True)
+        c1.record(stream)
+        torch.cuda.synchronize(self.dev)
+        es = c0.elapsed_time(c1) / 1000.0
+        sw = lb.lb_work_done(sim.ctx)[0] - s0
+        nbytes = sum(x.numel() * x.element_size() for x in h_in)
+        return {"value": sw / es, "unit": "cell-sweep updates/s",
+                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
+
+    def close(self):
+        self.sim.close()
+
+
 def main():
     args = parse()
     rank, local_rank, world = dist_env()
@@ -225,8 +340,6 @@ def main():
     import torch
     import torch.distributed as dist
 
-    from paper_1310_4218_gb300 import lb
-    from paper_1310_4218_gb300.sim import Simulation
     from workloads import get_config
 
     torch.cuda.set_device(local_rank)
@@ -239,149 +352,57 @@ def main():
     total_steps = (args.warmup + 2 * args.steps) * P     # warm-up, timed, end to end
     epochs = kc_epochs(w, total_steps)
     fields = [g.initial_field() for g in w.grids]
-    kc0 = [epochs[0][gi] for gi in range(len(w.grids))] if epochs else None
+    kc_dev = {e: [torch.as_tensor(a).to(dev) for a in arrs] for e, arrs in epochs.items()}
     stream = torch.cuda.Stream(dev)
-    opt = lb.lb_default_options()
-    sim = Simulation(w.grids, fields, w.vps, kc_arrays=kc0, options=opt, device=dev, stream=stream)
-    info = sim.info()
-    kc_dev = {}
-    if epochs:
-        for e, arrs in epochs.items():
-            kc_dev[e] = [torch.as_tensor(a).to(dev) for a in arrs]
 
-    def launches(t0, t1):
-        """Time steps t0..t1-1 as persistent launches, split where the k_c
-        array is re-drawn."""
-        t = t0
-        while t < t1:
-            n = t1 - t
-            if epochs:
-                e = t // w.kc_epoch_steps
-                if t % w.kc_epoch_steps == 0 or t == t0:
-                    for gi in range(len(w.grids)):
-                        lb.lb_set_kc(sim.ctx, gi, kc_dev[e][gi].data_ptr())
-                n = min(n, (e + 1) * w.kc_epoch_steps - t)
-            sim.step(n)
-            t += n
-        return t
-
-    stats = {}
-
-    def balance(tag):
-        """Load measurement (Sec. V) and the balancer call (Sec. VI)."""
-        cost, busy = sim.measure()
-        used = busy[busy > 0]
-        st = {"sm_max_over_mean": float(used.max() / used.mean()) if used.size else None}
-        tot = float(cost.sum())
-        mean = tot / info.nprocs
-        st["granularity_floor"] = float(max(cost.max(), mean) / mean) if mean > 0 else None
-        if args.strategy != "static":
-            mig, pred = sim.rebalance(args.strategy)
-            st["migrations"] = mig
-            st["predicted_max_over_mean"] = pred
-        stats[tag] = st
-
-    # warm-up; the first period runs under the static placement
-    t = 0
-    for wi in range(args.warmup):
-        t = launches(t, t + P)
-        balance("static" if wi == 0 else "warmup")
-    torch.cuda.synchronize(dev)
-    sweeps = sum(sweeps_per_step(w, s, epochs) for s in range(t, t + args.steps * P))
-    cells = w.cells * args.steps * P
-
-    # timed region: device-resident inputs
-    kev = []
-    sampler = ClockSampler(local_rank)
+    # the headline strategy: device-resident inputs, clocks sampled
+    run = StrategyRun(w, fields, epochs, kc_dev, args, dev, stream, args.strategy)
+    info = run.info
+    run.warmup(args.warmup)
     if world > 1:
         dist.barrier()
-    torch.cuda.synchronize(dev)
-    sampler.start()
-    time.sleep(0.3)
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        n_launch = 0
-        tt = t
-        while tt < t + P:      # count launches of this period
-            n = t + P - tt
-            if epochs:
-                e = tt // w.kc_epoch_steps
-                n = min(n, (e + 1) * w.kc_epoch_steps - tt)
-            tt += n
-            n_launch += 1
-        launches(t, t + P)
-        b.record(stream)
-        kev.append((a, b, n_launch))
-        balance("timed")
-        t = t + P
-    e1.record(stream)
-    torch.cuda.synchronize(dev)
-    clocks = sampler.stop()
-    ms = e0.elapsed_time(e1)
-    kernel_ms = [a.elapsed_time(b) / n for a, b, n in kev]
-    n_launches = sum(n for _, _, n in kev)
+    m = run.timed(args.steps, ClockSampler(local_rank))
+    ms = m["ms"]
     if world > 1:
         tm = torch.tensor([ms], device=dev)
         dist.all_reduce(tm, op=dist.ReduceOp.MAX)
         ms = float(tm.item())
     s = ms / 1000.0
-    value = sweeps * world / s
+    value = m["sweeps"] * world / s
 
     g0 = w.grids[0]
-    steps_per_launch = args.steps * P / n_launches
+    steps_per_launch = args.steps * P / m["launches"]
     bytes_per_step = 2 * w.cells * SIZEOF[g0.storage] + \
         4 * sum(g.nx * g.ny for g in w.grids if not g.kc_disk)
     bytes_per_launch = bytes_per_step * steps_per_launch
-    kern_s = statistics.median(kernel_ms) / 1000.0
+    kern_s = statistics.median(m["kernel_ms"]) / 1000.0
     peak, peak_src = roofline_peak()
     achieved = bytes_per_launch / kern_s / 1e9
-    tag = "lb_step_kernel:%s" % w.name
-    tr = load_traffic(tag)
-
-    # end to end through the public API with host buffers
-    def end_to_end():
-        """The same periods through the public API with host buffers: every
-        period copies its input field host -> device (pinned) and its
-        result device -> host inside the timed region."""
-        if not all(g.storage == "f32" for g in w.grids):
-            return None
-        h_in = [torch.from_numpy(np.ascontiguousarray(f, dtype=np.float32)).pin_memory()
-                for f in fields]
-        h_out = [torch.empty_like(x).pin_memory() for x in h_in]
-        torch.cuda.synchronize(dev)
-        c0 = torch.cuda.Event(enable_timing=True)
-        c1 = torch.cuda.Event(enable_timing=True)
-        c0.record(stream)
-        t_e = t
-        for _ in range(args.steps):
-            with torch.cuda.stream(stream):
-                for gi in range(len(w.grids)):
-                    sim.field_tensor(gi).view(-1).copy_(h_in[gi].view(-1), non_blocking=True)
-            launches(t_e, t_e + P)
-            balance("e2e")
-            with torch.cuda.stream(stream):
-                for gi in range(len(w.grids)):
-                    h_out[gi].view(-1).copy_(sim.field_tensor(gi).view(-1), non_blocking=True)
-            t_e += P
-        c1.record(stream)
-        torch.cuda.synchronize(dev)
-        es = c0.elapsed_time(c1) / 1000.0
-        sw = sum(sweeps_per_step(w, s2, epochs) for s2 in range(t, t + args.steps * P))
-        nbytes = sum(x.numel() * x.element_size() for x in h_in)
-        return {"value": sw * world / es, "unit": "cell-sweep updates/s",
-                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
+    tr = load_traffic("lb_step_kernel:%s" % w.name)
 
     e2e = None
     if not args.no_e2e:
         try:
-            e2e = end_to_end()
+            e2e = run.end_to_end(fields, args.steps)
+            if e2e:
+                e2e["value"] *= world
         except Exception as ex:    # report, keep the device-timed line
             e2e = {"value": None, "unit": "cell-sweep updates/s", "error": repr(ex)[:200]}
+    stats = run.stats
+    run.close()
+
+    # the other assignments, measured the same way (device-resident inputs)
+    compare = {}
+    if not args.no_compare:
+        for st in [x for x in ("static", "auto", "queue", "auto_spatial") if x != args.strategy]:
+            r2 = StrategyRun(w, fields, epochs, kc_dev, args, dev, stream, st)
+            r2.warmup(args.warmup)
+            m2 = r2.timed(args.steps)
+            compare[st] = {"value": m2["sweeps"] / (m2["ms"] / 1000.0),
+                           "kernel_ms_per_launch": statistics.median(m2["kernel_ms"]),
+                           "sm_max_over_mean": r2.stats["timed"]["sm_max_over_mean"],
+                           "first_period_sm_max_over_mean": r2.stats["first"]["sm_max_over_mean"]}
+            r2.close()
 
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -398,9 +419,10 @@ def main():
             "data": "synthetic",
             "config": {"workload": w.name, "global_batch": len(w.grids), "period_steps": P,
                        "time_steps_per_step": P, "vps": len(w.vps), "cells": w.cells,
-                       "strategy": args.strategy, "parallelism": "replicas" if world > 1 else "1gpu",
+                       "strategy": args.strategy,
+                       "parallelism": "replicas" if world > 1 else "1gpu",
                        "l2": "fields larger than L2 (no flush)",
-                       "cell_steps_per_s": cells * world / s,
+                       "cell_steps_per_s": m["cells"] * world / s,
                        "processors": info.nprocs, "threads_per_cta": info.threads_per_cta},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_source": peak_src,
@@ -410,13 +432,13 @@ def main():
                          "steps_per_launch": steps_per_launch,
                          "algorithmic_bytes_per_launch": bytes_per_launch},
             "imbalance": stats,
-            "clocks": clocks,
-            "gpu_launches": n_launches,
+            "strategies": compare,
+            "clocks": m["clocks"],
+            "gpu_launches": m["launches"],
             "e2e": e2e,
             "cpu_baseline": cpu,
         }
         print(json.dumps(out), flush=True)
-    sim.close()
     if world > 1:
         dist.destroy_process_group()
 

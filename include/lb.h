@@ -74,13 +74,23 @@ typedef enum { LB_F64 = 0, LB_F32 = 1, LB_BF16 = 2 } lb_dtype;
  *                   every step (the dynamic task-queue scheme of Sec. II)
  *   LB_AUTO         GreedyLB on the first rebalance of a ctx, RefineSwapLB
  *                   afterwards -- the schedule the paper recommends (Sec. VII)
+ *   LB_GREEDY_SPATIAL GreedyLB's rule (each VP to the least-loaded
+ *                   processor) with the VPs taken in spatial order (grid,
+ *                   y0, x0) instead of heaviest first.  Every processor
+ *                   visits its VPs in that order, so the whole GPU sweeps
+ *                   the grids together and neighbouring VPs' halo data is
+ *                   still in L2 when it is needed.
+ *   LB_AUTO_SPATIAL LB_GREEDY_SPATIAL on the first rebalance, RefineSwapLB
+ *                   afterwards
  */
 typedef enum {
     LB_STATIC = 0,
     LB_GREEDY = 1,
     LB_REFINE_SWAP = 2,
     LB_ATOMIC_QUEUE = 3,
-    LB_AUTO = 4
+    LB_AUTO = 4,
+    LB_GREEDY_SPATIAL = 5,
+    LB_AUTO_SPATIAL = 6
 } lb_strategy;
 
 /*
@@ -122,7 +132,9 @@ typedef struct {
                                      per-VP cost average (default 0.5) */
     double refine_tol;            /* RefineSwapLB tolerance (default 0.05) */
     int64_t barrier_timeout_ns;   /* grid-barrier wait limit (default 2 s) */
-    int32_t reserved[8];          /* must be 0 */
+    int32_t threads_hint;         /* threads per processor for kernels that
+                                     have several variants (0: default) */
+    int32_t reserved[7];          /* must be 0 */
 } lb_options;
 
 /* Fill *opt with the defaults listed above. */
@@ -175,7 +187,8 @@ lb_status lb_rebalance(lb_ctx *ctx, int32_t strategy, int32_t *migrations,
 
 /*
  * Host-only planning with the library's balancers (no ctx, no GPU): the
- * assignment `strategy` (LB_STATIC, LB_GREEDY or LB_REFINE_SWAP) produces for
+ * assignment `strategy` (LB_STATIC, LB_GREEDY, LB_REFINE_SWAP or
+ * LB_GREEDY_SPATIAL, which here takes the VPs in id order) produces for
  * FP64 costs[nvps] on nprocs processors.  current[nvps] is the present
  * assignment (needed by LB_REFINE_SWAP and for counting migrations; may be
  * NULL, meaning the static placement).  out[nvps] receives the assignment;
@@ -212,6 +225,12 @@ lb_status lb_mass(lb_ctx *ctx, int32_t grid, double *sum, double *comp);
    (oldest first, up to max entries, at most 1024 kept); synchronises. */
 lb_status lb_mass_history(lb_ctx *ctx, int32_t grid, double *sums, int32_t max,
                           int32_t *n);
+
+/* Work done since lb_create, counted on the device (synchronises):
+   cell_sweeps = sum over steps and columns of nz * k_c (the implicit-solve
+   row updates actually performed); cell_steps = sum over steps of the cells
+   advanced.  Either pointer may be NULL. */
+lb_status lb_work_done(lb_ctx *ctx, int64_t *cell_sweeps, int64_t *cell_steps);
 
 /* Device pointer of the buffer holding grid `grid`'s latest field. */
 lb_status lb_current_field(lb_ctx *ctx, int32_t grid, void **dev_ptr);

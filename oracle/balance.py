@@ -14,6 +14,9 @@ order reproduces these assignments bit for bit.
   refine_swap    -- RefineSwapLB (Sec. VI-B): moves objects off the most
                     overloaded processor toward the average, and swaps
                     objects when no single move fits.
+  greedy_ordered -- GreedyLB's rule (each object to the least loaded
+                    processor) with the objects taken in a given order
+                    instead of heaviest first: Graham's list scheduling.
 """
 import heapq
 
@@ -59,6 +62,19 @@ def greedy(costs, nbins):
     return assign
 
 
+def greedy_ordered(costs, nbins, order):
+    """Objects in the given order (a permutation of VP ids), each to the bin
+    with the least load so far (ties: lowest bin id)."""
+    heap = [(0.0, b) for b in range(nbins)]
+    heapq.heapify(heap)
+    assign = [0] * len(costs)
+    for v in order:
+        load, b = heapq.heappop(heap)
+        assign[v] = b
+        heapq.heappush(heap, (load + costs[v], b))
+    return assign
+
+
 def refine_swap(costs, assign, nbins, tol=0.05, max_iter=None):
     """RefineSwapLB, as read here (the paper gives no constants):
 
@@ -73,11 +89,11 @@ def refine_swap(costs, assign, nbins, tol=0.05, max_iter=None):
          b. swap: among pairs (o in P, o' in Q) with cost(o) > cost(o'),
             visited in o-order (cost desc, id asc) then o'-order
             (cost asc, id asc), the first pair that minimises
-            max(load(P) - c_o + c_o', load(Q) + c_o - c_o'); if that value is
-            below load(P), swap the two and go to 1.
+            max(load(P) - d, load(Q) + d) with d = c_o - c_o'; if that value
+            is below load(P), swap the two and go to 1.
       4. If no bin Q allowed a move or a swap, stop.
-    Loads are kept incrementally: load -= c for the source, load += c for
-    the target, in that order.
+    Loads are kept incrementally: the source's load minus c (a move) or
+    minus d (a swap), then the target's load plus the same amount.
     Returns the new assignment (a copy).
     """
     nv = len(costs)

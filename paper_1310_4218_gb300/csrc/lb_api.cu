@@ -45,6 +45,9 @@ struct lb_ctx {
     double *d_mass_hist = nullptr;
     long long *d_mass_t = nullptr;
     unsigned long long *d_mass_seq = nullptr;
+    unsigned long long *d_sweeps = nullptr;
+    long long cells = 0;               // cells of all grids
+    long long cell_steps = 0;
 
     std::vector<GridDev> h_grids;
     std::vector<int> assign;           // VP -> processor (static-type strategies)
@@ -132,6 +135,20 @@ static lb_status check_status(lb_ctx *ctx) {
     return LB_OK;
 }
 
+// VP ids in spatial order: grid, then row, then column (then id).
+static std::vector<int> spatial_order(const lb_ctx *ctx) {
+    std::vector<int> order(ctx->vps.size());
+    for (size_t v = 0; v < order.size(); ++v) order[v] = (int)v;
+    std::sort(order.begin(), order.end(), [&](int a, int b) {
+        const lb_vp &A = ctx->vps[a], &B = ctx->vps[b];
+        if (A.grid != B.grid) return A.grid < B.grid;
+        if (A.y0 != B.y0) return A.y0 < B.y0;
+        if (A.x0 != B.x0) return A.x0 < B.x0;
+        return a < b;
+    });
+    return order;
+}
+
 // Work items {vp, chunk} for the processor tables and the queue.
 static lb_status upload_items(lb_ctx *ctx) {
     const int nv = (int)ctx->vps.size();
@@ -140,6 +157,18 @@ static lb_status upload_items(lb_ctx *ctx) {
     std::vector<int32_t> start(ctx->nbins + 1, 0);
     std::vector<std::vector<int>> per(ctx->nbins);
     for (int v = 0; v < nv; ++v) per[ctx->assign[v]].push_back(v);
+    // each processor visits its VPs in spatial order (grid, row, column): all
+    // processors then sweep the grids in the same direction at about the
+    // same pace, so the halo and boundary sectors a VP shares with its
+    // neighbours are still in L2 when the neighbour needs them
+    for (auto &lst : per)
+        std::sort(lst.begin(), lst.end(), [&](int a, int b) {
+            const lb_vp &A = ctx->vps[a], &B = ctx->vps[b];
+            if (A.grid != B.grid) return A.grid < B.grid;
+            if (A.y0 != B.y0) return A.y0 < B.y0;
+            if (A.x0 != B.x0) return A.x0 < B.x0;
+            return a < b;
+        });
     for (int b = 0; b < ctx->nbins; ++b) {
         start[b] = (int32_t)items.size();
         for (int v : per[b])
@@ -171,7 +200,8 @@ static void free_ctx(lb_ctx *ctx) {
     void *ptrs[] = {ctx->d_grids,     ctx->d_vps,      ctx->d_items,     ctx->d_qitems,
                     ctx->d_bin_start, ctx->d_bar,      ctx->d_status,    ctx->d_qhead,
                     ctx->d_vp_cycles, ctx->d_bin_busy, ctx->d_bin_smid,  ctx->d_bin_cal,
-                    ctx->d_bin_mass,  ctx->d_mass_hist, ctx->d_mass_t,   ctx->d_mass_seq};
+                    ctx->d_bin_mass,  ctx->d_mass_hist, ctx->d_mass_t,   ctx->d_mass_seq,
+                    ctx->d_sweeps};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete ctx;
@@ -286,7 +316,8 @@ extern "C" lb_status lb_create(const lb_grid_desc *grids, int32_t ngrids, const 
         nzmax = std::max(nzmax, d.nz);
         nzmin = std::min(nzmin, d.nz);
     }
-    if (!find_step_kernel(ctx->storage, ctx->compute, nzmax, nzmin, nzmax == nzmin, &ctx->kinfo)) {
+    if (!find_step_kernel(ctx->storage, ctx->compute, nzmax, nzmin, nzmax == nzmin, &ctx->kinfo,
+                          ctx->opt.threads_hint)) {
         ctx->err = "no kernel variant for these grids";
         return bail(LB_EINVAL);
     }
@@ -328,6 +359,7 @@ extern "C" lb_status lb_create(const lb_grid_desc *grids, int32_t ngrids, const 
         ctx->coef_f.rm[k] = (float)(r * m[k]);
     }
     ctx->h_grids.resize(ngrids);
+    for (int g = 0; g < ngrids; ++g) ctx->cells += (long long)grids[g].nx * grids[g].ny * grids[g].nz;
     for (int g = 0; g < ngrids; ++g) {
         const lb_grid_desc &d = grids[g];
         GridDev &h = ctx->h_grids[g];
@@ -395,6 +427,7 @@ extern "C" lb_status lb_create(const lb_grid_desc *grids, int32_t ngrids, const 
     if (e == cudaSuccess) e = dalloc(&ctx->d_mass_hist, (size_t)kMassHist * ngrids * 2);
     if (e == cudaSuccess) e = dalloc(&ctx->d_mass_t, kMassHist);
     if (e == cudaSuccess) e = dalloc(&ctx->d_mass_seq, 1);
+    if (e == cudaSuccess) e = dalloc(&ctx->d_sweeps, 1);
     cudaStream_t sm = ctx->stream;
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(ctx->d_grids, ctx->h_grids.data(), sizeof(GridDev) * ngrids,
@@ -405,6 +438,7 @@ extern "C" lb_status lb_create(const lb_grid_desc *grids, int32_t ngrids, const 
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_vp_cycles, 0, sizeof(unsigned long long) * nvps, sm);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_bin_busy, 0, sizeof(unsigned long long) * nb, sm);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_mass_seq, 0, sizeof(unsigned long long), sm);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_sweeps, 0, sizeof(unsigned long long), sm);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_bin_cal, 0, sizeof(long long) * 4 * nb, sm);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_bin_smid, 0xff, sizeof(int32_t) * nb, sm);
     if (e == cudaSuccess) e = cudaStreamSynchronize(sm);
@@ -448,6 +482,7 @@ static lb_status launch(lb_ctx *ctx, int nsteps, const Coef<TC> &coef) {
     p.mass_hist = ctx->d_mass_hist;
     p.mass_t = ctx->d_mass_t;
     p.mass_seq = ctx->d_mass_seq;
+    p.sweeps = ctx->d_sweeps;
     p.coef = coef;
 
     CK(cudaMemsetAsync(ctx->d_bar, 0, 2 * sizeof(unsigned), ctx->stream));
@@ -476,6 +511,7 @@ extern "C" lb_status lb_step(lb_ctx *ctx, int32_t nsteps) {
                                           : launch<float>(ctx, nsteps, ctx->coef_f);
     if (st != LB_OK) return st;
     ctx->step += nsteps;
+    ctx->cell_steps += ctx->cells * nsteps;
     ctx->parity ^= (nsteps & 1);
     ctx->steps_since_measure += nsteps;
     return LB_OK;
@@ -562,7 +598,13 @@ extern "C" lb_status lb_plan(int32_t strategy, const double *costs, int32_t nvps
     if (strategy == LB_STATIC) static_blocks(nvps, nprocs, res);
     else if (strategy == LB_GREEDY) greedy(c, nprocs, res);
     else if (strategy == LB_REFINE_SWAP) refine_swap(c, cur, nprocs, refine_tol, res);
-    else return fail(nullptr, LB_EINVAL, "lb_plan: strategy must be STATIC, GREEDY or REFINE_SWAP");
+    else if (strategy == LB_GREEDY_SPATIAL) {
+        std::vector<int> order(nvps);
+        for (int v = 0; v < nvps; ++v) order[v] = v;
+        greedy_ordered(c, nprocs, order, res);
+    } else
+        return fail(nullptr, LB_EINVAL,
+                    "lb_plan: strategy must be STATIC, GREEDY, REFINE_SWAP or GREEDY_SPATIAL");
     for (int v = 0; v < nvps; ++v) out[v] = res[v];
     if (mig) *mig = migrations(cur, res);
     if (pred) *pred = max_over_mean(c, res, nprocs);
@@ -580,10 +622,13 @@ extern "C" lb_status lb_set_costs(lb_ctx *ctx, const double *costs) {
 
 extern "C" lb_status lb_rebalance(lb_ctx *ctx, int32_t strategy, int32_t *mig, double *pred) {
     if (!ctx) return fail(nullptr, LB_EINVAL, "ctx is NULL");
-    if (strategy < LB_STATIC || strategy > LB_AUTO) return fail(ctx, LB_EINVAL, "unknown strategy");
+    if (strategy < LB_STATIC || strategy > LB_AUTO_SPATIAL) return fail(ctx, LB_EINVAL, "unknown strategy");
     if (strategy == LB_AUTO) strategy = ctx->rebalances == 0 ? LB_GREEDY : LB_REFINE_SWAP;
+    if (strategy == LB_AUTO_SPATIAL)
+        strategy = ctx->rebalances == 0 ? LB_GREEDY_SPATIAL : LB_REFINE_SWAP;
     const int nv = (int)ctx->vps.size();
-    if ((strategy == LB_GREEDY || strategy == LB_REFINE_SWAP) && !ctx->have_costs)
+    if ((strategy == LB_GREEDY || strategy == LB_REFINE_SWAP || strategy == LB_GREEDY_SPATIAL) &&
+        !ctx->have_costs)
         return fail(ctx, LB_ESTATE, "no measured costs yet");
     std::vector<int> res;
     int m = 0;
@@ -601,6 +646,7 @@ extern "C" lb_status lb_rebalance(lb_ctx *ctx, int32_t strategy, int32_t *mig, d
     } else {
         if (strategy == LB_STATIC) static_blocks(nv, ctx->nbins, res);
         else if (strategy == LB_GREEDY) greedy(ctx->cost, ctx->nbins, res);
+        else if (strategy == LB_GREEDY_SPATIAL) greedy_ordered(ctx->cost, ctx->nbins, spatial_order(ctx), res);
         else refine_swap(ctx->cost, ctx->assign, ctx->nbins, ctx->opt.refine_tol, res);
         m = migrations(ctx->assign, res);
         pr = ctx->have_costs ? max_over_mean(ctx->cost, res, ctx->nbins) : 1.0;
@@ -646,6 +692,18 @@ extern "C" lb_status lb_set_kc(lb_ctx *ctx, int32_t grid, const int32_t *dev_kc)
     CK(cudaMemcpyAsync(&ctx->d_grids[grid], &ctx->h_grids[grid], sizeof(GridDev),
                        cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
+    return LB_OK;
+}
+
+extern "C" lb_status lb_work_done(lb_ctx *ctx, int64_t *cell_sweeps, int64_t *cell_steps) {
+    if (!ctx) return fail(nullptr, LB_EINVAL, "ctx is NULL");
+    lb_status st = check_status(ctx);
+    if (st != LB_OK) return st;
+    unsigned long long n = 0;
+    CK(cudaMemcpyAsync(&n, ctx->d_sweeps, sizeof(n), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (cell_sweeps) *cell_sweeps = (int64_t)n;
+    if (cell_steps) *cell_steps = ctx->cell_steps;
     return LB_OK;
 }
 
@@ -839,8 +897,10 @@ extern "C" void lb_destroy(lb_ctx *ctx) {
 }
 
 namespace lbk {
-bool find_step_kernel(int storage, int compute, int nz_max, int nz_min, bool same, KernelInfo *out) {
-    if (storage == LB_F32 && compute == LB_F32) return kernels_f32(nz_max, nz_min, same, out);
+bool find_step_kernel(int storage, int compute, int nz_max, int nz_min, bool same, KernelInfo *out,
+                      int threads_hint) {
+    if (storage == LB_F32 && compute == LB_F32)
+        return kernels_f32(nz_max, nz_min, same, threads_hint, out);
     if (storage == LB_F64 && compute == LB_F64) return kernels_f64(nz_max, nz_min, same, out);
     if (storage == LB_F64 && compute == LB_F32) return kernels_f64s(nz_max, nz_min, same, out);
     if (storage == LB_BF16 && compute == LB_F32) return kernels_bf16(nz_max, nz_min, same, out);

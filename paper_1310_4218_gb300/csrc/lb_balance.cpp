@@ -62,6 +62,24 @@ void greedy(const std::vector<double> &costs, int nbins, std::vector<int> &out) 
     }
 }
 
+// GreedyLB's rule with the objects in a caller-given order (Graham's list
+// scheduling).  With the VPs in spatial order and every processor visiting
+// its VPs in that order, all processors sweep the grid in step: the order
+// the GPU's L2 needs.
+void greedy_ordered(const std::vector<double> &costs, int nbins, const std::vector<int> &order,
+                    std::vector<int> &out) {
+    typedef std::pair<double, int> Item;
+    std::priority_queue<Item, std::vector<Item>, std::greater<Item>> heap;
+    for (int b = 0; b < nbins; ++b) heap.push(Item(0.0, b));
+    out.assign(costs.size(), 0);
+    for (int v : order) {
+        Item top = heap.top();
+        heap.pop();
+        out[v] = top.second;
+        heap.push(Item(top.first + costs[v], top.second));
+    }
+}
+
 // RefineSwapLB (Sec. VI-B): move objects off the most loaded processor
 // toward the mean; swap when no single move fits.  The paper gives no
 // constants; the reading implemented:

@@ -11,6 +11,8 @@ void bin_loads(const std::vector<double> &costs, const std::vector<int> &assign,
 double max_over_mean(const std::vector<double> &costs, const std::vector<int> &assign, int nbins);
 int migrations(const std::vector<int> &a, const std::vector<int> &b);
 void greedy(const std::vector<double> &costs, int nbins, std::vector<int> &out);
+void greedy_ordered(const std::vector<double> &costs, int nbins, const std::vector<int> &order,
+                    std::vector<int> &out);
 void refine_swap(const std::vector<double> &costs, const std::vector<int> &assign_in, int nbins,
                  double tol, std::vector<int> &assign);
 

@@ -65,6 +65,7 @@ struct StepParams {
     double *mass_hist;             // [kMassHist][ngrids][2] (sum, comp)
     long long *mass_t;             // [kMassHist] step index of each entry
     unsigned long long *mass_seq;  // number of entries written so far
+    unsigned long long *sweeps;    // cell-sweep updates performed (may be null)
     Coef<TC> coef;
 };
 
@@ -77,10 +78,10 @@ struct KernelInfo {
     int exact;
 };
 bool find_step_kernel(int storage, int compute, int nz_max, int nz_min, bool all_same_nz,
-                      KernelInfo *out);
+                      KernelInfo *out, int threads_hint = 0);
 
 // Per-type kernel tables (one translation unit each, compiled in parallel).
-bool kernels_f32(int nz_max, int nz_min, bool same, KernelInfo *out);
+bool kernels_f32(int nz_max, int nz_min, bool same, int threads_hint, KernelInfo *out);
 bool kernels_f64(int nz_max, int nz_min, bool same, KernelInfo *out);
 bool kernels_f64s(int nz_max, int nz_min, bool same, KernelInfo *out);
 bool kernels_bf16(int nz_max, int nz_min, bool same, KernelInfo *out);

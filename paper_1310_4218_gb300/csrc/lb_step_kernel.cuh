@@ -197,9 +197,9 @@ __device__ __forceinline__ ColGeom col_geom(const GridDev &g, const VPDev &vp, i
 
 // Advection and the k_c solves: leaves the new column in y, minus cref.
 template <class TS, class TC, int NZ, bool EXACT, int NZLO>
-__device__ __forceinline__ void column_physics(const StepParams<TC> &p, const GridDev &g,
-                                               const ColGeom &cg, long long t, int src,
-                                               TC (&y)[NZ], TC &cref) {
+__device__ __forceinline__ int column_physics(const StepParams<TC> &p, const GridDev &g,
+                                              const ColGeom &cg, long long t, int src,
+                                              TC (&y)[NZ], TC &cref) {
     const int nz = EXACT ? NZ : g.nz;
     const TS *in = static_cast<const TS *>(g.q[src]);
     const int plane = g.plane;
@@ -254,6 +254,7 @@ __device__ __forceinline__ void column_physics(const StepParams<TC> &p, const Gr
         const TC rl = EXACT ? TC(0) : rlast<TC>(g);
         for (int s = 0; s < kc; ++s) thomas_solve<TC, NZ, EXACT, NZLO>(y, p.coef, nz, ml, rl);
     }
+    return kc;
 }
 
 // 4. shift back, store, compensated sum of the stored values.
@@ -275,16 +276,18 @@ __device__ __forceinline__ void store_column(const GridDev &g, const ColGeom &cg
     if (MASS) acc.col_end();
 }
 
+// Returns the lane's k_c (0 for lanes past the VP's last column).
 template <class TS, class TC, int NZ, bool EXACT, int NZLO>
-__device__ __forceinline__ void process_item(const StepParams<TC> &p, const GridDev &g,
-                                             const VPDev &vp, int chunk, long long t, int src,
-                                             int lane, bool do_mass, LaneSum<TC> &acc) {
+__device__ __forceinline__ int process_item(const StepParams<TC> &p, const GridDev &g,
+                                            const VPDev &vp, int chunk, long long t, int src,
+                                            int lane, bool do_mass, LaneSum<TC> &acc) {
     const ColGeom cg = col_geom(g, vp, chunk, lane);
     TC y[NZ];
     TC cref;
-    column_physics<TS, TC, NZ, EXACT, NZLO>(p, g, cg, t, src, y, cref);
+    const int kc = column_physics<TS, TC, NZ, EXACT, NZLO>(p, g, cg, t, src, y, cref);
     if (do_mass) store_column<TS, TC, NZ, EXACT, NZLO, true>(g, cg, src, y, cref, acc);
     else store_column<TS, TC, NZ, EXACT, NZLO, false>(g, cg, src, y, cref, acc);
+    return kc;
 }
 
 // ------------------------------------------------------------ grid barrier
@@ -421,10 +424,16 @@ lb_step_kernel(const __grid_constant__ StepParams<TC> p) {
                 cur_grid = vp.grid;
             }
             long long c0 = clock64();
-            process_item<TS, TC, NZ, EXACT, NZLO>(p, g, vp, it.y, t, src, lane, do_mass, acc);
+            const int kc = process_item<TS, TC, NZ, EXACT, NZLO>(p, g, vp, it.y, t, src, lane,
+                                                                 do_mass, acc);
             __syncwarp();
             long long c1 = clock64();
-            if (lane == 0) atomicAdd(&p.vp_cycles[it.x], (unsigned long long)(c1 - c0));
+            // cell-sweep updates actually performed: sum of k_c * nz over the item
+            const unsigned ksum = __reduce_add_sync(0xffffffffu, (unsigned)kc);
+            if (lane == 0) {
+                atomicAdd(&p.vp_cycles[it.x], (unsigned long long)(c1 - c0));
+                if (p.sweeps) atomicAdd(p.sweeps, (unsigned long long)ksum * (unsigned)g.nz);
+            }
         }
         if (do_mass && cur_grid >= 0) {
             double v = acc.take();

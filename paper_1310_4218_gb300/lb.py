@@ -16,13 +16,15 @@ LIB_PATH = os.path.join(_PKG, "_build", "liblb.so")
 
 LB_OK, LB_EINVAL, LB_ECUDA, LB_ETIMEOUT, LB_ENUMERIC, LB_ESTATE, LB_ENORESIDENT, LB_EIO = range(8)
 LB_F64, LB_F32, LB_BF16 = 0, 1, 2
-LB_STATIC, LB_GREEDY, LB_REFINE_SWAP, LB_ATOMIC_QUEUE, LB_AUTO = range(5)
+(LB_STATIC, LB_GREEDY, LB_REFINE_SWAP, LB_ATOMIC_QUEUE, LB_AUTO, LB_GREEDY_SPATIAL,
+ LB_AUTO_SPATIAL) = range(7)
 
 STATUS_NAMES = {0: "LB_OK", 1: "LB_EINVAL", 2: "LB_ECUDA", 3: "LB_ETIMEOUT", 4: "LB_ENUMERIC",
                 5: "LB_ESTATE", 6: "LB_ENORESIDENT", 7: "LB_EIO"}
 DTYPES = {"f64": LB_F64, "f32": LB_F32, "bf16": LB_BF16}
 STRATEGIES = {"static": LB_STATIC, "greedy": LB_GREEDY, "refine_swap": LB_REFINE_SWAP,
-              "queue": LB_ATOMIC_QUEUE, "auto": LB_AUTO}
+              "queue": LB_ATOMIC_QUEUE, "auto": LB_AUTO, "greedy_spatial": LB_GREEDY_SPATIAL,
+              "auto_spatial": LB_AUTO_SPATIAL}
 
 
 class LBError(RuntimeError):
@@ -51,7 +53,8 @@ class lb_options(ctypes.Structure):
     _fields_ = [("ctas_per_sm", ctypes.c_int32), ("queue_order", ctypes.c_int32),
                 ("mass_every", ctypes.c_int32), ("device_balancer", ctypes.c_int32),
                 ("ema_alpha", ctypes.c_double), ("refine_tol", ctypes.c_double),
-                ("barrier_timeout_ns", ctypes.c_int64), ("reserved", ctypes.c_int32 * 8)]
+                ("barrier_timeout_ns", ctypes.c_int64), ("threads_hint", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 7)]
 
 
 class lb_info(ctypes.Structure):
@@ -78,6 +81,7 @@ _SIG = {
     "lb_set_kc": (_I32, [_P, _I32, _P]),
     "lb_mass": (_I32, [_P, _I32, _P, _P]),
     "lb_mass_history": (_I32, [_P, _I32, _P, _I32, _P]),
+    "lb_work_done": (_I32, [_P, _P, _P]),
     "lb_current_field": (_I32, [_P, _I32, ctypes.POINTER(_P)]),
     "lb_sync": (_I32, [_P]),
     "lb_checkpoint": (_I32, [_P, ctypes.c_char_p]),
@@ -210,6 +214,14 @@ def lb_mass_history(ctx, grid=0, max_entries=1024):
     _check(load_library().lb_mass_history(ctx, int(grid), _ptr(buf), int(max_entries),
                                           ctypes.addressof(n)), ctx)
     return buf[:n.value]
+
+
+def lb_work_done(ctx):
+    """(cell_sweeps, cell_steps) performed since lb_create, counted on the device."""
+    a = ctypes.c_int64(0)
+    b = ctypes.c_int64(0)
+    _check(load_library().lb_work_done(ctx, ctypes.addressof(a), ctypes.addressof(b)), ctx)
+    return a.value, b.value
 
 
 def lb_current_field(ctx, grid=0):

@@ -94,3 +94,13 @@ def test_create_rejects_invalid_layout_before_touching_the_device(lbmod):
     with pytest.raises(lbmod.LBError) as e:
         lbmod.lb_create([bad], [(0, 0, 0, 8, 8)])
     assert "cx" in str(e.value)
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_plan_greedy_spatial_matches_oracle(lbmod, seed):
+    rng = random.Random(500 + seed)
+    nb = rng.randint(2, 30)
+    nv = rng.randint(nb, 400)
+    costs = [rng.lognormvariate(0, 1) for _ in range(nv)]
+    g, _, _ = lbmod.lb_plan("greedy_spatial", costs, nb)
+    assert list(g) == B.greedy_ordered(costs, nb, list(range(nv)))

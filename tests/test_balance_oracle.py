@@ -120,3 +120,19 @@ def test_refine_is_idle_when_balanced():
 def test_greedy_ties_break_by_id():
     """Equal costs: VP v lands on bin v mod m (lowest-id tie rules)."""
     assert B.greedy([1.0] * 7, 3) == [0, 1, 2, 0, 1, 2, 0]
+
+
+def test_ordered_greedy_is_graham_list_scheduling():
+    """Objects in the given order to the least-loaded bin: Graham's bound
+    makespan <= (2 - 1/m) OPT holds for any order (brute-force OPT)."""
+    rng = random.Random(77)
+    for _ in range(30):
+        m = rng.choice([2, 3])
+        n = rng.randint(m, 8)
+        costs = [float(rng.randint(1, 30)) for _ in range(n)]
+        order = list(range(n))
+        rng.shuffle(order)
+        a = B.greedy_ordered(costs, m, order)
+        assert max(B.bin_loads(costs, a, m)) <= (2 - 1 / m) * brute_force_makespan(costs, m) + 1e-12
+    # equal costs in id order: round robin
+    assert B.greedy_ordered([1.0] * 5, 2, list(range(5))) == [0, 1, 0, 1, 0]

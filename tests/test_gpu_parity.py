@@ -74,7 +74,8 @@ def test_general_advection(cx, cy, cz):
     assert normwise(out, ref) <= 1e-5
 
 
-@pytest.mark.parametrize("strategy", ["static", "greedy", "refine_swap", "queue", "auto"])
+@pytest.mark.parametrize("strategy", ["static", "greedy", "refine_swap", "queue", "auto",
+                                      "greedy_spatial", "auto_spatial"])
 def test_strategies_give_identical_fields(strategy):
     """Balancing changes only where columns run, never their values: every
     strategy yields the same bits, and they match the oracle."""
@@ -275,3 +276,18 @@ def test_measured_costs_follow_kc():
     assert pred <= B.max_over_mean(list(cost), B.static_blocks(len(vps), sim.info().nprocs),
                                    sim.info().nprocs)
     sim.close()
+
+
+def test_device_work_counter_matches_kc_rule():
+    """lb_work_done counts nz * k_c over every column and step on the device."""
+    from paper_1310_4218_gb300 import lb
+    g = Grid(70, 45, 24, disk=(60, 40, 2, 1, 11), k_in=9, k_out=2)
+    q = round_to_storage(random_field(g, 21), "f32")
+    sim = make_sim([g], [q], regular_blocks(70, 45, 16, 8))
+    sim.step(4)
+    sim.step(3)
+    sweeps, cells = lb.lb_work_done(sim.ctx)
+    sim.close()
+    expect = sum(int(oracle.kc_field(g.oracle(), t).sum()) * g.nz for t in range(7))
+    assert sweeps == expect
+    assert cells == 7 * 70 * 45 * 24
