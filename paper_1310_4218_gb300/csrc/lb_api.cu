@@ -351,12 +351,24 @@ extern "C" lb_status lb_create(const lb_grid_desc *grids, int32_t ngrids, const 
     // coefficients and grid table
     const double r = grids[0].r;
     double m[kNzMax];
-    pivots(r, ctx->kinfo.exact ? ctx->kinfo.nz_variant : 0, m);
+    // split kernels eliminate from both ends: the pivots of a column that
+    // starts at a zero-flux end, and the middle 2x2 coupling
+    const bool exact_table = ctx->kinfo.exact && !ctx->kinfo.split;
+    pivots(r, exact_table ? ctx->kinfo.nz_variant : 0, m);
     for (int k = 0; k < kNzMax; ++k) {
         ctx->coef_d.m[k] = m[k];
         ctx->coef_d.rm[k] = r * m[k];
         ctx->coef_f.m[k] = (float)m[k];
         ctx->coef_f.rm[k] = (float)(r * m[k]);
+    }
+    {
+        const int h = ctx->kinfo.nz_variant / 2;
+        const double a = ctx->kinfo.split ? r * m[h - 1] : 0.0;
+        const double c = 1.0 / (1.0 - a * a);
+        ctx->coef_d.ifa = a;
+        ctx->coef_d.ifc = c;
+        ctx->coef_f.ifa = (float)a;
+        ctx->coef_f.ifc = (float)c;
     }
     ctx->h_grids.resize(ngrids);
     for (int g = 0; g < ngrids; ++g) ctx->cells += (long long)grids[g].nx * grids[g].ny * grids[g].nz;
@@ -404,7 +416,7 @@ extern "C" lb_status lb_create(const lb_grid_desc *grids, int32_t ngrids, const 
     for (int v = 0; v < nvps; ++v) {
         const lb_vp &p = vps[v];
         hv[v] = VPDev{p.grid, p.x0, p.y0, p.w, p.h, p.w * p.h, 0, 0};
-        ctx->vp_nchunks[v] = (p.w * p.h + kWarp - 1) / kWarp;
+        ctx->vp_nchunks[v] = (p.w * p.h + ctx->kinfo.cols_per_item - 1) / ctx->kinfo.cols_per_item;
         ctx->nitems += ctx->vp_nchunks[v];
     }
     static_blocks(nvps, ctx->nbins, ctx->assign);

@@ -42,6 +42,7 @@ template <class TC>
 struct Coef {
     TC m[kNzMax];
     TC rm[kNzMax];
+    TC ifa, ifc;   // split kernels: interface coupling a = r m_{H-1}, 1/(1-a^2)
 };
 
 template <class TC>
@@ -76,6 +77,8 @@ struct KernelInfo {
     int threads;
     int nz_variant;
     int exact;
+    int split;          // 1: two lanes per column (twisted factorisation)
+    int cols_per_item;  // columns of one work item: 32, or 16 when split
 };
 bool find_step_kernel(int storage, int compute, int nz_max, int nz_min, bool all_same_nz,
                       KernelInfo *out, int threads_hint = 0);

@@ -132,11 +132,14 @@ cudaError_t launch_noalloc(const KernelInfo &ki, unsigned char *base, int nbins,
     p.mass_t = reinterpret_cast<long long *>(base + kOffMassT);
     p.mass_seq = reinterpret_cast<unsigned long long *>(base + kOffMassSeq);
     double m[kNzMax];
-    pivot_table(r, ki.exact ? ki.nz_variant : 0, m);
+    pivot_table(r, (ki.exact && !ki.split) ? ki.nz_variant : 0, m);
     for (int k = 0; k < kNzMax; ++k) {
         p.coef.m[k] = (TC)m[k];
         p.coef.rm[k] = (TC)(r * m[k]);
     }
+    const double a = ki.split ? r * m[ki.nz_variant / 2 - 1] : 0.0;
+    p.coef.ifa = (TC)a;
+    p.coef.ifc = (TC)(1.0 / (1.0 - a * a));
     cudaLaunchConfig_t cfg;
     std::memset(&cfg, 0, sizeof(cfg));
     cfg.gridDim = dim3(nbins);
@@ -179,6 +182,10 @@ extern "C" lb_status lb_step_noalloc(const lb_grid_desc *grid, const lb_vp *vps,
     if (!d.kc_disk && !d.kc) return fail(LB_EINVAL, "kc array required");
     if (d.kc_disk && (d.k_in < 0 || d.k_out < 0 || d.disk_r < 0))
         return fail(LB_EINVAL, "disk needs k_in, k_out, R >= 0");
+    KernelInfo ki;
+    if (!find_step_kernel(d.storage, d.compute, d.nz, d.nz, true, &ki))
+        return fail(LB_EINVAL, "no kernel variant for this grid");
+    const int cpi = ki.cols_per_item;
     long long area = 0, nitems = 0;
     for (int v = 0; v < nvps; ++v) {
         const lb_vp &p = vps[v];
@@ -186,7 +193,7 @@ extern "C" lb_status lb_step_noalloc(const lb_grid_desc *grid, const lb_vp *vps,
             p.y0 + p.h > d.ny)
             return fail(LB_EINVAL, "a VP lies outside the grid (grid index must be 0)");
         area += (long long)p.w * p.h;
-        nitems += (p.w * p.h + kWarp - 1) / kWarp;
+        nitems += (p.w * p.h + cpi - 1) / cpi;
     }
     if (area != (long long)d.nx * d.ny) return fail(LB_EINVAL, "VPs do not tile the grid");
     if (nitems > kMaxItems) return fail(LB_EINVAL, "too many work items for LB_NOALLOC_MAX_ITEMS");
@@ -215,9 +222,6 @@ extern "C" lb_status lb_step_noalloc(const lb_grid_desc *grid, const lb_vp *vps,
     }
     unsigned char *base = g_dev_scratch[dev];
 
-    KernelInfo ki;
-    if (!find_step_kernel(d.storage, d.compute, d.nz, d.nz, true, &ki))
-        return fail(LB_EINVAL, "no kernel variant for this grid");
     int nsm = 0, occ = 0;
     e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess)
@@ -267,7 +271,7 @@ extern "C" lb_status lb_step_noalloc(const lb_grid_desc *grid, const lb_vp *vps,
         const int vend = (int)(((long long)(b + 1) * nvps) / nbins);
         for (; v < vend; ++v) {
             const int ncols = vps[v].w * vps[v].h;
-            for (int c = 0; c * kWarp < ncols; ++c) h_items[ni++] = make_int2(v, c);
+            for (int c = 0; c * cpi < ncols; ++c) h_items[ni++] = make_int2(v, c);
         }
     }
     h_bin_start[nbins] = ni;

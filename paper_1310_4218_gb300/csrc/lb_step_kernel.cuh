@@ -290,6 +290,116 @@ __device__ __forceinline__ int process_item(const StepParams<TC> &p, const GridD
     return kc;
 }
 
+// ------------------------------------------------------------ split columns
+// Two lanes per column: lane l (l < 16) holds levels 0..H-1 of the item's
+// column l, lane l+16 holds levels NZ-1..H of the same column, both indexed
+// by the distance s from their own end (H = NZ/2).  A solve is the twisted
+// ("burn at both ends") factorisation of the tridiagonal system: both lanes
+// eliminate toward the middle at once -- M is symmetric under k -> NZ-1-k,
+// so both use the same pivots m_s of a column that starts at a zero-flux
+// end -- then exchange their last eliminated values p (own) and p' (other,
+// one shuffle) and solve the 2x2 middle system
+//     x_own = (p + a p') / (1 - a^2),   a = r m_{H-1},
+// and back-substitute outward.  Same operation count as one lane running
+// the whole column, half the registers per thread and half the dependence
+// chain per solve.
+template <class TS, class TC, int NZ>
+__device__ __forceinline__ int process_item_split(const StepParams<TC> &p, const GridDev &g,
+                                                  const VPDev &vp, int chunk, long long t,
+                                                  int src, int lane, bool do_mass,
+                                                  LaneSum<TC> &acc) {
+    constexpr int H = NZ / 2;
+    constexpr int kCols = kWarp / 2;
+    const int top = lane >> 4;
+    const int q = chunk * kCols + (lane & (kCols - 1));
+    const bool active = q < vp.ncols;
+    const int qq = active ? q : vp.ncols - 1;
+    const int ly = qq / vp.w;
+    const int i = vp.x0 + (qq - ly * vp.w);
+    const int j = vp.y0 + ly;
+    int im = i - g.sx, jm = j - g.sy;
+    im = im < 0 ? im + g.nx : (im >= g.nx ? im - g.nx : im);
+    jm = jm < 0 ? jm + g.ny : (jm >= g.ny ? jm - g.ny : jm);
+    const int plane = g.plane;
+    const int oc = j * g.nx + i, oi = j * g.nx + im, oj = jm * g.nx + i;
+    // element offset of local level s: (top ? NZ-1-s : s) * plane
+    const int lbase = top ? (NZ - 1) * plane : 0;
+    const int lstep = top ? -plane : plane;
+    const TS *in = static_cast<const TS *>(g.q[src]);
+    TS *out = static_cast<TS *>(g.q[src ^ 1]);
+
+    int kc = g.kc_disk ? kc_disk(g, i, j, t) : g.kc[oc];
+    if (!active || !g.sweeps_on) kc = 0;
+
+    TC y[H];
+    const TC wx = wgt<TC>(g, 1), wy = wgt<TC>(g, 2);
+    if (g.xy_only) {
+#pragma unroll
+        for (int s = 0; s < H; ++s) {
+            const int off = lbase + s * lstep;
+            TC a = IO<TS, TC>::ld(in + (off + oi));
+            TC b = IO<TS, TC>::ld(in + (off + oj));
+            y[s] = fmaT(wy, b, wx * a);
+        }
+    } else {
+        const TC w0 = wgt<TC>(g, 0), wz = wgt<TC>(g, 3);
+        const int sz = g.sz;
+        const int kdown = sz >= 0 ? NZ - 1 : 0;
+#pragma unroll
+        for (int s = 0; s < H; ++s) {
+            const int k = top ? NZ - 1 - s : s;
+            const int off = lbase + s * lstep;
+            TC c = IO<TS, TC>::ld(in + (off + oc));
+            TC a = IO<TS, TC>::ld(in + (off + oi));
+            TC b = IO<TS, TC>::ld(in + (off + oj));
+            TC v = fmaT(wy, b, wx * a);
+            v = fmaT(k == kdown ? w0 + wz : w0, c, v);
+            const int ku = k - sz;
+            if (ku >= 0 && ku < NZ) v = fmaT(wz, IO<TS, TC>::ld(in + (ku * plane + oc)), v);
+            y[s] = v;
+        }
+    }
+
+    // shift by the column's level H-1 value (held by the bottom lane)
+    const TC mid = __shfl_xor_sync(0xffffffffu, y[H - 1], kCols);
+    TC cref = kc > 0 ? (top ? mid : y[H - 1]) : TC(0);
+    if (kc > 0) {
+#pragma unroll
+        for (int s = 0; s < H; ++s) y[s] -= cref;
+    }
+    const Coef<TC> &cf = p.coef;
+    const int kmax = __reduce_max_sync(0xffffffffu, (unsigned)kc);
+    for (int r = 0; r < kmax; ++r) {
+        const bool act = r < kc;
+        if (act) {
+            TC pp = y[0] * cf.m[0];
+            y[0] = pp;
+#pragma unroll
+            for (int s = 1; s < H; ++s) {
+                pp = fmaT(pp, cf.rm[s], y[s] * cf.m[s]);
+                y[s] = pp;
+            }
+        }
+        const TC other = __shfl_xor_sync(0xffffffffu, y[H - 1], kCols);
+        if (act) {
+            y[H - 1] = fmaT(cf.ifa, other, y[H - 1]) * cf.ifc;
+#pragma unroll
+            for (int s = H - 2; s >= 0; --s) y[s] = fmaT(cf.rm[s], y[s + 1], y[s]);
+        }
+    }
+
+    if (active) {
+        if (do_mass) acc.col_begin();
+#pragma unroll
+        for (int s = 0; s < H; ++s) {
+            TC xs = IO<TS, TC>::st(out + (lbase + s * lstep + oc), y[s] + cref);
+            if (do_mass) acc.add(xs);
+        }
+        if (do_mass) acc.col_end();
+    }
+    return top ? 0 : kc;
+}
+
 // ------------------------------------------------------------ grid barrier
 // Sense-reversing barrier over all CTAs with a time limit.  On timeout the
 // CTA records LB_ETIMEOUT in the status word and returns false; so does
@@ -365,7 +475,7 @@ __device__ __forceinline__ void reduce_mass(const StepParams<TC> &p, int s) {
 }
 
 // ------------------------------------------------------------ the kernel
-template <class TS, class TC, int NZ, bool EXACT, int NZLO, int THREADS>
+template <class TS, class TC, int NZ, bool EXACT, int NZLO, int THREADS, bool SPLIT>
 __global__ void __launch_bounds__(THREADS, 1)
 lb_step_kernel(const __grid_constant__ StepParams<TC> p) {
     extern __shared__ double s_mass[];          // [warps][ngrids]
@@ -424,8 +534,12 @@ lb_step_kernel(const __grid_constant__ StepParams<TC> p) {
                 cur_grid = vp.grid;
             }
             long long c0 = clock64();
-            const int kc = process_item<TS, TC, NZ, EXACT, NZLO>(p, g, vp, it.y, t, src, lane,
-                                                                 do_mass, acc);
+            int kc;
+            if constexpr (SPLIT)
+                kc = process_item_split<TS, TC, NZ>(p, g, vp, it.y, t, src, lane, do_mass, acc);
+            else
+                kc = process_item<TS, TC, NZ, EXACT, NZLO>(p, g, vp, it.y, t, src, lane, do_mass,
+                                                           acc);
             __syncwarp();
             long long c1 = clock64();
             // cell-sweep updates actually performed: sum of k_c * nz over the item
@@ -462,13 +576,16 @@ lb_step_kernel(const __grid_constant__ StepParams<TC> p) {
     }
 }
 
-template <class TS, class TC, int NZ, bool EXACT, int NZLO, int THREADS>
+template <class TS, class TC, int NZ, bool EXACT, int NZLO, int THREADS, bool SPLIT = false>
 inline KernelInfo kernel_entry() {
+    static_assert(!SPLIT || (EXACT && NZ % 2 == 0), "split kernels need an exact, even nz");
     KernelInfo k;
-    k.fn = (const void *)&lb_step_kernel<TS, TC, NZ, EXACT, NZLO, THREADS>;
+    k.fn = (const void *)&lb_step_kernel<TS, TC, NZ, EXACT, NZLO, THREADS, SPLIT>;
     k.threads = THREADS;
     k.nz_variant = NZ;
     k.exact = EXACT ? 1 : 0;
+    k.split = SPLIT ? 1 : 0;
+    k.cols_per_item = SPLIT ? kWarp / 2 : kWarp;
     return k;
 }
 
