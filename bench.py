@@ -117,6 +117,38 @@ def kc_epochs(w, nsteps_total):
     return {e: [w.kc_array(gi, e) for gi in range(len(w.grids))] for e in range(n)}
 
 
+def max_over_ranks(x):
+    """Largest value over all ranks (time-like quantities); identity on one rank."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    dev = (torch.device("cuda", torch.cuda.current_device()) if dist.get_backend() == "nccl"
+           else torch.device("cpu"))
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x):
+    """Sum over all ranks (work done by independent replicas)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    dev = (torch.device("cuda", torch.cuda.current_device()) if dist.get_backend() == "nccl"
+           else torch.device("cpu"))
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def whole_job_rate(work_local, ms_local):
+    """Whole-job throughput of N replicas: all ranks' work over the slowest
+    rank's time (the barrier-bracketed region)."""
+    return sum_over_ranks(work_local) / (max_over_ranks(ms_local) / 1000.0)
+
+
 def roofline_peak():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -362,13 +394,10 @@ def main():
     if world > 1:
         dist.barrier()
     m = run.timed(args.steps, ClockSampler(local_rank))
-    ms = m["ms"]
-    if world > 1:
-        tm = torch.tensor([ms], device=dev)
-        dist.all_reduce(tm, op=dist.ReduceOp.MAX)
-        ms = float(tm.item())
+    ms = max_over_ranks(m["ms"])
     s = ms / 1000.0
-    value = m["sweeps"] * world / s
+    value = whole_job_rate(m["sweeps"], m["ms"])
+    cells_all = sum_over_ranks(m["cells"])
 
     g0 = w.grids[0]
     steps_per_launch = args.steps * P / m["launches"]
@@ -385,7 +414,7 @@ def main():
         try:
             e2e = run.end_to_end(fields, args.steps)
             if e2e:
-                e2e["value"] *= world
+                e2e["value"] = sum_over_ranks(e2e["value"])
         except Exception as ex:    # report, keep the device-timed line
             e2e = {"value": None, "unit": "cell-sweep updates/s", "error": repr(ex)[:200]}
     stats = run.stats
@@ -422,7 +451,7 @@ def main():
                        "strategy": args.strategy,
                        "parallelism": "replicas" if world > 1 else "1gpu",
                        "l2": "fields larger than L2 (no flush)",
-                       "cell_steps_per_s": m["cells"] * world / s,
+                       "cell_steps_per_s": cells_all / s,
                        "processors": info.nprocs, "threads_per_cta": info.threads_per_cta},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_source": peak_src,

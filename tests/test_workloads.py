@@ -54,3 +54,14 @@ def test_batch_workload_grids():
         assert 64 <= g.nx <= 512 and g.nx == g.ny and 32 <= g.nz <= 96
         assert 2 <= g.k_in <= 48
         assert covers_exactly(w.vps, g.nx, g.ny, grid=gi)
+
+
+def test_autotune_split_layout_tiles():
+    from paper_1310_4218_gb300.autotune import split_layout
+    vps = guillotine(256, 256, 64, 8, 5)
+    for f in (1, 2, 3):
+        s = split_layout(vps, f)
+        assert covers_exactly(s, 256, 256)
+        assert len(s) >= len(vps)
+    s2 = split_layout(vps, 2)
+    assert all(w >= 8 and h >= 8 for (_, _, _, w, h) in s2)
