@@ -5,8 +5,11 @@ CPU-oracle baselines.
 One benchmark step = one rebalance period: `period` time steps of every VP
 (advection, k_c Thomas sweeps, store, global sum, per-VP cost stamps, grid
 barrier) in one persistent launch, then the load measurement and the
-rebalance (GreedyLB first, RefineSwapLB after).  The k_c array is re-drawn
-every 50 time steps as the workload prescribes.
+rebalance.  The headline strategy is auto_spatial: GreedyLB's rule with the
+VPs in spatial order on the first call, RefineSwapLB after; the static
+table, the paper-order GreedyLB/RefineSwapLB schedule and the atomic queue
+are measured the same way and reported beside it.  The k_c array is
+re-drawn every 50 time steps as the workload prescribes.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--workload NAME] [--period P] [--strategy auto|static|queue|...]
@@ -41,7 +44,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--period", type=int, default=10)
-    ap.add_argument("--strategy", default="auto")
+    ap.add_argument("--strategy", default="auto_spatial")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--threads", type=int, default=0, help="threads per processor (0: default)")

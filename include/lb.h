@@ -235,6 +235,23 @@ lb_status lb_work_done(lb_ctx *ctx, int64_t *cell_sweeps, int64_t *cell_steps);
 /* Device pointer of the buffer holding grid `grid`'s latest field. */
 lb_status lb_current_field(lb_ctx *ctx, int32_t grid, void **dev_ptr);
 
+/*
+ * CUDA graphs of the step (the Fig. 2 inner loop replayed without host
+ * launch work).  lb_graph_create captures one persistent launch of nsteps
+ * steps into an executable graph (a cudaGraphExec_t, returned as void*).
+ * The kernel reads the step index and the ping-pong parity from a device
+ * word that every launch advances, so each replay continues where the ctx
+ * stands.  lb_graph_launch replays it on the ctx stream and advances the
+ * ctx's host-side counters; only graphs made for the same ctx are accepted.
+ * A graph keeps the assignment mode it was captured with (processor tables
+ * or atomic queue): rebalancing between table strategies is picked up (the
+ * tables live in device memory), switching to or from LB_ATOMIC_QUEUE needs
+ * a new graph.  lb_destroy frees a ctx's remaining graphs.
+ */
+lb_status lb_graph_create(lb_ctx *ctx, int32_t nsteps, void **graph_exec);
+lb_status lb_graph_launch(lb_ctx *ctx, void *graph_exec);
+lb_status lb_graph_destroy(lb_ctx *ctx, void *graph_exec);
+
 /* Wait for all work of the ctx; report a pending device-side error. */
 lb_status lb_sync(lb_ctx *ctx);
 

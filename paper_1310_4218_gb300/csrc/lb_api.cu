@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -46,6 +47,7 @@ struct lb_ctx {
     long long *d_mass_t = nullptr;
     unsigned long long *d_mass_seq = nullptr;
     unsigned long long *d_sweeps = nullptr;
+    long long *d_clock = nullptr;      // [step, parity] mirrored on the device
     long long cells = 0;               // cells of all grids
     long long cell_steps = 0;
 
@@ -62,6 +64,7 @@ struct lb_ctx {
     long long steps_since_measure = 0;
     Coef<float> coef_f;
     Coef<double> coef_d;
+    std::map<cudaGraphExec_t, int> graph_steps;   // graphs made by lb_graph_create
     std::string err;
 };
 
@@ -201,7 +204,7 @@ static void free_ctx(lb_ctx *ctx) {
                     ctx->d_bin_start, ctx->d_bar,      ctx->d_status,    ctx->d_qhead,
                     ctx->d_vp_cycles, ctx->d_bin_busy, ctx->d_bin_smid,  ctx->d_bin_cal,
                     ctx->d_bin_mass,  ctx->d_mass_hist, ctx->d_mass_t,   ctx->d_mass_seq,
-                    ctx->d_sweeps};
+                    ctx->d_sweeps,    ctx->d_clock};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete ctx;
@@ -440,6 +443,7 @@ extern "C" lb_status lb_create(const lb_grid_desc *grids, int32_t ngrids, const 
     if (e == cudaSuccess) e = dalloc(&ctx->d_mass_t, kMassHist);
     if (e == cudaSuccess) e = dalloc(&ctx->d_mass_seq, 1);
     if (e == cudaSuccess) e = dalloc(&ctx->d_sweeps, 1);
+    if (e == cudaSuccess) e = dalloc(&ctx->d_clock, 2);
     cudaStream_t sm = ctx->stream;
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(ctx->d_grids, ctx->h_grids.data(), sizeof(GridDev) * ngrids,
@@ -451,6 +455,7 @@ extern "C" lb_status lb_create(const lb_grid_desc *grids, int32_t ngrids, const 
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_bin_busy, 0, sizeof(unsigned long long) * nb, sm);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_mass_seq, 0, sizeof(unsigned long long), sm);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_sweeps, 0, sizeof(unsigned long long), sm);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_clock, 0, 2 * sizeof(long long), sm);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_bin_cal, 0, sizeof(long long) * 4 * nb, sm);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_bin_smid, 0xff, sizeof(int32_t) * nb, sm);
     if (e == cudaSuccess) e = cudaStreamSynchronize(sm);
@@ -495,6 +500,7 @@ static lb_status launch(lb_ctx *ctx, int nsteps, const Coef<TC> &coef) {
     p.mass_t = ctx->d_mass_t;
     p.mass_seq = ctx->d_mass_seq;
     p.sweeps = ctx->d_sweeps;
+    p.dclock = ctx->d_clock;
     p.coef = coef;
 
     CK(cudaMemsetAsync(ctx->d_bar, 0, 2 * sizeof(unsigned), ctx->stream));
@@ -526,6 +532,61 @@ extern "C" lb_status lb_step(lb_ctx *ctx, int32_t nsteps) {
     ctx->cell_steps += ctx->cells * nsteps;
     ctx->parity ^= (nsteps & 1);
     ctx->steps_since_measure += nsteps;
+    return LB_OK;
+}
+
+// ------------------------------------------------------------------ graphs
+extern "C" lb_status lb_graph_create(lb_ctx *ctx, int32_t nsteps, void **graph_exec) {
+    if (!ctx || !graph_exec || nsteps < 1) return fail(ctx, LB_EINVAL, "lb_graph_create: bad arguments");
+    *graph_exec = nullptr;
+    CK(cudaStreamSynchronize(ctx->stream));
+    // capture on a private stream: the ctx stream may be the legacy default
+    // stream, which cannot be captured; the graph does not depend on it
+    cudaStream_t cap = nullptr;
+    CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    cudaStream_t own = ctx->stream;
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    lb_status st = LB_OK;
+    if (e == cudaSuccess) {
+        ctx->stream = cap;
+        st = ctx->compute == LB_F64 ? launch<double>(ctx, nsteps, ctx->coef_d)
+                                    : launch<float>(ctx, nsteps, ctx->coef_f);
+        ctx->stream = own;
+        e = cudaStreamEndCapture(cap, &graph);
+    }
+    cudaStreamDestroy(cap);
+    if (st != LB_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return st;
+    }
+    if (e != cudaSuccess) return fail(ctx, LB_ECUDA, std::string("capture: ") + cudaGetErrorString(e));
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return fail(ctx, LB_ECUDA, std::string("instantiate: ") + cudaGetErrorString(e));
+    ctx->graph_steps[exec] = nsteps;
+    *graph_exec = exec;
+    return LB_OK;
+}
+
+extern "C" lb_status lb_graph_launch(lb_ctx *ctx, void *graph_exec) {
+    if (!ctx || !graph_exec) return fail(ctx, LB_EINVAL, "lb_graph_launch: bad arguments");
+    auto it = ctx->graph_steps.find((cudaGraphExec_t)graph_exec);
+    if (it == ctx->graph_steps.end()) return fail(ctx, LB_EINVAL, "graph was not made for this ctx");
+    CK(cudaGraphLaunch((cudaGraphExec_t)graph_exec, ctx->stream));
+    const int n = it->second;
+    ctx->step += n;
+    ctx->cell_steps += ctx->cells * n;
+    ctx->parity ^= (n & 1);
+    ctx->steps_since_measure += n;
+    return LB_OK;
+}
+
+extern "C" lb_status lb_graph_destroy(lb_ctx *ctx, void *graph_exec) {
+    if (!ctx || !graph_exec) return fail(ctx, LB_EINVAL, "lb_graph_destroy: bad arguments");
+    ctx->graph_steps.erase((cudaGraphExec_t)graph_exec);
+    CK(cudaGraphExecDestroy((cudaGraphExec_t)graph_exec));
     return LB_OK;
 }
 
@@ -877,6 +938,9 @@ extern "C" lb_status lb_restore(lb_ctx *ctx, const char *path) {
     ctx->step = step;
     ctx->parity = parity;
     ctx->steps_since_measure = 0;
+    long long clk[2] = {step, parity};
+    CK(cudaMemcpyAsync(ctx->d_clock, clk, sizeof(clk), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
     CK(cudaMemsetAsync(ctx->d_vp_cycles, 0, sizeof(unsigned long long) * ctx->vps.size(), ctx->stream));
     CK(cudaMemsetAsync(ctx->d_bin_busy, 0, sizeof(unsigned long long) * ctx->nbins, ctx->stream));
     return upload_items(ctx);
@@ -905,6 +969,7 @@ extern "C" const char *lb_last_error(const lb_ctx *ctx) {
 extern "C" void lb_destroy(lb_ctx *ctx) {
     if (!ctx) return;
     cudaStreamSynchronize(ctx->stream);
+    for (auto &kv : ctx->graph_steps) cudaGraphExecDestroy(kv.first);
     free_ctx(ctx);
 }
 

@@ -303,12 +303,40 @@ __device__ __forceinline__ int process_item(const StepParams<TC> &p, const GridD
 // and back-substitute outward.  Same operation count as one lane running
 // the whole column, half the registers per thread and half the dependence
 // chain per solve.
+// Packed FP32 pairs (sm_100+ f32x2 instructions) for independent work on two
+// levels: advection, shift, and two interleaved compensated sums.
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+
+// Sum2 (TwoSum errors kept apart) on two interleaved chains at once.
+struct PairSum {
+    float2 s, e;
+    __device__ __forceinline__ void begin() {
+        s = f2(0.f, 0.f);
+        e = f2(0.f, 0.f);
+    }
+    __device__ __forceinline__ void add(float2 v) {
+        const float2 m1 = f2(-1.f, -1.f);
+        const float2 t = add2(s, v);
+        const float2 bp = fma2(s, m1, t);       // t - s
+        const float2 a1 = fma2(bp, m1, t);      // t - bp
+        const float2 a2 = fma2(a1, m1, s);      // s - (t - bp)
+        const float2 a3 = fma2(bp, m1, v);      // v - bp
+        e = add2(e, add2(a2, a3));
+        s = t;
+    }
+};
+
 template <class TS, class TC, int NZ>
 __device__ __forceinline__ int process_item_split(const StepParams<TC> &p, const GridDev &g,
                                                   const VPDev &vp, int chunk, long long t,
                                                   int src, int lane, bool do_mass,
                                                   LaneSum<TC> &acc) {
+    static_assert(sizeof(TS) == 4 && sizeof(TC) == 4, "split kernels are FP32");
     constexpr int H = NZ / 2;
+    static_assert(H % 2 == 0, "levels are processed in pairs");
     constexpr int kCols = kWarp / 2;
     const int top = lane >> 4;
     const int q = chunk * kCols + (lane & (kCols - 1));
@@ -331,28 +359,30 @@ __device__ __forceinline__ int process_item_split(const StepParams<TC> &p, const
     int kc = g.kc_disk ? kc_disk(g, i, j, t) : g.kc[oc];
     if (!active || !g.sweeps_on) kc = 0;
 
-    TC y[H];
-    const TC wx = wgt<TC>(g, 1), wy = wgt<TC>(g, 2);
+    float2 y2[H / 2];                  // levels 2m, 2m+1 in one register pair
+    float *y = reinterpret_cast<float *>(y2);
+    const float wx = wgt<float>(g, 1), wy = wgt<float>(g, 2);
     if (g.xy_only) {
+        const float2 wx2 = f2(wx, wx), wy2 = f2(wy, wy);
 #pragma unroll
-        for (int s = 0; s < H; ++s) {
-            const int off = lbase + s * lstep;
-            TC a = IO<TS, TC>::ld(in + (off + oi));
-            TC b = IO<TS, TC>::ld(in + (off + oj));
-            y[s] = fmaT(wy, b, wx * a);
+        for (int m = 0; m < H / 2; ++m) {
+            const int off0 = lbase + (2 * m) * lstep, off1 = off0 + lstep;
+            const float2 a = f2(IO<TS, TC>::ld(in + (off0 + oi)), IO<TS, TC>::ld(in + (off1 + oi)));
+            const float2 b = f2(IO<TS, TC>::ld(in + (off0 + oj)), IO<TS, TC>::ld(in + (off1 + oj)));
+            y2[m] = fma2(wy2, b, mul2(wx2, a));
         }
     } else {
-        const TC w0 = wgt<TC>(g, 0), wz = wgt<TC>(g, 3);
+        const float w0 = wgt<float>(g, 0), wz = wgt<float>(g, 3);
         const int sz = g.sz;
         const int kdown = sz >= 0 ? NZ - 1 : 0;
 #pragma unroll
         for (int s = 0; s < H; ++s) {
             const int k = top ? NZ - 1 - s : s;
             const int off = lbase + s * lstep;
-            TC c = IO<TS, TC>::ld(in + (off + oc));
-            TC a = IO<TS, TC>::ld(in + (off + oi));
-            TC b = IO<TS, TC>::ld(in + (off + oj));
-            TC v = fmaT(wy, b, wx * a);
+            float c = IO<TS, TC>::ld(in + (off + oc));
+            float a = IO<TS, TC>::ld(in + (off + oi));
+            float b = IO<TS, TC>::ld(in + (off + oj));
+            float v = fmaT(wy, b, wx * a);
             v = fmaT(k == kdown ? w0 + wz : w0, c, v);
             const int ku = k - sz;
             if (ku >= 0 && ku < NZ) v = fmaT(wz, IO<TS, TC>::ld(in + (ku * plane + oc)), v);
@@ -361,18 +391,19 @@ __device__ __forceinline__ int process_item_split(const StepParams<TC> &p, const
     }
 
     // shift by the column's level H-1 value (held by the bottom lane)
-    const TC mid = __shfl_xor_sync(0xffffffffu, y[H - 1], kCols);
-    TC cref = kc > 0 ? (top ? mid : y[H - 1]) : TC(0);
+    const float mid = __shfl_xor_sync(0xffffffffu, y[H - 1], kCols);
+    const float cref = kc > 0 ? (top ? mid : y[H - 1]) : 0.f;
     if (kc > 0) {
+        const float2 nc = f2(-cref, -cref);
 #pragma unroll
-        for (int s = 0; s < H; ++s) y[s] -= cref;
+        for (int m = 0; m < H / 2; ++m) y2[m] = add2(y2[m], nc);
     }
     const Coef<TC> &cf = p.coef;
     const int kmax = __reduce_max_sync(0xffffffffu, (unsigned)kc);
     for (int r = 0; r < kmax; ++r) {
         const bool act = r < kc;
         if (act) {
-            TC pp = y[0] * cf.m[0];
+            float pp = y[0] * cf.m[0];
             y[0] = pp;
 #pragma unroll
             for (int s = 1; s < H; ++s) {
@@ -380,7 +411,7 @@ __device__ __forceinline__ int process_item_split(const StepParams<TC> &p, const
                 y[s] = pp;
             }
         }
-        const TC other = __shfl_xor_sync(0xffffffffu, y[H - 1], kCols);
+        const float other = __shfl_xor_sync(0xffffffffu, y[H - 1], kCols);
         if (act) {
             y[H - 1] = fmaT(cf.ifa, other, y[H - 1]) * cf.ifc;
 #pragma unroll
@@ -389,13 +420,25 @@ __device__ __forceinline__ int process_item_split(const StepParams<TC> &p, const
     }
 
     if (active) {
-        if (do_mass) acc.col_begin();
+        const float2 c2 = f2(cref, cref);
+        PairSum ps;
+        if (do_mass) ps.begin();
 #pragma unroll
-        for (int s = 0; s < H; ++s) {
-            TC xs = IO<TS, TC>::st(out + (lbase + s * lstep + oc), y[s] + cref);
-            if (do_mass) acc.add(xs);
+        for (int m = 0; m < H / 2; ++m) {
+            const float2 x = add2(y2[m], c2);
+            out[lbase + (2 * m) * lstep + oc] = x.x;
+            out[lbase + (2 * m + 1) * lstep + oc] = x.y;
+            if (do_mass) ps.add(x);
         }
-        if (do_mass) acc.col_end();
+        if (do_mass) {
+            // fold the two chains into the lane's column sum
+            acc.col_begin();
+            acc.s = ps.s.x;
+            acc.e = ps.e.x;
+            acc.add(ps.s.y);
+            acc.e = __fadd_rn(acc.e, ps.e.y);
+            acc.col_end();
+        }
     }
     return top ? 0 : kc;
 }
@@ -448,8 +491,8 @@ __device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned nblocks, lo
 // into one Neumaier-compensated FP64 sum per grid, in processor order, and
 // appends it to the history ring.  Called after the barrier that ends step s.
 template <class TC, int THREADS>
-__device__ __forceinline__ void reduce_mass(const StepParams<TC> &p, int s) {
-    const long long tp = p.t0 + s;
+__device__ __forceinline__ void reduce_mass(const StepParams<TC> &p, long long t0, int s) {
+    const long long tp = t0 + s;
     if (!(p.mass_every > 0 && ((tp + 1) % p.mass_every) == 0)) return;
     const int par = s & 1;
     const unsigned long long seq = *p.mass_seq;
@@ -494,14 +537,18 @@ lb_step_kernel(const __grid_constant__ StepParams<TC> p) {
     }
     const int ibeg = p.queue_mode ? 0 : p.bin_start[bin];
     const int iend = p.queue_mode ? p.nitems : p.bin_start[bin + 1];
+    // step index and buffer parity: kernel parameters, or the device clock
+    // (graph replays: parameters are frozen at capture, the clock is not)
+    const long long t0 = p.dclock ? p.dclock[0] : p.t0;
+    const int parity0 = p.dclock ? (int)p.dclock[1] : p.parity0;
 
     for (int s = 0; s < p.nsteps; ++s) {
-        const long long t = p.t0 + s;
-        const int src = (p.parity0 + s) & 1;
+        const long long t = t0 + s;
+        const int src = (parity0 + s) & 1;
         const bool do_mass = p.mass_every > 0 && ((t + 1) % p.mass_every) == 0;
 
         // reduce the previous step's per-processor sums (processor 0 only)
-        if (bin == 0 && s > 0) reduce_mass<TC, THREADS>(p, s - 1);
+        if (bin == 0 && s > 0) reduce_mass<TC, THREADS>(p, t0, s - 1);
 
         if (threadIdx.x == 0) {
             s_ctr = 0;
@@ -568,8 +615,15 @@ lb_step_kernel(const __grid_constant__ StepParams<TC> p) {
         if (!grid_barrier(p.bar, gridDim.x, p.timeout_ns, p.status, &s_flag)) return;
     }
 
-    // the last step's sums
-    if (bin == 0 && p.nsteps > 0) reduce_mass<TC, THREADS>(p, p.nsteps - 1);
+    // the last step's sums; advance the device clock (every CTA read it
+    // before the first barrier, so processor 0 may now overwrite it)
+    if (bin == 0 && p.nsteps > 0) {
+        reduce_mass<TC, THREADS>(p, t0, p.nsteps - 1);
+        if (p.dclock && threadIdx.x == 0) {
+            p.dclock[0] = t0 + p.nsteps;
+            p.dclock[1] = (parity0 + p.nsteps) & 1;
+        }
+    }
     if (threadIdx.x == 0) {
         p.bin_cal[4 * bin + 2] = (long long)globaltimer_ns();
         p.bin_cal[4 * bin + 3] = clock64();

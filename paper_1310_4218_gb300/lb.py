@@ -84,6 +84,9 @@ _SIG = {
     "lb_work_done": (_I32, [_P, _P, _P]),
     "lb_current_field": (_I32, [_P, _I32, ctypes.POINTER(_P)]),
     "lb_sync": (_I32, [_P]),
+    "lb_graph_create": (_I32, [_P, _I32, ctypes.POINTER(_P)]),
+    "lb_graph_launch": (_I32, [_P, _P]),
+    "lb_graph_destroy": (_I32, [_P, _P]),
     "lb_checkpoint": (_I32, [_P, ctypes.c_char_p]),
     "lb_restore": (_I32, [_P, ctypes.c_char_p]),
     "lb_get_info": (_I32, [_P, ctypes.POINTER(lb_info)]),
@@ -228,6 +231,21 @@ def lb_current_field(ctx, grid=0):
     p = _P()
     _check(load_library().lb_current_field(ctx, int(grid), ctypes.byref(p)), ctx)
     return p.value
+
+
+def lb_graph_create(ctx, nsteps):
+    """Executable CUDA graph of one nsteps-step launch (handle as int)."""
+    g = _P()
+    _check(load_library().lb_graph_create(ctx, int(nsteps), ctypes.byref(g)), ctx)
+    return g.value
+
+
+def lb_graph_launch(ctx, graph):
+    _check(load_library().lb_graph_launch(ctx, _P(graph)), ctx)
+
+
+def lb_graph_destroy(ctx, graph):
+    _check(load_library().lb_graph_destroy(ctx, _P(graph)), ctx)
 
 
 def lb_sync(ctx):

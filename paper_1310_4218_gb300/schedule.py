@@ -11,12 +11,20 @@ from . import lb as L
 
 class Schedule:
     """kc_epochs: {epoch: [int32 (ny, nx) per grid]} for array-k_c grids,
-    re-drawn every `epoch_steps` time steps (0: never)."""
+    re-drawn every `epoch_steps` time steps (0: never).
 
-    def __init__(self, sim, period, strategy="auto", kc_epochs=None, epoch_steps=0):
+    threshold: if set, the balancer is called only when the measured SM
+    max/mean load of the period exceeds it -- the threshold-triggered
+    migration the paper plans as future work (Sec. VII): measurements stay
+    on (they are free on the device), migrations happen only when needed.
+    """
+
+    def __init__(self, sim, period, strategy="auto", kc_epochs=None, epoch_steps=0,
+                 threshold=None):
         self.sim = sim
         self.period = int(period)
         self.strategy = strategy
+        self.threshold = threshold
         self.epoch_steps = int(epoch_steps or 0)
         self.kc_dev = {}
         if kc_epochs:
@@ -63,7 +71,10 @@ class Schedule:
         nprocs = self.sim.info().nprocs
         mean = float(cost.sum()) / nprocs
         rec["granularity_floor"] = float(max(cost.max(), mean) / mean) if mean > 0 else None
-        if self.strategy != "static":
+        skip = (self.threshold is not None and rec["sm_max_over_mean"] is not None
+                and rec["sm_max_over_mean"] <= self.threshold)
+        rec["rebalanced"] = self.strategy != "static" and not skip
+        if rec["rebalanced"]:
             mig, pred = self.sim.rebalance(self.strategy)
             rec["migrations"] = mig
             rec["predicted_max_over_mean"] = pred

@@ -291,3 +291,48 @@ def test_device_work_counter_matches_kc_rule():
     expect = sum(int(oracle.kc_field(g.oracle(), t).sum()) * g.nz for t in range(7))
     assert sweeps == expect
     assert cells == 7 * 70 * 45 * 24
+
+
+def test_graph_replays_equal_direct_steps():
+    """A captured 3-step launch replayed 3 times, after 2 direct steps and
+    with a rebalance between replays, gives the same bits as 11 direct steps."""
+    from paper_1310_4218_gb300 import lb
+    g = Grid(80, 48, 32, disk=(10, 40, 1, 2, 9), k_in=11, k_out=1)
+    q = round_to_storage(gaussian_blob(80, 48, 32, (40, 24, 16), 9.0, 1e-3, 41), "f32")
+    vps = regular_blocks(80, 48, 16, 8)
+    a = make_sim([g], [q], vps)
+    a.step(11)
+    ref = a.field(0)
+    a.close()
+    b = make_sim([g], [q], vps)
+    b.step(2)
+    graph = lb.lb_graph_create(b.ctx, 3)
+    lb.lb_graph_launch(b.ctx, graph)
+    b.measure()
+    b.rebalance("greedy_spatial")
+    lb.lb_graph_launch(b.ctx, graph)
+    lb.lb_graph_launch(b.ctx, graph)
+    out = b.field(0)
+    assert b.info().step == 11
+    lb.lb_graph_destroy(b.ctx, graph)
+    b.close()
+    assert np.array_equal(out, ref)
+
+
+def test_threshold_triggered_rebalancing():
+    """With a threshold the balancer runs only when the measured SM max/mean
+    exceeds it; values are unaffected."""
+    from paper_1310_4218_gb300.schedule import Schedule
+    g = Grid(128, 128, 32, disk=(20, 20, 0, 0, 24), k_in=40, k_out=1)
+    q = round_to_storage(random_field(g, 51), "f32")
+    sim = make_sim([g], [q], regular_blocks(128, 128, 16, 16))
+    sch = Schedule(sim, 3, "auto_spatial", threshold=1e9)
+    sch.run(9)
+    assert not any(r["rebalanced"] for r in sch.history)
+    sch.threshold = 1.0
+    sch.run(3)
+    assert sch.history[-1]["rebalanced"]
+    out = sim.field(0)
+    sim.close()
+    ref, _ = oracle.run(g.oracle(), q, 12)
+    assert normwise(out, ref) <= 1e-5

@@ -40,6 +40,13 @@ def test_guillotine_tiles_with_min_side():
     assert vps == guillotine(1024, 1024, 4096, 8, 99)
 
 
+def test_guillotine_x_alignment():
+    vps = guillotine(1024, 1024, 4096, 8, 99, x_align=8)
+    assert len(vps) == 4096 and covers_exactly(vps, 1024, 1024)
+    assert all(x0 % 8 == 0 and w % 8 == 0 for (_, x0, _, w, _) in vps)
+    assert len({w for (_, _, _, w, _) in vps}) > 3 and len({h for (_, _, _, _, h) in vps}) > 10
+
+
 def test_lognormal_kc_range_and_mean():
     k = lognormal_kc(256, 256, 3, 0)
     assert k.dtype == np.int32 and k.min() >= 1 and k.max() <= 64

@@ -6,8 +6,8 @@ Names describe the workload; `get_config(name)` builds it.
 
   plain_fp64_64x64x32        64x64x32 FP64, 16 VPs of 16x16, 10 steps, static disk
   hotspot_fp32_512x512x64    512x512x64 FP32, 256 VPs of 32x32, 100 steps, moving disk
-  lognormal_fp32_1024x1024x96  1024x1024x96 FP32, 4096 guillotine VPs, 200 steps,
-                               lognormal k_c re-drawn every 50 steps
+  lognormal_fp32_1024x1024x96  1024x1024x96 FP32, 4096 guillotine VPs (x extents on
+                               8-column sectors), 200 steps, lognormal k_c re-drawn every 50 steps
   precision_2048x2048x64     2048x2048x64, FP64/FP32/BF16 storage, FP32 compute, 50 steps
   batch64_fp32               64 grids s x s x nz, s in 64..512, nz in 32..96, FP32
 """
@@ -93,7 +93,9 @@ def lognormal_fp32_1024x1024x96():
     c, s = _blob(1024, 1024, 96)
     g = GridSpec(1024, 1024, 96, 0.5, 0.5, 0.0, 0.1, "f32", "f32", False,
                  (0, 0, 0, 0, 0), 1, 1, c, s, 1e-3, 3)
-    vps = guillotine(1024, 1024, 4096, 8, subseed(3, 11))
+    # x extents on multiples of 8 columns: every VP row segment starts on a
+    # 32-byte sector (FP32), so no sector is shared by two VPs
+    vps = guillotine(1024, 1024, 4096, 8, subseed(3, 11), x_align=8)
     return Workload("lognormal_fp32_1024x1024x96", [g], vps, 200, 3, period=10,
                     kc_epoch_steps=50,
                     notes="guillotine VPs, lognormal k_c (mu=1, smoothed sigma 4) in 1..64")

@@ -19,15 +19,17 @@ def regular_blocks(nx, ny, bw, bh, grid=0):
     return vps
 
 
-def guillotine(nx, ny, nleaves, min_side, seed, grid=0):
+def guillotine(nx, ny, nleaves, min_side, seed, grid=0, x_align=1):
     """Seeded guillotine partition into `nleaves` uneven rectangles.
 
     Repeatedly take the region of largest area (ties: lowest creation id),
     cut it across its longer side (ties: cut across x, i.e. split the width)
     at a position drawn uniformly among those that leave both parts at least
-    `min_side` long.  Split number s draws its position from output s of
-    SplitMix64(seed).  The two parts get the next two creation ids.  Leaves
-    are returned in row-major order of their (y0, x0) corners.
+    `min_side` long -- for cuts across x, among the positions on multiples of
+    `x_align` columns (min_side and nx multiples of x_align keep every x
+    extent a multiple of it).  Split number s draws its position from output
+    s of SplitMix64(seed).  The two parts get the next two creation ids.
+    Leaves are returned in row-major order of their (y0, x0) corners.
     """
     heap = [(-nx * ny, 0, 0, 0, nx, ny)]
     next_id = 1
@@ -37,10 +39,11 @@ def guillotine(nx, ny, nleaves, min_side, seed, grid=0):
         negarea, rid, x0, y0, w, h = heapq.heappop(heap)
         split_w = w >= h
         length = w if split_w else h
-        npos = length - 2 * min_side + 1
+        step = x_align if split_w else 1
+        npos = (length - 2 * min_side) // step + 1
         if npos <= 0:
             raise ValueError("cannot split region %r further" % ((x0, y0, w, h),))
-        cut = min_side + int(splitmix64(seed, s) % np.uint64(npos))
+        cut = min_side + step * int(splitmix64(seed, s) % np.uint64(npos))
         s += 1
         if split_w:
             a = (x0, y0, cut, h)
