@@ -5,10 +5,12 @@ CPU-oracle baselines.
 One benchmark step = one rebalance period: `period` time steps of every VP
 (advection, k_c Thomas sweeps, store, global sum, per-VP cost stamps, grid
 barrier) in one persistent launch, then the load measurement and the
-rebalance.  The headline strategy is auto_spatial: GreedyLB's rule with the
-VPs in spatial order on the first call, RefineSwapLB after; the static
-table, the paper-order GreedyLB/RefineSwapLB schedule and the atomic queue
-are measured the same way and reported beside it.  The k_c array is
+rebalance.  The headline strategy is auto_spatial+steal: GreedyLB's rule
+with the VPs in spatial order on the first call, RefineSwapLB after, and
+processors that finish their VPs early taking the next items of the
+processor with the most left.  The static table, the paper-order
+GreedyLB/RefineSwapLB schedule, plain auto_spatial and the atomic queue are
+measured the same way and reported beside it.  The k_c array is
 re-drawn every 50 time steps as the workload prescribes.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
@@ -44,7 +46,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--period", type=int, default=10)
-    ap.add_argument("--strategy", default="auto_spatial")
+    ap.add_argument("--strategy", default="auto_spatial+steal")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--threads", type=int, default=0, help="threads per processor (0: default)")
@@ -247,10 +249,14 @@ class StrategyRun:
         from paper_1310_4218_gb300 import lb
         from paper_1310_4218_gb300.sim import Simulation
         self.lb, self.w, self.epochs, self.kc_dev = lb, w, epochs, kc_dev
+        # "<strategy>+steal": processor tables with end-of-step work stealing
+        steal = strategy.endswith("+steal")
+        strategy = strategy[:-len("+steal")] if steal else strategy
         self.P, self.strategy, self.dev, self.stream = args.period, strategy, dev, stream
         opt = lb.lb_default_options()
         opt.threads_hint = args.threads
         opt.queue_order = 0
+        opt.steal = 1 if steal else 0
         kc0 = [epochs[0][gi] for gi in range(len(w.grids))] if epochs else None
         self.sim = Simulation(w.grids, fields, w.vps, kc_arrays=kc0, options=opt, device=dev,
                               stream=stream)
@@ -426,7 +432,8 @@ def main():
     # the other assignments, measured the same way (device-resident inputs)
     compare = {}
     if not args.no_compare:
-        for st in [x for x in ("static", "auto", "queue", "auto_spatial") if x != args.strategy]:
+        for st in [x for x in ("static", "auto", "queue", "auto_spatial", "auto_spatial+steal",
+                               "static+steal") if x != args.strategy]:
             r2 = StrategyRun(w, fields, epochs, kc_dev, args, dev, stream, st)
             r2.warmup(args.warmup)
             m2 = r2.timed(args.steps)

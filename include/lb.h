@@ -134,7 +134,11 @@ typedef struct {
     int64_t barrier_timeout_ns;   /* grid-barrier wait limit (default 2 s) */
     int32_t threads_hint;         /* threads per processor for kernels that
                                      have several variants (0: default) */
-    int32_t reserved[7];          /* must be 0 */
+    int32_t steal;                /* 1: with processor tables, a processor
+                                     that finishes its VPs takes the next
+                                     work items of the processor with the
+                                     most left (default 0) */
+    int32_t reserved[6];          /* must be 0 */
 } lb_options;
 
 /* Fill *opt with the defaults listed above. */

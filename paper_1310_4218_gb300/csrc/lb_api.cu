@@ -48,6 +48,7 @@ struct lb_ctx {
     unsigned long long *d_mass_seq = nullptr;
     unsigned long long *d_sweeps = nullptr;
     long long *d_clock = nullptr;      // [step, parity] mirrored on the device
+    unsigned *d_bin_ctr = nullptr;     // [2][nbins] per-processor counters (stealing)
     long long cells = 0;               // cells of all grids
     long long cell_steps = 0;
 
@@ -204,7 +205,7 @@ static void free_ctx(lb_ctx *ctx) {
                     ctx->d_bin_start, ctx->d_bar,      ctx->d_status,    ctx->d_qhead,
                     ctx->d_vp_cycles, ctx->d_bin_busy, ctx->d_bin_smid,  ctx->d_bin_cal,
                     ctx->d_bin_mass,  ctx->d_mass_hist, ctx->d_mass_t,   ctx->d_mass_seq,
-                    ctx->d_sweeps,    ctx->d_clock};
+                    ctx->d_sweeps,    ctx->d_clock,    ctx->d_bin_ctr};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete ctx;
@@ -444,6 +445,7 @@ extern "C" lb_status lb_create(const lb_grid_desc *grids, int32_t ngrids, const 
     if (e == cudaSuccess) e = dalloc(&ctx->d_mass_seq, 1);
     if (e == cudaSuccess) e = dalloc(&ctx->d_sweeps, 1);
     if (e == cudaSuccess) e = dalloc(&ctx->d_clock, 2);
+    if (e == cudaSuccess) e = dalloc(&ctx->d_bin_ctr, 2 * (size_t)nb);
     cudaStream_t sm = ctx->stream;
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(ctx->d_grids, ctx->h_grids.data(), sizeof(GridDev) * ngrids,
@@ -501,10 +503,13 @@ static lb_status launch(lb_ctx *ctx, int nsteps, const Coef<TC> &coef) {
     p.mass_seq = ctx->d_mass_seq;
     p.sweeps = ctx->d_sweeps;
     p.dclock = ctx->d_clock;
+    p.bin_ctr = ctx->d_bin_ctr;
+    p.steal = ctx->opt.steal ? 1 : 0;
     p.coef = coef;
 
     CK(cudaMemsetAsync(ctx->d_bar, 0, 2 * sizeof(unsigned), ctx->stream));
     CK(cudaMemsetAsync(ctx->d_qhead, 0, 2 * sizeof(unsigned), ctx->stream));
+    CK(cudaMemsetAsync(ctx->d_bin_ctr, 0, 2 * sizeof(unsigned) * ctx->nbins, ctx->stream));
     cudaLaunchConfig_t cfg;
     std::memset(&cfg, 0, sizeof(cfg));
     cfg.gridDim = dim3(ctx->nbins);

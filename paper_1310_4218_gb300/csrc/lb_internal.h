@@ -67,6 +67,8 @@ struct StepParams {
     long long *mass_t;             // [kMassHist] step index of each entry
     unsigned long long *mass_seq;  // number of entries written so far
     unsigned long long *sweeps;    // cell-sweep updates performed (may be null)
+    unsigned *bin_ctr;             // [2][nbins] per-processor item counters (stealing)
+    int32_t steal;                 // 1: processors that run out take others' items
     long long *dclock;             // [0] step index, [1] buffer parity: read at start
                                    // instead of t0/parity0, advanced at the end (may be null)
     Coef<TC> coef;

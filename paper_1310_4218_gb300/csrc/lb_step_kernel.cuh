@@ -517,6 +517,48 @@ __device__ __forceinline__ void reduce_mass(const StepParams<TC> &p, long long t
     }
 }
 
+// ------------------------------------------------------------ work stealing
+// Table mode with stealing: a processor's warps take items from its own
+// counter; once it runs dry they scan every processor's remaining count
+// (one lane per processor, 32 at a time) and take the next item of the
+// processor with the most left.  Each counter hands out every index once,
+// so no item runs twice.  Returns the global item index, or -1 when no
+// processor has work left.
+template <class TC>
+__device__ __forceinline__ int pop_with_stealing(const StepParams<TC> &p, int par, int bin,
+                                                 int lane) {
+    unsigned *ctr = p.bin_ctr + (size_t)par * p.nbins;
+    int c = 0;
+    if (lane == 0) c = (int)atomicAdd(&ctr[bin], 1u);
+    c = __shfl_sync(0xffffffffu, c, 0);
+    if (c < p.bin_start[bin + 1] - p.bin_start[bin]) return p.bin_start[bin] + c;
+    for (int attempt = 0; attempt < 4 * p.nbins + 8; ++attempt) {
+        int best_rem = 0, best_v = -1;
+        for (int base = 0; base < p.nbins; base += kWarp) {
+            const int v = base + lane;
+            int rem = 0;
+            if (v < p.nbins) {
+                const int len = p.bin_start[v + 1] - p.bin_start[v];
+                rem = len - (int)*(volatile unsigned *)&ctr[v];
+            }
+            int vv = v;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const int r2 = __shfl_xor_sync(0xffffffffu, rem, o);
+                const int v2 = __shfl_xor_sync(0xffffffffu, vv, o);
+                if (r2 > rem || (r2 == rem && v2 < vv)) { rem = r2; vv = v2; }
+            }
+            if (rem > best_rem) { best_rem = rem; best_v = vv; }
+        }
+        if (best_rem <= 0) return -1;
+        int got = 0;
+        if (lane == 0) got = (int)atomicAdd(&ctr[best_v], 1u);
+        got = __shfl_sync(0xffffffffu, got, 0);
+        if (got < p.bin_start[best_v + 1] - p.bin_start[best_v]) return p.bin_start[best_v] + got;
+    }
+    return -1;
+}
+
 // ------------------------------------------------------------ the kernel
 template <class TS, class TC, int NZ, bool EXACT, int NZLO, int THREADS, bool SPLIT>
 __global__ void __launch_bounds__(THREADS, 1)
@@ -555,6 +597,8 @@ lb_step_kernel(const __grid_constant__ StepParams<TC> p) {
             s_tend = 0ull;
             s_t0 = (unsigned long long)clock64();
             if (bin == 0) p.qhead[(s + 1) & 1] = 0u;
+            // next step's counter: nobody touches it before this step's barrier
+            if (p.steal) p.bin_ctr[(size_t)((s + 1) & 1) * p.nbins + bin] = 0u;
         }
         if (do_mass)
             for (int n = threadIdx.x; n < kWarps * p.ngrids; n += THREADS) s_mass[n] = 0.0;
@@ -564,10 +608,15 @@ lb_step_kernel(const __grid_constant__ StepParams<TC> p) {
         int cur_grid = -1;
         for (;;) {
             int c = 0;
-            if (lane == 0)
-                c = p.queue_mode ? (int)atomicAdd(&p.qhead[s & 1], 1u) : atomicAdd(&s_ctr, 1);
-            c = __shfl_sync(0xffffffffu, c, 0) + ibeg;
-            if (c >= iend) break;
+            if (p.steal && !p.queue_mode) {
+                c = pop_with_stealing(p, s & 1, bin, lane);
+                if (c < 0) break;
+            } else {
+                if (lane == 0)
+                    c = p.queue_mode ? (int)atomicAdd(&p.qhead[s & 1], 1u) : atomicAdd(&s_ctr, 1);
+                c = __shfl_sync(0xffffffffu, c, 0) + ibeg;
+                if (c >= iend) break;
+            }
             const int2 it = p.items[c];
             const VPDev vp = p.vps[it.x];
             const GridDev &g = p.grids[vp.grid];

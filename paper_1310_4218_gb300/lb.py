@@ -54,7 +54,7 @@ class lb_options(ctypes.Structure):
                 ("mass_every", ctypes.c_int32), ("device_balancer", ctypes.c_int32),
                 ("ema_alpha", ctypes.c_double), ("refine_tol", ctypes.c_double),
                 ("barrier_timeout_ns", ctypes.c_int64), ("threads_hint", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 7)]
+                ("steal", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
 
 
 class lb_info(ctypes.Structure):

@@ -75,14 +75,18 @@ def test_general_advection(cx, cy, cz):
 
 
 @pytest.mark.parametrize("strategy", ["static", "greedy", "refine_swap", "queue", "auto",
-                                      "greedy_spatial", "auto_spatial"])
+                                      "greedy_spatial", "auto_spatial", "static+steal",
+                                      "auto_spatial+steal"])
 def test_strategies_give_identical_fields(strategy):
     """Balancing changes only where columns run, never their values: every
-    strategy yields the same bits, and they match the oracle."""
+    strategy (with or without work stealing) yields the same bits, and they
+    match the oracle."""
     g = Grid(64, 48, 32, disk=(10, 10, 1, 1, 12), k_in=20, k_out=1)
     q = round_to_storage(gaussian_blob(64, 48, 32, (32, 24, 16), 10.0, 1e-3, 5), "f32")
     vps = guillotine(64, 48, 24, 4, 17)
-    sim = make_sim([g], [q], vps, queue_order=1)
+    steal = strategy.endswith("+steal")
+    strategy = strategy.replace("+steal", "")
+    sim = make_sim([g], [q], vps, queue_order=1, steal=1 if steal else 0)
     sim.step(3)
     sim.measure()
     sim.rebalance(strategy)
