@@ -34,12 +34,19 @@ def bin_loads(costs, assign, nbins):
     return loads
 
 
+def total_load(loads):
+    """Sum of the per-bin loads, bins in increasing id order: the numerator
+    of the mean load per processor that RefineSwapLB balances toward
+    (Sec. VI-B).  Equal to the sum of all costs up to rounding."""
+    total = 0.0
+    for x in loads:
+        total += x
+    return total
+
+
 def max_over_mean(costs, assign, nbins):
     loads = bin_loads(costs, assign, nbins)
-    total = 0.0
-    for c in costs:
-        total += c
-    mean = total / nbins
+    mean = total_load(loads) / nbins
     return max(loads) / mean if mean > 0 else 1.0
 
 
@@ -78,7 +85,7 @@ def greedy_ordered(costs, nbins, order):
 def refine_swap(costs, assign, nbins, tol=0.05, max_iter=None):
     """RefineSwapLB, as read here (the paper gives no constants):
 
-    threshold T = (1 + tol) * mean, mean = (sum of costs in id order) / nbins.
+    threshold T = (1 + tol) * mean, mean = total_load(bin loads) / nbins.
     Repeat, at most 4 * nvps times:
       1. Stop if the largest bin load is <= T.
       2. P = most loaded bin (ties: lowest id).
@@ -99,10 +106,7 @@ def refine_swap(costs, assign, nbins, tol=0.05, max_iter=None):
     nv = len(costs)
     assign = list(assign)
     loads = bin_loads(costs, assign, nbins)
-    total = 0.0
-    for c in costs:
-        total += c
-    thr = (1.0 + tol) * (total / nbins)
+    thr = (1.0 + tol) * (total_load(loads) / nbins)
     members = [[] for _ in range(nbins)]
     for v, b in enumerate(assign):
         members[b].append(v)

@@ -23,12 +23,17 @@ void bin_loads(const std::vector<double> &costs, const std::vector<int> &assign,
     for (size_t v = 0; v < assign.size(); ++v) loads[assign[v]] += costs[v];
 }
 
+// Sum of the processor loads, processors in id order.
+double total_load(const std::vector<double> &loads) {
+    double total = 0.0;
+    for (double x : loads) total += x;
+    return total;
+}
+
 double max_over_mean(const std::vector<double> &costs, const std::vector<int> &assign, int nbins) {
     std::vector<double> loads;
     bin_loads(costs, assign, nbins, loads);
-    double total = 0.0;
-    for (double c : costs) total += c;
-    double mean = total / nbins;
+    double mean = total_load(loads) / nbins;
     double mx = *std::max_element(loads.begin(), loads.end());
     return mean > 0.0 ? mx / mean : 1.0;
 }
@@ -83,7 +88,7 @@ void greedy_ordered(const std::vector<double> &costs, int nbins, const std::vect
 // RefineSwapLB (Sec. VI-B): move objects off the most loaded processor
 // toward the mean; swap when no single move fits.  The paper gives no
 // constants; the reading implemented:
-//   T = (1 + tol) * mean, mean = (sum of costs in id order) / nbins.
+//   T = (1 + tol) * mean, mean = total_load(loads) / nbins.
 //   Repeat at most 4*nvps times:
 //     stop if max load <= T; P = most loaded (ties: lowest id);
 //     for Q in (load asc, id asc), Q != P:
@@ -101,9 +106,7 @@ void refine_swap(const std::vector<double> &costs, const std::vector<int> &assig
     assign = assign_in;
     std::vector<double> loads;
     bin_loads(costs, assign, nbins, loads);
-    double total = 0.0;
-    for (double c : costs) total += c;
-    const double thr = (1.0 + tol) * (total / nbins);
+    const double thr = (1.0 + tol) * (total_load(loads) / nbins);
     std::vector<std::vector<int>> members(nbins);
     for (int v = 0; v < nv; ++v) members[assign[v]].push_back(v);
     auto erase = [](std::vector<int> &vec, int x) {

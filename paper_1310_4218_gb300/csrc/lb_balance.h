@@ -8,6 +8,7 @@ namespace lbk {
 void static_blocks(int nvps, int nbins, std::vector<int> &out);
 void bin_loads(const std::vector<double> &costs, const std::vector<int> &assign, int nbins,
                std::vector<double> &loads);
+double total_load(const std::vector<double> &loads);
 double max_over_mean(const std::vector<double> &costs, const std::vector<int> &assign, int nbins);
 int migrations(const std::vector<int> &a, const std::vector<int> &b);
 void greedy(const std::vector<double> &costs, int nbins, std::vector<int> &out);
