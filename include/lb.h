@@ -33,7 +33,7 @@
  *   - Device-side failures (grid-barrier timeout, non-finite sum) are
  *     recorded in a device status word and reported by the next call that
  *     synchronises (lb_measure_loads, lb_mass, lb_mass_history,
- *     lb_checkpoint, lb_sync).
+ *     lb_checkpoint, lb_sync, lb_get_costs, lb_balance_history).
  *   - lb_last_error(ctx) returns a text for the last failure of that ctx.
  *   - A ctx is not thread-safe; one host thread drives it at a time.
  *   - Work is issued on the stream given to lb_create (a cudaStream_t
@@ -255,6 +255,62 @@ lb_status lb_current_field(lb_ctx *ctx, int32_t grid, void **dev_ptr);
 lb_status lb_graph_create(lb_ctx *ctx, int32_t nsteps, void **graph_exec);
 lb_status lb_graph_launch(lb_ctx *ctx, void *graph_exec);
 lb_status lb_graph_destroy(lb_ctx *ctx, void *graph_exec);
+
+/*
+ * Device-side measurement and rebalancing: the same cost average and the
+ * same balancers as lb_measure_loads / lb_rebalance, run as kernels on the
+ * ctx stream.  Both calls only enqueue work (no synchronisation, no host
+ * copies), so a rebalance period -- lb_step, lb_device_measure,
+ * lb_device_rebalance -- runs back to back on the GPU and can be captured
+ * in one CUDA graph (lb_graph_create_periods).
+ *
+ * lb_device_measure folds the loads accumulated since the previous
+ * measurement into the per-VP cost average (Sec. V) with exactly
+ * lb_measure_loads's FP64 arithmetic, and records the period's SM busy
+ * max/mean.  With no step since the previous measurement it changes
+ * nothing and the next synchronising call returns LB_ESTATE.
+ *
+ * lb_device_rebalance remaps VPs from the device cost average (Sec. VI)
+ * and rewrites the processor tables in device memory; the next step uses
+ * them.  strategy: LB_STATIC, LB_GREEDY, LB_REFINE_SWAP, LB_AUTO,
+ * LB_GREEDY_SPATIAL or LB_AUTO_SPATIAL (LB_AUTO* decide on the device, from
+ * the number of table rebalances so far).  For equal costs and current
+ * assignment the new assignment equals lb_rebalance's bit for bit.  Its
+ * migrations and predicted max/mean are recorded in the balance history.
+ * Without costs (never measured or set) the next synchronising call
+ * returns LB_ESTATE.  Not available in LB_ATOMIC_QUEUE mode (LB_ESTATE) or
+ * for more than 8192 VPs or 1024 processors (LB_EINVAL).
+ *
+ * Host calls that read or change costs or the assignment (lb_measure_loads,
+ * lb_rebalance, lb_set_costs, lb_get_assignment, lb_set_assignment,
+ * lb_checkpoint, lb_get_info) first wait for pending device-side
+ * rebalancing work and see its result.
+ */
+lb_status lb_device_measure(lb_ctx *ctx);
+lb_status lb_device_rebalance(lb_ctx *ctx, int32_t strategy);
+
+/* Per-VP costs, ns per step (host double[nvps] each, may be NULL): the
+   cost average balancers use and the last measurement.  Synchronises. */
+lb_status lb_get_costs(lb_ctx *ctx, double *avg_ns, double *last_ns);
+
+/*
+ * The last *n (at most max, at most 1024 kept) device rebalances, oldest
+ * first, 8 doubles each: step index, strategy applied (LB_AUTO* resolved),
+ * migrations, predicted max/mean processor load, measured SM busy max/mean
+ * of the preceding measurement, granularity floor max(max cost, mean)/mean,
+ * RefineSwapLB iterations, 0.  rows: host double[max*8].  Synchronises.
+ */
+lb_status lb_balance_history(lb_ctx *ctx, double *rows, int32_t max, int32_t *n);
+
+/*
+ * One executable graph of nperiods rebalance periods (Fig. 2's loop): each
+ * period is one persistent launch of nsteps steps, lb_device_measure and
+ * lb_device_rebalance(strategy).  Replay with lb_graph_launch (the ctx's
+ * step counters advance by nsteps*nperiods); destroy with
+ * lb_graph_destroy.  Same availability rules as lb_device_rebalance.
+ */
+lb_status lb_graph_create_periods(lb_ctx *ctx, int32_t nsteps, int32_t strategy,
+                                  int32_t nperiods, void **graph_exec);
 
 /* Wait for all work of the ctx; report a pending device-side error. */
 lb_status lb_sync(lb_ctx *ctx);

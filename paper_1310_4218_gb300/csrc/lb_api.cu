@@ -49,6 +49,20 @@ struct lb_ctx {
     unsigned long long *d_sweeps = nullptr;
     long long *d_clock = nullptr;      // [step, parity] mirrored on the device
     unsigned *d_bin_ctr = nullptr;     // [2][nbins] per-processor counters (stealing)
+    // device balancer: mirrors of cost / assign and its own state
+    double *d_cost = nullptr;
+    double *d_last = nullptr;
+    int32_t *d_assign = nullptr;
+    int32_t *d_order = nullptr;
+    int32_t *d_spatial = nullptr;
+    int32_t *d_nchunks = nullptr;
+    long long *d_bstate = nullptr;
+    double *d_pend = nullptr;
+    double *d_bhist = nullptr;
+    unsigned *d_ticket = nullptr;
+    bool dev_newer = false;            // device balancer state newer than the host copy
+    std::string devbal_off;            // why the device balancer is unavailable ("" = available)
+    double fallback_npc = 1.0;
     long long cells = 0;               // cells of all grids
     long long cell_steps = 0;
 
@@ -59,13 +73,18 @@ struct lb_ctx {
     bool queue_mode = false;
     int rebalances = 0;
     std::vector<double> cost;          // per-VP cost average, ns per step
+    std::vector<double> last;          // per-VP cost of the last measurement
     bool have_costs = false;
     long long step = 0;
     int parity = 0;
     long long steps_since_measure = 0;
     Coef<float> coef_f;
     Coef<double> coef_d;
-    std::map<cudaGraphExec_t, int> graph_steps;   // graphs made by lb_graph_create
+    struct GraphRec {
+        int steps;      // time steps per replay
+        bool balances;  // replays run the device balancer
+    };
+    std::map<cudaGraphExec_t, GraphRec> graph_steps;   // graphs made for this ctx
     std::string err;
 };
 
@@ -134,8 +153,53 @@ static lb_status check_status(lb_ctx *ctx) {
         if (st == LB_ETIMEOUT)
             return fail(ctx, LB_ETIMEOUT, "grid barrier wait exceeded barrier_timeout_ns");
         if (st == LB_ENUMERIC) return fail(ctx, LB_ENUMERIC, "global sum is not finite");
+        if (st == LB_ESTATE)
+            return fail(ctx, LB_ESTATE,
+                        "device balancer: no step since the last measurement, or no costs yet");
         return fail(ctx, (lb_status)st, "device reported an error");
     }
+    return LB_OK;
+}
+
+// Host copies of what the device balancer owns: costs, assignment and its
+// state words.  The device copy is newer after lb_device_* calls and graph
+// replays that balance (pull before the host reads), the host copy after
+// every host-side change (push).
+static lb_status pull_state(lb_ctx *ctx) {
+    if (!ctx->dev_newer) return LB_OK;
+    const size_t nv = ctx->vps.size();
+    long long stw[kStWords];
+    std::vector<int32_t> a(nv);
+    CK(cudaMemcpyAsync(ctx->cost.data(), ctx->d_cost, sizeof(double) * nv, cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    CK(cudaMemcpyAsync(ctx->last.data(), ctx->d_last, sizeof(double) * nv, cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    CK(cudaMemcpyAsync(a.data(), ctx->d_assign, sizeof(int32_t) * nv, cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    CK(cudaMemcpyAsync(stw, ctx->d_bstate, sizeof(stw), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->assign.assign(a.begin(), a.end());
+    ctx->have_costs = stw[kStHave] != 0;
+    ctx->rebalances = (int)stw[kStRebal];
+    ctx->steps_since_measure = ctx->step - stw[kStMeasStep];
+    ctx->strategy = (int)stw[kStStrategy];
+    ctx->dev_newer = false;
+    return LB_OK;
+}
+
+static lb_status push_state(lb_ctx *ctx) {
+    const size_t nv = ctx->vps.size();
+    std::vector<int32_t> a(ctx->assign.begin(), ctx->assign.end());
+    long long stw[4] = {ctx->have_costs ? 1 : 0, ctx->rebalances,
+                        ctx->step - ctx->steps_since_measure, ctx->strategy};
+    CK(cudaMemcpyAsync(ctx->d_cost, ctx->cost.data(), sizeof(double) * nv, cudaMemcpyHostToDevice,
+                       ctx->stream));
+    CK(cudaMemcpyAsync(ctx->d_last, ctx->last.data(), sizeof(double) * nv, cudaMemcpyHostToDevice,
+                       ctx->stream));
+    CK(cudaMemcpyAsync(ctx->d_assign, a.data(), sizeof(int32_t) * nv, cudaMemcpyHostToDevice,
+                       ctx->stream));
+    CK(cudaMemcpyAsync(ctx->d_bstate, stw, sizeof(stw), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
     return LB_OK;
 }
 
@@ -197,7 +261,7 @@ static lb_status upload_items(lb_ctx *ctx) {
     CK(cudaMemcpyAsync(ctx->d_bin_start, start.data(), sizeof(int32_t) * start.size(),
                        cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
-    return LB_OK;
+    return push_state(ctx);
 }
 
 static void free_ctx(lb_ctx *ctx) {
@@ -205,7 +269,10 @@ static void free_ctx(lb_ctx *ctx) {
                     ctx->d_bin_start, ctx->d_bar,      ctx->d_status,    ctx->d_qhead,
                     ctx->d_vp_cycles, ctx->d_bin_busy, ctx->d_bin_smid,  ctx->d_bin_cal,
                     ctx->d_bin_mass,  ctx->d_mass_hist, ctx->d_mass_t,   ctx->d_mass_seq,
-                    ctx->d_sweeps,    ctx->d_clock,    ctx->d_bin_ctr};
+                    ctx->d_sweeps,    ctx->d_clock,    ctx->d_bin_ctr,   ctx->d_cost,
+                    ctx->d_last,      ctx->d_assign,   ctx->d_order,     ctx->d_spatial,
+                    ctx->d_nchunks,   ctx->d_bstate,   ctx->d_pend,      ctx->d_bhist,
+                    ctx->d_ticket};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete ctx;
@@ -425,6 +492,7 @@ extern "C" lb_status lb_create(const lb_grid_desc *grids, int32_t ngrids, const 
     }
     static_blocks(nvps, ctx->nbins, ctx->assign);
     ctx->cost.assign(nvps, 0.0);
+    ctx->last.assign(nvps, 0.0);
 
     const int nb = ctx->nbins;
     e = dalloc(&ctx->d_grids, ngrids);
@@ -446,6 +514,18 @@ extern "C" lb_status lb_create(const lb_grid_desc *grids, int32_t ngrids, const 
     if (e == cudaSuccess) e = dalloc(&ctx->d_sweeps, 1);
     if (e == cudaSuccess) e = dalloc(&ctx->d_clock, 2);
     if (e == cudaSuccess) e = dalloc(&ctx->d_bin_ctr, 2 * (size_t)nb);
+    if (e == cudaSuccess) e = dalloc(&ctx->d_cost, nvps);
+    if (e == cudaSuccess) e = dalloc(&ctx->d_last, nvps);
+    if (e == cudaSuccess) e = dalloc(&ctx->d_assign, nvps);
+    if (e == cudaSuccess) e = dalloc(&ctx->d_order, nvps);
+    if (e == cudaSuccess) e = dalloc(&ctx->d_spatial, nvps);
+    if (e == cudaSuccess) e = dalloc(&ctx->d_nchunks, nvps);
+    if (e == cudaSuccess) e = dalloc(&ctx->d_bstate, kStWords);
+    if (e == cudaSuccess) e = dalloc(&ctx->d_pend, 2);
+    if (e == cudaSuccess) e = dalloc(&ctx->d_bhist, (size_t)kBalHist * kBalHistCols);
+    if (e == cudaSuccess) e = dalloc(&ctx->d_ticket, 1);
+    const std::vector<int> sp = spatial_order(ctx);
+    std::vector<int32_t> sp32(sp.begin(), sp.end()), nch(ctx->vp_nchunks.begin(), ctx->vp_nchunks.end());
     cudaStream_t sm = ctx->stream;
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(ctx->d_grids, ctx->h_grids.data(), sizeof(GridDev) * ngrids,
@@ -460,10 +540,29 @@ extern "C" lb_status lb_create(const lb_grid_desc *grids, int32_t ngrids, const 
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_clock, 0, 2 * sizeof(long long), sm);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_bin_cal, 0, sizeof(long long) * 4 * nb, sm);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_bin_smid, 0xff, sizeof(int32_t) * nb, sm);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(ctx->d_spatial, sp32.data(), sizeof(int32_t) * nvps, cudaMemcpyHostToDevice, sm);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(ctx->d_nchunks, nch.data(), sizeof(int32_t) * nvps, cudaMemcpyHostToDevice, sm);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_bstate, 0, sizeof(long long) * kStWords, sm);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_pend, 0, sizeof(double) * 2, sm);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_ticket, 0, sizeof(unsigned), sm);
     if (e == cudaSuccess) e = cudaStreamSynchronize(sm);
     if (e != cudaSuccess) {
         ctx->err = std::string("device tables: ") + cudaGetErrorString(e);
         return bail(LB_ECUDA);
+    }
+    {
+        int khz = 0;
+        cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, ctx->device);
+        ctx->fallback_npc = khz > 0 ? 1e6 / khz : 1.0;
+    }
+    if (nvps > kDevBalMaxVps) ctx->devbal_off = "more than " + std::to_string(kDevBalMaxVps) + " VPs";
+    else if (nb > kDevBalMaxBins) ctx->devbal_off = "more than " + std::to_string(kDevBalMaxBins) + " processors";
+    else if (ctx->nsm > kDevBalMaxSms) ctx->devbal_off = "more SMs than the device balancer handles";
+    else if (dev_balance_init() != cudaSuccess) {
+        cudaGetLastError();
+        ctx->devbal_off = "device balancer kernel needs more shared memory than the device offers";
     }
     st = upload_items(ctx);
     if (st != LB_OK) return bail(st);
@@ -570,7 +669,7 @@ extern "C" lb_status lb_graph_create(lb_ctx *ctx, int32_t nsteps, void **graph_e
     e = cudaGraphInstantiate(&exec, graph, 0);
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) return fail(ctx, LB_ECUDA, std::string("instantiate: ") + cudaGetErrorString(e));
-    ctx->graph_steps[exec] = nsteps;
+    ctx->graph_steps[exec] = lb_ctx::GraphRec{nsteps, false};
     *graph_exec = exec;
     return LB_OK;
 }
@@ -580,11 +679,12 @@ extern "C" lb_status lb_graph_launch(lb_ctx *ctx, void *graph_exec) {
     auto it = ctx->graph_steps.find((cudaGraphExec_t)graph_exec);
     if (it == ctx->graph_steps.end()) return fail(ctx, LB_EINVAL, "graph was not made for this ctx");
     CK(cudaGraphLaunch((cudaGraphExec_t)graph_exec, ctx->stream));
-    const int n = it->second;
+    const int n = it->second.steps;
     ctx->step += n;
     ctx->cell_steps += ctx->cells * n;
     ctx->parity ^= (n & 1);
     ctx->steps_since_measure += n;
+    if (it->second.balances) ctx->dev_newer = true;
     return LB_OK;
 }
 
@@ -592,6 +692,149 @@ extern "C" lb_status lb_graph_destroy(lb_ctx *ctx, void *graph_exec) {
     if (!ctx || !graph_exec) return fail(ctx, LB_EINVAL, "lb_graph_destroy: bad arguments");
     ctx->graph_steps.erase((cudaGraphExec_t)graph_exec);
     CK(cudaGraphExecDestroy((cudaGraphExec_t)graph_exec));
+    return LB_OK;
+}
+
+// ------------------------------------------------------------------ device balancer
+static DevBal make_devbal(lb_ctx *ctx) {
+    DevBal p;
+    std::memset(&p, 0, sizeof(p));
+    p.nvps = (int)ctx->vps.size();
+    p.nbins = ctx->nbins;
+    p.nsm = ctx->nsm;
+    p.nitems = ctx->nitems;
+    p.ema_alpha = ctx->opt.ema_alpha;
+    p.refine_tol = ctx->opt.refine_tol;
+    p.fallback_ns_per_cycle = ctx->fallback_npc;
+    p.vp_cycles = ctx->d_vp_cycles;
+    p.bin_busy = ctx->d_bin_busy;
+    p.bin_smid = ctx->d_bin_smid;
+    p.bin_cal = ctx->d_bin_cal;
+    p.dclock = ctx->d_clock;
+    p.status = ctx->d_status;
+    p.ticket = ctx->d_ticket;
+    p.cost = ctx->d_cost;
+    p.last = ctx->d_last;
+    p.assign = ctx->d_assign;
+    p.order = ctx->d_order;
+    p.spatial = ctx->d_spatial;
+    p.nchunks = ctx->d_nchunks;
+    p.state = ctx->d_bstate;
+    p.pend = ctx->d_pend;
+    p.hist = ctx->d_bhist;
+    p.items = ctx->d_items;
+    p.bin_start = ctx->d_bin_start;
+    return p;
+}
+
+static bool table_strategy(int s) {
+    return s == LB_STATIC || s == LB_GREEDY || s == LB_REFINE_SWAP || s == LB_AUTO ||
+           s == LB_GREEDY_SPATIAL || s == LB_AUTO_SPATIAL;
+}
+
+static lb_status devbal_check(lb_ctx *ctx, int strategy, bool need_strategy) {
+    if (!ctx->devbal_off.empty())
+        return fail(ctx, LB_EINVAL, "device balancer unavailable: " + ctx->devbal_off);
+    if (need_strategy && !table_strategy(strategy))
+        return fail(ctx, LB_EINVAL, "device balancer: strategy must build a processor table");
+    if (need_strategy && ctx->queue_mode)
+        return fail(ctx, LB_ESTATE, "device balancer: ctx is in atomic-queue mode (leave it with lb_rebalance)");
+    return LB_OK;
+}
+
+extern "C" lb_status lb_device_measure(lb_ctx *ctx) {
+    if (!ctx) return fail(nullptr, LB_EINVAL, "ctx is NULL");
+    lb_status st = devbal_check(ctx, 0, false);
+    if (st != LB_OK) return st;
+    CK(dev_measure(make_devbal(ctx), ctx->stream));
+    ctx->dev_newer = true;
+    return LB_OK;
+}
+
+extern "C" lb_status lb_device_rebalance(lb_ctx *ctx, int32_t strategy) {
+    if (!ctx) return fail(nullptr, LB_EINVAL, "ctx is NULL");
+    lb_status st = devbal_check(ctx, strategy, true);
+    if (st != LB_OK) return st;
+    CK(dev_rebalance(make_devbal(ctx), strategy, ctx->stream));
+    ctx->dev_newer = true;
+    return LB_OK;
+}
+
+extern "C" lb_status lb_get_costs(lb_ctx *ctx, double *avg_ns, double *last_ns) {
+    if (!ctx) return fail(nullptr, LB_EINVAL, "ctx is NULL");
+    lb_status st = check_status(ctx);
+    if (st != LB_OK) return st;
+    st = pull_state(ctx);
+    if (st != LB_OK) return st;
+    for (size_t v = 0; v < ctx->vps.size(); ++v) {
+        if (avg_ns) avg_ns[v] = ctx->cost[v];
+        if (last_ns) last_ns[v] = ctx->last[v];
+    }
+    return LB_OK;
+}
+
+extern "C" lb_status lb_balance_history(lb_ctx *ctx, double *rows, int32_t max, int32_t *n) {
+    if (!ctx) return fail(nullptr, LB_EINVAL, "ctx is NULL");
+    lb_status st = check_status(ctx);
+    if (st != LB_OK) return st;
+    long long stw[kStWords];
+    CK(cudaMemcpyAsync(stw, ctx->d_bstate, sizeof(stw), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    const long long written = stw[kStHist];
+    const long long cnt = std::min<long long>(std::min<long long>(written, kBalHist), std::max(max, 0));
+    if (n) *n = (int32_t)cnt;
+    if (cnt == 0 || !rows) return LB_OK;
+    std::vector<double> h((size_t)kBalHist * kBalHistCols);
+    CK(cudaMemcpyAsync(h.data(), ctx->d_bhist, sizeof(double) * h.size(), cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (long long i = 0; i < cnt; ++i) {
+        const long long r = (written - cnt + i) % kBalHist;
+        for (int c = 0; c < kBalHistCols; ++c) rows[i * kBalHistCols + c] = h[(size_t)r * kBalHistCols + c];
+    }
+    return LB_OK;
+}
+
+extern "C" lb_status lb_graph_create_periods(lb_ctx *ctx, int32_t nsteps, int32_t strategy,
+                                             int32_t nperiods, void **graph_exec) {
+    if (!ctx || !graph_exec || nsteps < 1 || nperiods < 1)
+        return fail(ctx, LB_EINVAL, "lb_graph_create_periods: bad arguments");
+    *graph_exec = nullptr;
+    lb_status st = devbal_check(ctx, strategy, true);
+    if (st != LB_OK) return st;
+    if ((long long)nsteps * nperiods > 0x7fffffffLL)
+        return fail(ctx, LB_EINVAL, "lb_graph_create_periods: too many steps");
+    CK(cudaStreamSynchronize(ctx->stream));
+    cudaStream_t cap = nullptr;
+    CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    cudaStream_t own = ctx->stream;
+    cudaGraph_t graph = nullptr;
+    const DevBal db = make_devbal(ctx);
+    cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        ctx->stream = cap;
+        for (int k = 0; k < nperiods && st == LB_OK && e == cudaSuccess; ++k) {
+            st = ctx->compute == LB_F64 ? launch<double>(ctx, nsteps, ctx->coef_d)
+                                        : launch<float>(ctx, nsteps, ctx->coef_f);
+            if (st == LB_OK) e = dev_measure(db, cap);
+            if (st == LB_OK && e == cudaSuccess) e = dev_rebalance(db, strategy, cap);
+        }
+        ctx->stream = own;
+        cudaError_t e2 = cudaStreamEndCapture(cap, &graph);
+        if (e == cudaSuccess) e = e2;
+    }
+    cudaStreamDestroy(cap);
+    if (st != LB_OK || e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        if (st != LB_OK) return st;
+        return fail(ctx, LB_ECUDA, std::string("capture: ") + cudaGetErrorString(e));
+    }
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return fail(ctx, LB_ECUDA, std::string("instantiate: ") + cudaGetErrorString(e));
+    ctx->graph_steps[exec] = lb_ctx::GraphRec{nsteps * nperiods, true};
+    *graph_exec = exec;
     return LB_OK;
 }
 
@@ -607,6 +850,8 @@ extern "C" lb_status lb_measure_loads(lb_ctx *ctx, double *vp_cost_ns, double *s
     lb_status st = check_status(ctx);
     if (st != LB_OK) return st;
     if (nsm) *nsm = ctx->nsm;
+    st = pull_state(ctx);
+    if (st != LB_OK) return st;
     if (ctx->steps_since_measure <= 0) return fail(ctx, LB_ESTATE, "no step since the last measurement");
     const int nv = (int)ctx->vps.size(), nb = ctx->nbins;
     std::vector<unsigned long long> cyc(nv), busy(nb);
@@ -644,6 +889,7 @@ extern "C" lb_status lb_measure_loads(lb_ctx *ctx, double *vp_cost_ns, double *s
     for (int v = 0; v < nv; ++v) {
         double c = (double)cyc[v] * ns_per_cycle / steps;
         ctx->cost[v] = ctx->have_costs ? a * c + (1.0 - a) * ctx->cost[v] : c;
+        ctx->last[v] = c;
         if (vp_cost_ns) vp_cost_ns[v] = c;
     }
     ctx->have_costs = true;
@@ -653,7 +899,7 @@ extern "C" lb_status lb_measure_loads(lb_ctx *ctx, double *vp_cost_ns, double *s
             if (sm[b] >= 0 && sm[b] < ctx->nsm) sm_busy_ns[sm[b]] += (double)busy[b] * ns_per_cycle / steps;
     }
     ctx->steps_since_measure = 0;
-    return LB_OK;
+    return push_state(ctx);
 }
 
 // ------------------------------------------------------------------ balance
@@ -693,14 +939,20 @@ extern "C" lb_status lb_set_costs(lb_ctx *ctx, const double *costs) {
     if (!ctx || !costs) return fail(ctx, LB_EINVAL, "lb_set_costs: bad arguments");
     for (size_t v = 0; v < ctx->vps.size(); ++v)
         if (!std::isfinite(costs[v]) || costs[v] < 0) return fail(ctx, LB_EINVAL, "costs must be finite and >= 0");
+    lb_status st = pull_state(ctx);
+    if (st != LB_OK) return st;
     ctx->cost.assign(costs, costs + ctx->vps.size());
     ctx->have_costs = true;
-    return LB_OK;
+    return push_state(ctx);
 }
 
 extern "C" lb_status lb_rebalance(lb_ctx *ctx, int32_t strategy, int32_t *mig, double *pred) {
     if (!ctx) return fail(nullptr, LB_EINVAL, "ctx is NULL");
     if (strategy < LB_STATIC || strategy > LB_AUTO_SPATIAL) return fail(ctx, LB_EINVAL, "unknown strategy");
+    {
+        lb_status ps = pull_state(ctx);
+        if (ps != LB_OK) return ps;
+    }
     if (strategy == LB_AUTO) strategy = ctx->rebalances == 0 ? LB_GREEDY : LB_REFINE_SWAP;
     if (strategy == LB_AUTO_SPATIAL)
         strategy = ctx->rebalances == 0 ? LB_GREEDY_SPATIAL : LB_REFINE_SWAP;
@@ -742,6 +994,8 @@ extern "C" lb_status lb_rebalance(lb_ctx *ctx, int32_t strategy, int32_t *mig, d
 
 extern "C" lb_status lb_get_assignment(lb_ctx *ctx, int32_t *vp_to_proc, int32_t *nprocs) {
     if (!ctx) return fail(nullptr, LB_EINVAL, "ctx is NULL");
+    lb_status st = pull_state(ctx);
+    if (st != LB_OK) return st;
     if (vp_to_proc)
         for (size_t v = 0; v < ctx->assign.size(); ++v) vp_to_proc[v] = ctx->assign[v];
     if (nprocs) *nprocs = ctx->nbins;
@@ -753,6 +1007,8 @@ extern "C" lb_status lb_set_assignment(lb_ctx *ctx, const int32_t *vp_to_proc) {
     for (size_t v = 0; v < ctx->vps.size(); ++v)
         if (vp_to_proc[v] < 0 || vp_to_proc[v] >= ctx->nbins)
             return fail(ctx, LB_EINVAL, "processor index out of range");
+    lb_status st = pull_state(ctx);
+    if (st != LB_OK) return st;
     ctx->assign.assign(vp_to_proc, vp_to_proc + ctx->vps.size());
     ctx->queue_mode = false;
     ctx->strategy = LB_STATIC;
@@ -844,6 +1100,8 @@ static const char kMagic[8] = {'L', 'B', 'C', 'K', 'P', 'T', '0', '1'};
 extern "C" lb_status lb_checkpoint(lb_ctx *ctx, const char *path) {
     if (!ctx || !path) return fail(ctx, LB_EINVAL, "bad arguments");
     lb_status st = check_status(ctx);
+    if (st != LB_OK) return st;
+    st = pull_state(ctx);
     if (st != LB_OK) return st;
     FILE *f = std::fopen(path, "wb");
     if (!f) return fail(ctx, LB_EIO, std::string("cannot open ") + path);
@@ -943,6 +1201,7 @@ extern "C" lb_status lb_restore(lb_ctx *ctx, const char *path) {
     ctx->step = step;
     ctx->parity = parity;
     ctx->steps_since_measure = 0;
+    ctx->dev_newer = false;
     long long clk[2] = {step, parity};
     CK(cudaMemcpyAsync(ctx->d_clock, clk, sizeof(clk), cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
@@ -954,6 +1213,8 @@ extern "C" lb_status lb_restore(lb_ctx *ctx, const char *path) {
 // ------------------------------------------------------------------ misc
 extern "C" lb_status lb_get_info(lb_ctx *ctx, lb_info *info) {
     if (!ctx || !info) return fail(ctx, LB_EINVAL, "bad arguments");
+    lb_status st = pull_state(ctx);
+    if (st != LB_OK) return st;
     info->nprocs = ctx->nbins;
     info->nsm = ctx->nsm;
     info->threads_per_cta = ctx->threads;

@@ -94,6 +94,50 @@ bool kernels_f64s(int nz_max, int nz_min, bool same, KernelInfo *out);
 bool kernels_bf16(int nz_max, int nz_min, bool same, KernelInfo *out);
 bool kernels_f32_any(int nz_max, int nz_min, KernelInfo *out);
 
+// Device balancer (lb_device_balance.cu): limits, state words, history.
+constexpr int kDevBalMaxVps = 8192;
+constexpr int kDevBalMaxBins = 1024;
+constexpr int kDevBalMaxSms = 1024;
+constexpr int kBalHist = 1024;        // rows kept
+constexpr int kBalHistCols = 8;       // step, strategy, migrations, predicted
+                                      // max/mean, measured SM max/mean,
+                                      // granularity floor, refine iterations, 0
+enum {
+    kStHave = 0,       // 1 once costs exist (measured or set)
+    kStRebal = 1,      // table rebalances so far (decides LB_AUTO*)
+    kStMeasStep = 2,   // step index of the last measurement
+    kStStrategy = 3,   // strategy of the current table
+    kStHist = 4,       // history rows written
+    kStWords = 8
+};
+
+struct DevBal {
+    int32_t nvps, nbins, nsm, nitems;
+    double ema_alpha, refine_tol, fallback_ns_per_cycle;
+    unsigned long long *vp_cycles;  // step kernel accumulators (reset here)
+    unsigned long long *bin_busy;
+    const int32_t *bin_smid;
+    const long long *bin_cal;
+    const long long *dclock;        // [0] step index
+    int32_t *status;                // sticky device status
+    unsigned *ticket;               // k_measure completion counter (0 between calls)
+    double *cost;                   // [nvps] cost average, ns per step
+    double *last;                   // [nvps] last measured cost, ns per step
+    int32_t *assign;                // [nvps] VP -> processor
+    int32_t *order;                 // [nvps] scratch: VPs by (cost desc, id asc)
+    const int32_t *spatial;         // [nvps] VPs in spatial order
+    const int32_t *nchunks;         // [nvps] work items per VP
+    long long *state;               // [kStWords]
+    double *pend;                   // [2] measured SM max/mean of the last measurement
+    double *hist;                   // [kBalHist][kBalHistCols]
+    int2 *items;                    // processor tables (written)
+    int32_t *bin_start;             // [nbins + 1] (written)
+};
+size_t dev_balance_smem(int nvps, int nbins);
+cudaError_t dev_balance_init();
+cudaError_t dev_measure(const DevBal &p, cudaStream_t s);
+cudaError_t dev_rebalance(const DevBal &p, int strategy, cudaStream_t s);
+
 // Text returned by lb_last_error(NULL) (calls without a ctx).
 void set_ctxless_error(const char *msg);
 

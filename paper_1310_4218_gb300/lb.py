@@ -92,6 +92,11 @@ _SIG = {
     "lb_get_info": (_I32, [_P, ctypes.POINTER(lb_info)]),
     "lb_last_error": (ctypes.c_char_p, [_P]),
     "lb_destroy": (None, [_P]),
+    "lb_device_measure": (_I32, [_P]),
+    "lb_device_rebalance": (_I32, [_P, _I32]),
+    "lb_get_costs": (_I32, [_P, _P, _P]),
+    "lb_balance_history": (_I32, [_P, _P, _I32, _P]),
+    "lb_graph_create_periods": (_I32, [_P, _I32, _I32, _I32, ctypes.POINTER(_P)]),
     "lb_step_noalloc": (_I32, [ctypes.POINTER(lb_grid_desc), ctypes.POINTER(lb_vp), _I32,
                                ctypes.c_int64, _I32, _P, _P]),
 }
@@ -246,6 +251,47 @@ def lb_graph_launch(ctx, graph):
 
 def lb_graph_destroy(ctx, graph):
     _check(load_library().lb_graph_destroy(ctx, _P(graph)), ctx)
+
+
+def lb_device_measure(ctx):
+    _check(load_library().lb_device_measure(ctx), ctx)
+
+
+def lb_device_rebalance(ctx, strategy):
+    s = STRATEGIES.get(strategy, strategy)
+    _check(load_library().lb_device_rebalance(ctx, int(s)), ctx)
+
+
+def lb_get_costs(ctx, nvps):
+    """(cost average, last measurement) per VP, ns per step."""
+    a = np.zeros(nvps, np.float64)
+    b = np.zeros(nvps, np.float64)
+    _check(load_library().lb_get_costs(ctx, _ptr(a), _ptr(b)), ctx)
+    return a, b
+
+
+BALANCE_HISTORY_COLUMNS = ("step", "strategy", "migrations", "predicted_max_over_mean",
+                           "sm_max_over_mean", "granularity_floor", "refine_iterations", "zero")
+
+
+def lb_balance_history(ctx, max_rows=1024):
+    """Device rebalances, oldest first: float64 array [n, 8] with the
+    columns of BALANCE_HISTORY_COLUMNS."""
+    buf = np.zeros((max_rows, 8), np.float64)
+    n = ctypes.c_int32(0)
+    _check(load_library().lb_balance_history(ctx, _ptr(buf), int(max_rows),
+                                             ctypes.addressof(n)), ctx)
+    return buf[:n.value]
+
+
+def lb_graph_create_periods(ctx, nsteps, strategy, nperiods):
+    """Executable CUDA graph of nperiods x (nsteps steps, device measurement,
+    device rebalance)."""
+    g = _P()
+    s = STRATEGIES.get(strategy, strategy)
+    _check(load_library().lb_graph_create_periods(ctx, int(nsteps), int(s), int(nperiods),
+                                                  ctypes.byref(g)), ctx)
+    return g.value
 
 
 def lb_sync(ctx):
