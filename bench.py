@@ -249,9 +249,14 @@ class StrategyRun:
         from paper_1310_4218_gb300 import lb
         from paper_1310_4218_gb300.sim import Simulation
         self.lb, self.w, self.epochs, self.kc_dev = lb, w, epochs, kc_dev
-        # "<strategy>+steal": processor tables with end-of-step work stealing
-        steal = strategy.endswith("+steal")
-        strategy = strategy[:-len("+steal")] if steal else strategy
+        # "<strategy>[+steal][+dev]": +steal, processor tables with end-of-step
+        # work stealing; +dev, measurement and balancer on the device
+        parts = strategy.split("+")
+        strategy, flags = parts[0], set(parts[1:])
+        steal = "steal" in flags
+        self.dev_mode = "dev" in flags
+        self.dev_tags = []
+        self.kernels = 0             # our kernel launches (step, k_c switch, balancer)
         self.P, self.strategy, self.dev, self.stream = args.period, strategy, dev, stream
         opt = lb.lb_default_options()
         opt.threads_hint = args.threads
@@ -276,14 +281,23 @@ class StrategyRun:
                 if t % w.kc_epoch_steps == 0 or t == t0:
                     for gi in range(len(w.grids)):
                         self.lb.lb_set_kc(self.sim.ctx, gi, self.kc_dev[e][gi].data_ptr())
+                        self.kernels += 1
                 n = min(n, (e + 1) * w.kc_epoch_steps - t)
             self.sim.step(n)
             t += n
             n_launch += 1
+        self.kernels += n_launch
         return n_launch
 
     def balance(self, tag):
         """Load measurement (Sec. V) and the balancer call (Sec. VI)."""
+        if self.dev_mode:
+            # enqueued only: measurement, rank, balancer, table kernels
+            self.lb.lb_device_measure(self.sim.ctx)
+            self.lb.lb_device_rebalance(self.sim.ctx, self.strategy)
+            self.kernels += 4
+            self.dev_tags.append(tag)
+            return
         cost, busy = self.sim.measure()
         used = busy[busy > 0]
         st = {"sm_max_over_mean": float(used.max() / used.mean()) if used.size else None}
@@ -295,6 +309,16 @@ class StrategyRun:
             st["predicted_max_over_mean"] = pred
         self.stats[tag] = st
 
+    def collect(self):
+        """Device mode: per-period records from the balance history."""
+        if not self.dev_mode or not self.dev_tags:
+            return
+        rows = self.lb.lb_balance_history(self.sim.ctx)[-len(self.dev_tags):]
+        for tag, r in zip(self.dev_tags, rows):
+            self.stats[tag] = {"sm_max_over_mean": float(r[4]), "granularity_floor": float(r[5]),
+                               "migrations": int(r[2]), "predicted_max_over_mean": float(r[3])}
+        self.dev_tags = []
+
     def warmup(self, nper):
         import torch
         for wi in range(nper):
@@ -302,6 +326,7 @@ class StrategyRun:
             self.t += self.P
             self.balance("first" if wi == 0 else "warmup")
         torch.cuda.synchronize(self.dev)
+        self.collect()
 
     def timed(self, nper, sampler=None):
         """nper periods between CUDA events; returns the measurement."""
@@ -309,6 +334,7 @@ class StrategyRun:
         lb, stream = self.lb, self.stream
         sw0, cs0 = lb.lb_work_done(self.sim.ctx)
         torch.cuda.synchronize(self.dev)
+        k0 = self.kernels
         if sampler:
             sampler.start()
             time.sleep(0.3)
@@ -329,9 +355,11 @@ class StrategyRun:
         torch.cuda.synchronize(self.dev)
         clocks = sampler.stop() if sampler else None
         sw1, cs1 = lb.lb_work_done(self.sim.ctx)
+        self.collect()
         return {"ms": e0.elapsed_time(e1), "sweeps": sw1 - sw0, "cells": cs1 - cs0,
                 "kernel_ms": [a.elapsed_time(b) / n for a, b, n in kev],
-                "launches": sum(n for _, _, n in kev), "clocks": clocks}
+                "launches": sum(n for _, _, n in kev), "kernels": self.kernels - k0,
+                "clocks": clocks}
 
     def end_to_end(self, fields, nper):
         """The same periods through the public API with host buffers: every
@@ -361,6 +389,7 @@ class StrategyRun:
                     h_out[gi].view(-1).copy_(sim.field_tensor(gi).view(-1), non_blocking=True)
         c1.record(stream)
         torch.cuda.synchronize(self.dev)
+        self.collect()
         es = c0.elapsed_time(c1) / 1000.0
         sw = lb.lb_work_done(sim.ctx)[0] - s0
         nbytes = sum(x.numel() * x.element_size() for x in h_in)
@@ -433,7 +462,8 @@ def main():
     compare = {}
     if not args.no_compare:
         for st in [x for x in ("static", "auto", "queue", "auto_spatial", "auto_spatial+steal",
-                               "static+steal") if x != args.strategy]:
+                               "static+steal", "auto_spatial+steal+dev", "auto_spatial+dev")
+                   if x != args.strategy]:
             r2 = StrategyRun(w, fields, epochs, kc_dev, args, dev, stream, st)
             r2.warmup(args.warmup)
             m2 = r2.timed(args.steps)
@@ -473,7 +503,7 @@ def main():
             "imbalance": stats,
             "strategies": compare,
             "clocks": m["clocks"],
-            "gpu_launches": m["launches"],
+            "gpu_launches": m["kernels"],
             "e2e": e2e,
             "cpu_baseline": cpu,
         }

@@ -216,8 +216,9 @@ lb_status lb_get_assignment(lb_ctx *ctx, int32_t *vp_to_proc, int32_t *nprocs);
 lb_status lb_set_assignment(lb_ctx *ctx, const int32_t *vp_to_proc);
 
 /* Point grid `grid`'s k_c source at a new device array int32[ny*nx] (the
-   load array re-drawn between segments); the array is read from the next
-   lb_step on and stays caller-owned. */
+   load array re-drawn between segments).  The switch is enqueued on the
+   ctx stream (no synchronisation): steps enqueued after this call read the
+   new array, which stays caller-owned and must stay valid while they run. */
 lb_status lb_set_kc(lb_ctx *ctx, int32_t grid, const int32_t *dev_kc);
 
 /* Compensated FP64 global sum of grid `grid` after the latest step that

@@ -54,6 +54,7 @@ struct lb_ctx {
     double *d_last = nullptr;
     int32_t *d_assign = nullptr;
     int32_t *d_order = nullptr;
+    long long *d_q = nullptr;          // fixed-point costs (device balancer scratch)
     int32_t *d_spatial = nullptr;
     int32_t *d_nchunks = nullptr;
     long long *d_bstate = nullptr;
@@ -272,7 +273,7 @@ static void free_ctx(lb_ctx *ctx) {
                     ctx->d_sweeps,    ctx->d_clock,    ctx->d_bin_ctr,   ctx->d_cost,
                     ctx->d_last,      ctx->d_assign,   ctx->d_order,     ctx->d_spatial,
                     ctx->d_nchunks,   ctx->d_bstate,   ctx->d_pend,      ctx->d_bhist,
-                    ctx->d_ticket};
+                    ctx->d_ticket,    ctx->d_q};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete ctx;
@@ -518,6 +519,7 @@ extern "C" lb_status lb_create(const lb_grid_desc *grids, int32_t ngrids, const 
     if (e == cudaSuccess) e = dalloc(&ctx->d_last, nvps);
     if (e == cudaSuccess) e = dalloc(&ctx->d_assign, nvps);
     if (e == cudaSuccess) e = dalloc(&ctx->d_order, nvps);
+    if (e == cudaSuccess) e = dalloc(&ctx->d_q, nvps);
     if (e == cudaSuccess) e = dalloc(&ctx->d_spatial, nvps);
     if (e == cudaSuccess) e = dalloc(&ctx->d_nchunks, nvps);
     if (e == cudaSuccess) e = dalloc(&ctx->d_bstate, kStWords);
@@ -717,6 +719,7 @@ static DevBal make_devbal(lb_ctx *ctx) {
     p.last = ctx->d_last;
     p.assign = ctx->d_assign;
     p.order = ctx->d_order;
+    p.q = ctx->d_q;
     p.spatial = ctx->d_spatial;
     p.nchunks = ctx->d_nchunks;
     p.state = ctx->d_bstate;
@@ -868,22 +871,19 @@ extern "C" lb_status lb_measure_loads(lb_ctx *ctx, double *vp_cost_ns, double *s
     CK(cudaMemsetAsync(ctx->d_vp_cycles, 0, sizeof(unsigned long long) * nv, s0));
     CK(cudaMemsetAsync(ctx->d_bin_busy, 0, sizeof(unsigned long long) * nb, s0));
     CK(cudaStreamSynchronize(s0));
-    // ns per SM cycle from each processor's globaltimer / clock64 pair
-    double ns = 0.0, cy = 0.0;
+    // ns per SM cycle from each processor's globaltimer / clock64 pair:
+    // integer sums (exact in any order), one FP64 division
+    long long ns = 0, cy = 0;
     for (int b = 0; b < nb; ++b) {
-        double dn = (double)(cal[4 * b + 2] - cal[4 * b + 0]);
-        double dc = (double)(cal[4 * b + 3] - cal[4 * b + 1]);
+        const long long dn = cal[4 * b + 2] - cal[4 * b + 0];
+        const long long dc = cal[4 * b + 3] - cal[4 * b + 1];
         if (dn > 0 && dc > 0) {
             ns += dn;
             cy += dc;
         }
     }
-    double ns_per_cycle = (cy > 0) ? ns / cy : 0.0;
-    if (!(ns_per_cycle > 0)) {
-        int khz = 0;
-        cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, ctx->device);
-        ns_per_cycle = khz > 0 ? 1e6 / khz : 1.0;
-    }
+    double ns_per_cycle = (cy > 0) ? (double)ns / (double)cy : 0.0;
+    if (!(ns_per_cycle > 0)) ns_per_cycle = ctx->fallback_npc;
     const double steps = (double)ctx->steps_since_measure;
     const double a = ctx->opt.ema_alpha;
     for (int v = 0; v < nv; ++v) {
@@ -1023,9 +1023,8 @@ extern "C" lb_status lb_set_kc(lb_ctx *ctx, int32_t grid, const int32_t *dev_kc)
     if (ctx->grids[grid].kc_disk) return fail(ctx, LB_ESTATE, "grid uses the disk rule");
     ctx->grids[grid].kc = dev_kc;
     ctx->h_grids[grid].kc = dev_kc;
-    CK(cudaMemcpyAsync(&ctx->d_grids[grid], &ctx->h_grids[grid], sizeof(GridDev),
-                       cudaMemcpyHostToDevice, ctx->stream));
-    CK(cudaStreamSynchronize(ctx->stream));
+    // a one-thread kernel, so the switch is stream-ordered and needs no sync
+    CK(dev_set_kc(&ctx->d_grids[grid], dev_kc, ctx->stream));
     return LB_OK;
 }
 

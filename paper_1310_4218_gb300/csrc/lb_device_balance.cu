@@ -4,22 +4,25 @@
 // measurement, balancer, new work tables -- can be enqueued, or captured in
 // one CUDA graph, without a host round trip.
 //
-// Every FP64 result equals the host balancers' (lb_balance.cpp) bit for bit
-// for equal inputs: the same operations in the same order, written as
-// explicitly rounded intrinsics (__dadd_rn and friends are never contracted
-// into FMAs).  Orders of FP64 values are taken on order-preserving 64-bit
-// integer keys: FP64 compares run on GB300's narrow FP64 pipe, integer
-// compares on the full-rate ALUs.
+// The balancers work on the fixed-point cost grid of lb_balance.cpp: each
+// cost rounded once to an integer, every load and total an integer below
+// 2^53.  Loads are int64 sums (exact in any order), so the device reproduces
+// the host balancers' assignments bit for bit while adding in parallel, and
+// no sequential FP64 chain is needed (a dependent FP64 add costs ~64 cycles
+// on GB300, an integer add a few).  The cost average itself stays FP64, with
+// the host's operations in the host's order (explicitly rounded intrinsics,
+// never contracted into FMAs).
 //
 // Kernels (all on the ctx stream):
-//   k_measure  one thread per VP: cycles -> ns per step -> EMA; the last
-//              block to finish (threadfence ticket) records SM busy times
-//              and the measurement step
-//   k_rank     one thread per VP: rank by (cost desc, id asc) -- GreedyLB's
-//              order; exits at once unless the resolved strategy is GreedyLB
-//   k_balance  one CTA of 1024 threads: static / GreedyLB / list
-//              scheduling in spatial order / RefineSwapLB on a shared-memory
-//              copy of the assignment; migrations and predicted max/mean
+//   k_measure  one thread per VP: cycles -> ns per step -> cost average;
+//              the last block to finish (threadfence ticket) records SM
+//              busy times and the measurement step
+//   k_prep     one thread per VP: costs on the fixed-point grid; for
+//              GreedyLB also each VP's rank by (cost desc, id asc)
+//   k_balance  one CTA of 1024 threads: static / GreedyLB / list scheduling
+//              in spatial order (one warp) / RefineSwapLB (whole CTA) on
+//              shared-memory copies of the assignment and the costs;
+//              migrations and predicted max/mean
 //   k_items    one CTA per processor: its work-item range and its items in
 //              spatial order (the tables the step kernel reads)
 #include <cuda_runtime.h>
@@ -33,9 +36,12 @@ namespace {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kBalThreads = 1024;
 constexpr int kBalWarps = kBalThreads / kWarp;
-constexpr int kRankThreads = 256;
+constexpr int kPrepThreads = 256;
 constexpr int kItemThreads = 256;
+constexpr int kMeasThreads = 256;
 constexpr unsigned kNone = 0x7fffffffu;
+constexpr int kIdBits = 10;                   // bins < 1024 = 2^kIdBits
+constexpr unsigned long long kIdMask = (1ull << kIdBits) - 1;
 
 // a < b (IEEE, -0 == +0, no NaN) iff okey(a) < okey(b)
 __device__ __forceinline__ unsigned long long okey(double x) {
@@ -44,198 +50,172 @@ __device__ __forceinline__ unsigned long long okey(double x) {
     return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
 }
 
+__device__ __forceinline__ double from_okey(unsigned long long k) {
+    return __longlong_as_double((long long)((k >> 63) ? (k & 0x7fffffffffffffffull) : ~k));
+}
+
 __device__ __forceinline__ int resolve(int s, long long rebalances) {
     if (s == LB_AUTO) return rebalances == 0 ? LB_GREEDY : LB_REFINE_SWAP;
     if (s == LB_AUTO_SPATIAL) return rebalances == 0 ? LB_GREEDY_SPATIAL : LB_REFINE_SWAP;
     return s;
 }
 
-// Lexicographic minimum of (key, id) over a full warp; every lane gets the id.
-__device__ __forceinline__ unsigned warp_min_key_id(unsigned long long k, unsigned id) {
+__device__ __forceinline__ int bit_length(long long n) { return n > 0 ? 64 - __clzll(n) : 0; }
+
+// Warp minimum / maximum of a 64-bit key; every lane gets it.
+__device__ __forceinline__ unsigned long long warp_min64(unsigned long long k) {
     const unsigned hi = (unsigned)(k >> 32), lo = (unsigned)k;
     const unsigned mh = __reduce_min_sync(kFull, hi);
     const unsigned ml = __reduce_min_sync(kFull, hi == mh ? lo : ~0u);
-    return __reduce_min_sync(kFull, (hi == mh && lo == ml) ? id : ~0u);
+    return ((unsigned long long)mh << 32) | ml;
 }
 
-// Bin with the lowest (load, id), skipping `skip` and every bin at or before
-// (after_key, after_id) in that order when after_id >= 0.  One full warp.
-__device__ unsigned warp_next_bin(const double *s_load, int nb, int skip,
-                                  unsigned long long after_key, int after_id) {
-    const int lane = threadIdx.x % kWarp;
-    unsigned long long bk = ~0ull;
-    unsigned bi = kNone;
-    for (int b = lane; b < nb; b += kWarp) {
-        if (b == skip) continue;
-        const unsigned long long k = okey(s_load[b]);
-        if (after_id >= 0 && (k < after_key || (k == after_key && b <= after_id))) continue;
-        if (k < bk) {
-            bk = k;
-            bi = (unsigned)b;
-        }
-    }
-    return warp_min_key_id(bk, bi);
+__device__ __forceinline__ unsigned long long warp_max64(unsigned long long k) {
+    return ~warp_min64(~k);
 }
 
-// Lexicographic minimum of (key, id) over a full warp, both parts returned.
-__device__ __forceinline__ void warp_min_pair(unsigned long long &k, unsigned &id) {
-    const unsigned hi = (unsigned)(k >> 32), lo = (unsigned)k;
-    const unsigned mh = __reduce_min_sync(kFull, hi);
-    const unsigned ml = __reduce_min_sync(kFull, hi == mh ? lo : ~0u);
-    id = __reduce_min_sync(kFull, (hi == mh && lo == ml) ? id : ~0u);
-    k = ((unsigned long long)mh << 32) | ml;
-}
-
-// Block-wide lexicographic minimum of (key, idx) (1024 threads); every
-// thread gets it.  (~0, ~0) means none.
-__device__ void block_min_key_idx(unsigned long long &k, unsigned &idx, unsigned long long *s_wk,
-                                  unsigned *s_wi) {
-    const int lane = threadIdx.x % kWarp, warp = threadIdx.x / kWarp;
-    warp_min_pair(k, idx);
-    if (lane == 0) {
-        s_wk[warp] = k;
-        s_wi[warp] = idx;
-    }
-    __syncthreads();
-    if (warp == 0) {
-        unsigned long long k2 = s_wk[lane];
-        unsigned i2 = s_wi[lane];
-        warp_min_pair(k2, i2);
-        if (lane == 0) {
-            s_wk[kBalWarps] = k2;
-            s_wi[kBalWarps] = i2;
-        }
-    }
-    __syncthreads();
-    k = s_wk[kBalWarps];
-    idx = s_wi[kBalWarps];
-    __syncthreads();
-}
-
-__device__ __forceinline__ double from_okey(unsigned long long k) {
-    return __longlong_as_double((long long)((k >> 63) ? (k & 0x7fffffffffffffffull) : ~k));
-}
-
-__device__ int block_sum_int(int v, int *s_w) {
+// Block minimum of a 64-bit key (blockDim a multiple of 32); every thread
+// gets it.  s_w holds one word per warp plus one.
+__device__ unsigned long long block_min64(unsigned long long k, unsigned long long *s_w) {
     const int lane = threadIdx.x % kWarp, warp = threadIdx.x / kWarp;
     const int nw = blockDim.x / kWarp;
-    v = __reduce_add_sync(kFull, v);
+    k = warp_min64(k);
+    if (lane == 0) s_w[warp] = k;
+    __syncthreads();
+    if (warp == 0) {
+        unsigned long long x = lane < nw ? s_w[lane] : ~0ull;
+        x = warp_min64(x);
+        if (lane == 0) s_w[nw] = x;
+    }
+    __syncthreads();
+    k = s_w[nw];
+    __syncthreads();
+    return k;
+}
+
+__device__ unsigned long long block_sum64(unsigned long long v, unsigned long long *s_w) {
+    const int lane = threadIdx.x % kWarp, warp = threadIdx.x / kWarp;
+    const int nw = blockDim.x / kWarp;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
     if (lane == 0) s_w[warp] = v;
     __syncthreads();
-    int t = 0;
+    unsigned long long t = 0;
     for (int w = 0; w < nw; ++w) t += s_w[w];
     __syncthreads();
     return t;
 }
 
-// Per-bin loads, each the FP64 sum of its VPs' costs in increasing VP id
-// (bin_loads); warp w sums bins w, w + 32, ...
-__device__ void bin_loads_dev(const int *s_assign, const double *cost, int nv, int nb,
-                              double *s_load) {
-    const int lane = threadIdx.x % kWarp, warp = threadIdx.x / kWarp;
-    for (int b = warp; b < nb; b += kBalWarps) {
-        double acc = 0.0;
-        for (int base = 0; base < nv; base += kWarp) {
-            const int v = base + lane;
-            unsigned m = __ballot_sync(kFull, v < nv && s_assign[v] == b);
-            while (m) {
-                const int j = __ffs(m) - 1;
-                m &= m - 1;
-                acc = __dadd_rn(acc, cost[base + j]);
-            }
-        }
-        if (lane == 0) s_load[b] = acc;
-    }
-    __syncthreads();
-}
-
-// GreedyLB's rule over VPs in a given order (ov[i], with costs oc[i]): each
-// to the bin with the lowest (load, id); loads summed in assignment order.
-// One warp; lane l keeps the loads of bins l, l + 32, ... in registers.
-template <int NBL>
-__device__ void greedy_warp(const int *ov, const double *oc, int nv, int nb, int *s_assign) {
+// Graham's list scheduling -- each VP of ord[0..nv) in turn to the bin with
+// the lowest (load, id), loads summed in assignment order (GreedyLB's rule)
+// -- reproduced exactly in rounds by one warp.  Keys load * 2^10 + bin are
+// unique and ordered like (load, bin); cur holds the bins' keys in ascending
+// order.  With the bins in that order as s_0, s_1, ..., the sequential rule
+// gives VPs i, i+1, ... to s_0, s_1, ... for as long as each next s_j is
+// still below every key already updated in this round (its key plus the
+// VP's cost); the first VP for which that fails starts the next round.  The
+// new order merges the updated keys into the untouched ones.
+template <int R>   // candidates per lane: nb <= 32 * R
+__device__ __noinline__ void list_schedule(const int32_t *ord, const long long *s_q, int nv, int nb,
+                              int *s_assign, unsigned long long *sk0, unsigned long long *sk1,
+                              unsigned long long *s_t) {
     const int lane = threadIdx.x % kWarp;
-    double ld[NBL];
-#pragma unroll
-    for (int j = 0; j < NBL; ++j) ld[j] = 0.0;
-    unsigned long long mk = lane < nb ? okey(0.0) : ~0ull;
-    unsigned mi = lane < nb ? (unsigned)lane : kNone;
-    for (int i = 0; i < nv; ++i) {
-        const int v = ov[i];
-        const double c = oc[i];
-        const unsigned w = warp_min_key_id(mk, mi);
-        if (lane == 0) s_assign[v] = (int)w;
-        if ((int)(w % kWarp) == lane) {
-            const int slot = (int)(w / kWarp);
-            unsigned long long bk = ~0ull;
-            unsigned bi = kNone;
-#pragma unroll
-            for (int j = 0; j < NBL; ++j) {
-                if (j == slot) ld[j] = __dadd_rn(ld[j], c);
-                const int b = lane + kWarp * j;
-                if (b < nb) {
-                    const unsigned long long k = okey(ld[j]);
-                    if (k < bk) {
-                        bk = k;
-                        bi = (unsigned)b;
-                    }
-                }
-            }
-            mk = bk;
-            mi = bi;
-        }
-        __syncwarp();
-    }
-}
-
-// Same rule with the loads in shared memory (any bin count).
-__device__ void greedy_warp_smem(const int *ov, const double *oc, int nv, int nb, int *s_assign,
-                                 double *s_load) {
-    const int lane = threadIdx.x % kWarp;
-    for (int b = lane; b < nb; b += kWarp) s_load[b] = 0.0;
+    for (int b = lane; b < nb; b += kWarp) sk0[b] = (unsigned long long)b;
     __syncwarp();
-    unsigned long long mk = lane < nb ? okey(0.0) : ~0ull;
-    unsigned mi = lane < nb ? (unsigned)lane : kNone;
-    for (int i = 0; i < nv; ++i) {
-        const int v = ov[i];
-        const double c = oc[i];
-        const unsigned w = warp_min_key_id(mk, mi);
-        if (lane == 0) s_assign[v] = (int)w;
-        if ((int)(w % kWarp) == lane) {
-            s_load[w] = __dadd_rn(s_load[w], c);
-            unsigned long long bk = ~0ull;
-            unsigned bi = kNone;
-            for (int b = lane; b < nb; b += kWarp) {
-                const unsigned long long k = okey(s_load[b]);
-                if (k < bk) {
-                    bk = k;
-                    bi = (unsigned)b;
-                }
+    unsigned long long *cur = sk0, *nxt = sk1;
+    for (int i = 0; i < nv;) {
+        const int n = min(nb, nv - i);
+        unsigned long long k[R], u[R];
+        int vv[R];
+        unsigned long long run = ~0ull;   // min of u over this lane's candidates
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int j = lane * R + r;
+            k[r] = ~0ull;
+            u[r] = ~0ull;
+            vv[r] = -1;
+            if (j < n) {
+                k[r] = cur[j];
+                vv[r] = ord[i + j];
+                u[r] = k[r] + ((unsigned long long)s_q[vv[r]] << kIdBits);
             }
-            mk = bk;
-            mi = bi;
+            run = u[r] < run ? u[r] : run;
+        }
+        unsigned long long incl = run;
+#pragma unroll
+        for (int o = 1; o < kWarp; o <<= 1) {
+            const unsigned long long y = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o && y < incl) incl = y;
+        }
+        unsigned long long pre = __shfl_up_sync(kFull, incl, 1);   // earlier lanes
+        if (lane == 0) pre = ~0ull;
+        unsigned first = ~0u;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int j = lane * R + r;
+            if (first == ~0u && j >= 1 && j < n && !(k[r] < pre)) first = (unsigned)j;
+            pre = u[r] < pre ? u[r] : pre;
+        }
+        const unsigned f = __reduce_min_sync(kFull, first);
+        const int K = f == ~0u ? n : (int)f;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int j = lane * R + r;
+            if (j < K) {
+                s_assign[vv[r]] = (int)(k[r] & kIdMask);
+                s_t[j] = u[r];
+            }
         }
         __syncwarp();
+        for (int j = lane; j < nb; j += kWarp) {
+            unsigned long long key;
+            int pos;
+            if (j < K) {
+                key = s_t[j];
+                int lo = K, hi = nb;   // untouched keys below key
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    if (cur[mid] < key) lo = mid + 1;
+                    else hi = mid;
+                }
+                pos = lo - K;
+            } else {
+                key = cur[j];
+                pos = j - K;
+            }
+            for (int t = 0; t < K; ++t) pos += s_t[t] < key;
+            nxt[pos] = key;
+        }
+        __syncwarp();
+        unsigned long long *tmp = cur;
+        cur = nxt;
+        nxt = tmp;
+        i += K;
     }
 }
 
 // ---------------------------------------------------------------- kernels
-__global__ void __launch_bounds__(256) k_measure(const DevBal p) {
+__global__ void __launch_bounds__(kMeasThreads) k_measure(const DevBal p) {
     __shared__ double s_npc, s_steps;
     __shared__ int s_last;
+    __shared__ unsigned long long s_w[kMeasThreads / kWarp + 1];
     __shared__ unsigned long long s_busy[kDevBalMaxSms];
-    if (threadIdx.x == 0) {
-        // ns per SM cycle from every processor's globaltimer / clock64 pair
-        double ns = 0.0, cy = 0.0;
-        for (int b = 0; b < p.nbins; ++b) {
-            const double dn = __ll2double_rn(p.bin_cal[4 * b + 2] - p.bin_cal[4 * b + 0]);
-            const double dc = __ll2double_rn(p.bin_cal[4 * b + 3] - p.bin_cal[4 * b + 1]);
-            if (dn > 0.0 && dc > 0.0) {
-                ns = __dadd_rn(ns, dn);
-                cy = __dadd_rn(cy, dc);
-            }
+    // ns per SM cycle from every processor's globaltimer / clock64 pair:
+    // integer sums (exact in any order), one FP64 division
+    unsigned long long ns = 0, cy = 0;
+    for (int b = threadIdx.x; b < p.nbins; b += blockDim.x) {
+        const long long dn = p.bin_cal[4 * b + 2] - p.bin_cal[4 * b + 0];
+        const long long dc = p.bin_cal[4 * b + 3] - p.bin_cal[4 * b + 1];
+        if (dn > 0 && dc > 0) {
+            ns += (unsigned long long)dn;
+            cy += (unsigned long long)dc;
         }
-        double npc = cy > 0.0 ? __ddiv_rn(ns, cy) : 0.0;
+    }
+    ns = block_sum64(ns, s_w);
+    cy = block_sum64(cy, s_w);
+    if (threadIdx.x == 0) {
+        double npc = cy > 0 ? __ddiv_rn(__ll2double_rn((long long)ns), __ll2double_rn((long long)cy))
+                            : 0.0;
         if (!(npc > 0.0)) npc = p.fallback_ns_per_cycle;
         s_npc = npc;
         s_steps = __ll2double_rn(p.dclock[0] - p.state[kStMeasStep]);
@@ -272,60 +252,79 @@ __global__ void __launch_bounds__(256) k_measure(const DevBal p) {
         p.bin_busy[b] = 0ull;
     }
     __syncthreads();
+    unsigned long long mx = 0, tot = 0, used = 0;
+    for (int s = threadIdx.x; s < p.nsm; s += blockDim.x) {
+        const unsigned long long x = s_busy[s];
+        mx = x > mx ? x : mx;
+        tot += x;
+        used += x > 0;
+    }
+    mx = ~block_min64(~mx, s_w);
+    tot = block_sum64(tot, s_w);
+    used = block_sum64(used, s_w);
     if (threadIdx.x == 0) {
-        double mx = 0.0, tot = 0.0;
-        int n = 0;
-        for (int s = 0; s < p.nsm; ++s)
-            if (s_busy[s] > 0ull) {
-                const double x = (double)s_busy[s];
-                mx = x > mx ? x : mx;
-                tot += x;
-                ++n;
-            }
-        p.pend[0] = (n > 0 && tot > 0.0) ? mx / (tot / n) : 0.0;
+        p.pend[0] = (used > 0 && tot > 0) ? (double)mx / ((double)tot / (double)used) : 0.0;
         p.state[kStHave] = 1;
         p.state[kStMeasStep] = p.dclock[0];
         *p.ticket = 0u;
     }
 }
 
-__global__ void __launch_bounds__(kRankThreads) k_rank(const DevBal p, int strategy) {
-    __shared__ unsigned long long s_key[kRankThreads];
-    if (resolve(strategy, p.state[kStRebal]) != LB_GREEDY) return;
-    const int v = blockIdx.x * blockDim.x + threadIdx.x;
-    const unsigned long long kv = v < p.nvps ? okey(p.cost[v]) : 0ull;
-    int rank = 0;
-    for (int base = 0; base < p.nvps; base += kRankThreads) {
-        const int u = base + threadIdx.x;
-        s_key[threadIdx.x] = u < p.nvps ? okey(p.cost[u]) : 0ull;
-        __syncthreads();
-        const int n = min(kRankThreads, p.nvps - base);
-        for (int j = 0; j < n; ++j) {
-            const unsigned long long ku = s_key[j];
-            rank += (ku > kv) || (ku == kv && base + j < v);
-        }
-        __syncthreads();
+// Costs on the fixed-point grid (lb_balance.cpp: fixed_point), and for
+// GreedyLB each VP's position in (cost desc, id asc) order.  Every block
+// rounds all costs into shared memory and writes its own range.
+__global__ void __launch_bounds__(kPrepThreads) k_prep(const DevBal p, int strategy) {
+    extern __shared__ long long s_qall[];          // [nvps]
+    __shared__ unsigned long long s_w[kPrepThreads / kWarp + 1];
+    __shared__ int s_e, s_any;
+    const int nv = p.nvps;
+    unsigned long long kmax = okey(0.0);
+    for (int v = threadIdx.x; v < nv; v += blockDim.x) {
+        const unsigned long long k = okey(p.cost[v]);
+        kmax = k > kmax ? k : kmax;
     }
-    if (v < p.nvps) p.order[rank] = v;
+    kmax = ~block_min64(~kmax, s_w);
+    if (threadIdx.x == 0) {
+        const double cmax = from_okey(kmax);
+        int x = 0;
+        if (cmax > 0.0) frexp(cmax, &x);
+        s_e = cmax > 0.0 ? 53 - bit_length(nv) - x : 0;
+        s_any = cmax > 0.0;
+    }
+    __syncthreads();
+    const bool any = s_any != 0;
+    const int e = s_e;
+    for (int v = threadIdx.x; v < nv; v += blockDim.x)
+        s_qall[v] = any ? __double2ll_rn(ldexp(p.cost[v], e)) : 0ll;
+    __syncthreads();
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v < nv) p.q[v] = s_qall[v];
+    if (resolve(strategy, p.state[kStRebal]) != LB_GREEDY || v >= nv) return;
+    const long long qv = s_qall[v];
+    int rank = 0;
+    for (int u = 0; u < nv; ++u) {
+        const long long qu = s_qall[u];
+        rank += (qu > qv) || (qu == qv && u < v);
+    }
+    p.order[rank] = v;
 }
 
 __global__ void __launch_bounds__(kBalThreads, 1) k_balance(const DevBal p, int strategy) {
-    extern __shared__ double s_dyn[];
+    extern __shared__ long long s_dyn[];
     const int nv = p.nvps, nb = p.nbins;
-    double *s_load = s_dyn;                          // [nb]
-    int *s_assign = (int *)(s_load + nb);            // [nv]
-    int *s_pl = s_assign + nv;                       // [nv] members of P (unordered)
-    int *s_ps = s_pl + nv;                           // [nv] members of P, (cost desc, id asc)
-    int *s_ql = s_ps + nv;                           // [nv] members of Q (unordered)
-    int *s_qs = s_ql + nv;                           // [nv] members of Q, (cost asc, id asc)
-    double *s_oc = (double *)s_ps;                   // [nv] greedy: costs in visiting order
-                                                     // (over s_ps and s_ql; 8-byte aligned)
+    long long *s_q = s_dyn;                                          // [nv] fixed-point costs
+    unsigned long long *s_load = (unsigned long long *)(s_q + nv);   // [nb]
+    unsigned long long *s_k0 = s_load + nb;                          // [nb] list-scheduling keys
+    unsigned long long *s_k1 = s_k0 + nb;                            // [nb]
+    unsigned long long *s_t = s_k1 + nb;                             // [nb]
+    int *s_assign = (int *)(s_t + nb);                               // [nv]
+    int *s_ul = s_assign + nv;       // [nv] members of P or Q (unordered)
+    int *s_ps = s_ul + nv;           // [nv] members of P, (cost desc, id asc)
+    int *s_qs = s_ps + nv;           // [nv] members of Q, (cost asc, id asc)
     __shared__ int s_strat, s_skip, s_P, s_Q, s_np, s_nq, s_iters;
     __shared__ unsigned s_found;
     __shared__ double s_thr;
-    __shared__ unsigned long long s_wk[kBalWarps + 1];
-    __shared__ unsigned s_wi[kBalWarps + 1];
-    __shared__ int s_wsum[kBalWarps];
+    __shared__ unsigned long long s_w[kBalWarps + 1];
     const int tid = threadIdx.x, lane = tid % kWarp, warp = tid / kWarp;
 
     if (tid == 0) {
@@ -338,70 +337,76 @@ __global__ void __launch_bounds__(kBalThreads, 1) k_balance(const DevBal p, int 
     __syncthreads();
     if (s_skip) return;
     const int st = s_strat;
-    for (int v = tid; v < nv; v += kBalThreads) s_assign[v] = p.assign[v];
+    for (int v = tid; v < nv; v += kBalThreads) {
+        s_assign[v] = p.assign[v];
+        s_q[v] = p.q[v];
+    }
     __syncthreads();
 
     if (st == LB_STATIC) {
         for (int v = tid; v < nv; v += kBalThreads) s_assign[v] = (int)(((long long)v * nb) / nv);
     } else if (st == LB_GREEDY || st == LB_GREEDY_SPATIAL) {
-        const int *ord = st == LB_GREEDY ? p.order : p.spatial;
-        for (int i = tid; i < nv; i += kBalThreads) {
-            const int v = ord[i];
-            s_pl[i] = v;
-            s_oc[i] = p.cost[v];
-        }
-        __syncthreads();
         if (warp == 0) {
-            if (nb <= 8 * kWarp) greedy_warp<8>(s_pl, s_oc, nv, nb, s_assign);
-            else greedy_warp_smem(s_pl, s_oc, nv, nb, s_assign, s_load);
+            const int32_t *ord = st == LB_GREEDY ? p.order : p.spatial;
+            if (nb <= 5 * kWarp) list_schedule<5>(ord, s_q, nv, nb, s_assign, s_k0, s_k1, s_t);
+            else if (nb <= 8 * kWarp) list_schedule<8>(ord, s_q, nv, nb, s_assign, s_k0, s_k1, s_t);
+            else list_schedule<kDevBalMaxBins / kWarp>(ord, s_q, nv, nb, s_assign, s_k0, s_k1, s_t);
         }
     } else {
-        // RefineSwapLB (lb_balance.cpp: refine_swap)
-        bin_loads_dev(s_assign, p.cost, nv, nb, s_load);
-        if (tid == 0) {
-            double t = 0.0;
-            for (int b = 0; b < nb; ++b) t = __dadd_rn(t, s_load[b]);
-            s_thr = __dmul_rn(__dadd_rn(1.0, p.refine_tol), __ddiv_rn(t, (double)nb));
+        // RefineSwapLB (lb_balance.cpp: refine_swap); loads are exact
+        // integers, so they may be summed in any order
+        for (int b = tid; b < nb; b += kBalThreads) s_load[b] = 0ull;
+        __syncthreads();
+        unsigned long long tot = 0;
+        for (int v = tid; v < nv; v += kBalThreads) {
+            atomicAdd(&s_load[s_assign[v]], (unsigned long long)s_q[v]);
+            tot += (unsigned long long)s_q[v];
         }
+        tot = block_sum64(tot, s_w);
+        if (tid == 0)
+            s_thr = __dmul_rn(__dadd_rn(1.0, p.refine_tol),
+                              __ddiv_rn(__ull2double_rn(tot), (double)nb));
         __syncthreads();
         const double thr = s_thr;
         for (long long it = 0; it < 4LL * nv; ++it) {
             if (warp == 0) {
-                // P: largest load, lowest id
-                unsigned long long bk = ~0ull;
-                unsigned bi = kNone;
+                // P: largest load, lowest id; Q0: smallest (load, id) other than P
+                unsigned long long kp = 0ull;
                 for (int b = lane; b < nb; b += kWarp) {
-                    const unsigned long long k = ~okey(s_load[b]);
-                    if (k < bk) {
-                        bk = k;
-                        bi = (unsigned)b;
-                    }
+                    const unsigned long long k = (s_load[b] << kIdBits) | (kIdMask - b);
+                    kp = k > kp ? k : kp;
                 }
-                const unsigned P = warp_min_key_id(bk, bi);
-                const unsigned Q0 = warp_next_bin(s_load, nb, (int)P, 0ull, -1);
+                kp = warp_max64(kp);
+                const int P = (int)(kIdMask - (kp & kIdMask));
+                unsigned long long kq = ~0ull;
+                for (int b = lane; b < nb; b += kWarp) {
+                    const unsigned long long k = (s_load[b] << kIdBits) | (unsigned long long)b;
+                    if (b != P && k < kq) kq = k;
+                }
+                kq = warp_min64(kq);
                 if (lane == 0) {
-                    s_P = (int)P;
-                    s_Q = (int)Q0;
+                    s_P = P;
+                    s_Q = kq == ~0ull ? (int)kNone : (int)(kq & kIdMask);
                     s_np = 0;
                     s_found = kNone;
                 }
             }
             __syncthreads();
             const int P = s_P;
-            if (!(s_load[P] > thr)) break;
+            if (__ull2double_rn(s_load[P]) <= thr) break;
             if (tid == 0) ++s_iters;
             for (int v = tid; v < nv; v += kBalThreads)
-                if (s_assign[v] == P) s_pl[atomicAdd(&s_np, 1)] = v;
+                if (s_assign[v] == P) s_ul[atomicAdd(&s_np, 1)] = v;
             __syncthreads();
             const int np = s_np;
             for (int i = tid; i < np; i += kBalThreads) {
-                const int vi = s_pl[i];
-                const unsigned long long ki = okey(p.cost[vi]);
+                const int vi = s_ul[i];
+                const long long qi = s_q[vi];
                 int r = 0;
                 for (int j = 0; j < np; ++j) {
-                    const int vj = s_pl[j];
-                    const unsigned long long kj = okey(p.cost[vj]);
-                    r += (kj > ki) || (kj == ki && vj < vi);
+                    const int vj = s_ul[j];
+                    const long long qj = s_q[vj];
+                    r += (qj > qi) || (qj == qi && vj < vi);
                 }
                 s_ps[r] = vi;
             }
@@ -412,19 +417,20 @@ __global__ void __launch_bounds__(kBalThreads, 1) k_balance(const DevBal p, int 
             // bin is at least as loaded), so later bins only try swaps.
             const int Q0 = s_Q;
             if (Q0 < nb) {
-                const double lq = s_load[Q0];
+                const unsigned long long lq = s_load[Q0];
                 for (int i = tid; i < np; i += kBalThreads) {
-                    const double c = p.cost[s_ps[i]];
-                    if (c > 0.0 && __dadd_rn(lq, c) <= thr) atomicMin(&s_found, (unsigned)i);
+                    const long long c = s_q[s_ps[i]];
+                    if (c > 0 && __ull2double_rn(lq + (unsigned long long)c) <= thr)
+                        atomicMin(&s_found, (unsigned)i);
                 }
             }
             __syncthreads();
             if (s_found != kNone) {
                 if (tid == 0) {
                     const int o = s_ps[s_found];
-                    const double c = p.cost[o];
-                    s_load[P] = __dsub_rn(s_load[P], c);
-                    s_load[Q0] = __dadd_rn(s_load[Q0], c);
+                    const unsigned long long c = (unsigned long long)s_q[o];
+                    s_load[P] -= c;
+                    s_load[Q0] += c;
                     s_assign[o] = Q0;
                 }
                 __syncthreads();
@@ -437,48 +443,49 @@ __global__ void __launch_bounds__(kBalThreads, 1) k_balance(const DevBal p, int 
                 if (tid == 0) s_nq = 0;
                 __syncthreads();
                 for (int v = tid; v < nv; v += kBalThreads)
-                    if (s_assign[v] == Q) s_ql[atomicAdd(&s_nq, 1)] = v;
+                    if (s_assign[v] == Q) s_ul[atomicAdd(&s_nq, 1)] = v;
                 __syncthreads();
                 const int nq = s_nq;
                 for (int i = tid; i < nq; i += kBalThreads) {
-                    const int vi = s_ql[i];
-                    const unsigned long long ki = okey(p.cost[vi]);
+                    const int vi = s_ul[i];
+                    const long long qi = s_q[vi];
                     int r = 0;
                     for (int j = 0; j < nq; ++j) {
-                        const int vj = s_ql[j];
-                        const unsigned long long kj = okey(p.cost[vj]);
-                        r += (kj < ki) || (kj == ki && vj < vi);
+                        const int vj = s_ul[j];
+                        const long long qj = s_q[vj];
+                        r += (qj < qi) || (qj == qi && vj < vi);
                     }
                     s_qs[r] = vi;
                 }
                 __syncthreads();
                 // the first pair (o-order, then o'-order) of least
-                // max(load P - d, load Q + d) below load P
-                const double LP = s_load[P], LQ = s_load[Q];
-                unsigned long long bk = ~0ull;
-                unsigned bi = ~0u;
+                // m = max(load P - d, load Q + d) below load P: the least m,
+                // then the least pair index among the holders of it
+                const long long LP = (long long)s_load[P], LQ = (long long)s_load[Q];
+                unsigned long long bm = ~0ull, be = ~0ull;
                 const long long npairs = (long long)np * nq;
                 for (long long e = tid; e < npairs; e += kBalThreads) {
                     const int i = (int)(e / nq), j = (int)(e % nq);
-                    const double co = p.cost[s_ps[i]], c2 = p.cost[s_qs[j]];
-                    if (!(co > c2)) continue;
-                    const double d = __dsub_rn(co, c2);
-                    const double a = __dsub_rn(LP, d), b = __dadd_rn(LQ, d);
-                    const double m = (a < b) ? b : a;
+                    const long long qo = s_q[s_ps[i]], q2 = s_q[s_qs[j]];
+                    if (!(qo > q2)) continue;
+                    const long long d = qo - q2;
+                    const long long a = LP - d, b = LQ + d;
+                    const long long m = a < b ? b : a;
                     if (!(m < LP)) continue;
-                    const unsigned long long k = okey(m);
-                    if (k < bk || (k == bk && (unsigned)e < bi)) {
-                        bk = k;
-                        bi = (unsigned)e;
+                    if ((unsigned long long)m < bm ||
+                        ((unsigned long long)m == bm && (unsigned long long)e < be)) {
+                        bm = (unsigned long long)m;
+                        be = (unsigned long long)e;
                     }
                 }
-                block_min_key_idx(bk, bi, s_wk, s_wi);
-                if (bi != ~0u) {
+                const unsigned long long gm = block_min64(bm, s_w);
+                const unsigned long long ge = block_min64(bm == gm ? be : ~0ull, s_w);
+                if (gm != ~0ull) {
                     if (tid == 0) {
-                        const int o = s_ps[bi / nq], o2 = s_qs[bi % nq];
-                        const double d = __dsub_rn(p.cost[o], p.cost[o2]);
-                        s_load[P] = __dsub_rn(s_load[P], d);
-                        s_load[Q] = __dadd_rn(s_load[Q], d);
+                        const int o = s_ps[ge / nq], o2 = s_qs[ge % nq];
+                        const unsigned long long d = (unsigned long long)(s_q[o] - s_q[o2]);
+                        s_load[P] -= d;
+                        s_load[Q] += d;
                         s_assign[o] = Q;
                         s_assign[o2] = P;
                     }
@@ -487,8 +494,14 @@ __global__ void __launch_bounds__(kBalThreads, 1) k_balance(const DevBal p, int 
                     break;
                 }
                 if (warp == 0) {
-                    const unsigned nQ = warp_next_bin(s_load, nb, P, okey(s_load[Q]), Q);
-                    if (lane == 0) s_Q = (int)nQ;
+                    const unsigned long long after = (s_load[Q] << kIdBits) | (unsigned long long)Q;
+                    unsigned long long kq = ~0ull;
+                    for (int b = lane; b < nb; b += kWarp) {
+                        const unsigned long long k = (s_load[b] << kIdBits) | (unsigned long long)b;
+                        if (b != P && k > after && k < kq) kq = k;
+                    }
+                    kq = warp_min64(kq);
+                    if (lane == 0) s_Q = kq == ~0ull ? (int)kNone : (int)(kq & kIdMask);
                 }
                 __syncthreads();
                 Q = s_Q;
@@ -499,37 +512,27 @@ __global__ void __launch_bounds__(kBalThreads, 1) k_balance(const DevBal p, int 
     __syncthreads();
 
     // migrations, new table, predicted max/mean, record
-    int mig = 0;
-    unsigned long long cmax = okey(0.0);
+    for (int b = tid; b < nb; b += kBalThreads) s_load[b] = 0ull;
+    __syncthreads();
+    unsigned long long mig = 0, qmax = 0, tot = 0;
     for (int v = tid; v < nv; v += kBalThreads) {
         mig += s_assign[v] != p.assign[v];
-        const unsigned long long k = okey(p.cost[v]);
-        cmax = k > cmax ? k : cmax;
+        const unsigned long long q = (unsigned long long)s_q[v];
+        qmax = q > qmax ? q : qmax;
+        tot += q;
+        atomicAdd(&s_load[s_assign[v]], q);
     }
-    mig = block_sum_int(mig, s_wsum);
-    {
-        unsigned long long nk = ~cmax;
-        unsigned ni = 0u;
-        block_min_key_idx(nk, ni, s_wk, s_wi);
-        cmax = ~nk;
-    }
+    mig = block_sum64(mig, s_w);
+    tot = block_sum64(tot, s_w);
+    qmax = ~block_min64(~qmax, s_w);
+    unsigned long long lmax = 0;
+    for (int b = tid; b < nb; b += kBalThreads) lmax = s_load[b] > lmax ? s_load[b] : lmax;
+    lmax = ~block_min64(~lmax, s_w);
     for (int v = tid; v < nv; v += kBalThreads) p.assign[v] = s_assign[v];
-    bin_loads_dev(s_assign, p.cost, nv, nb, s_load);
     if (tid == 0) {
-        double total = 0.0;
-        unsigned long long mk = 0ull;
-        int mb = 0;
-        for (int b = 0; b < nb; ++b) {
-            total = __dadd_rn(total, s_load[b]);
-            const unsigned long long k = okey(s_load[b]);
-            if (k > mk) {
-                mk = k;
-                mb = b;
-            }
-        }
-        const double mean = __ddiv_rn(total, (double)nb);
-        const double pred = mean > 0.0 ? __ddiv_rn(s_load[mb], mean) : 1.0;
-        const double cm = from_okey(cmax);
+        const double mean = __ddiv_rn(__ull2double_rn(tot), (double)nb);
+        const double pred = mean > 0.0 ? __ddiv_rn(__ull2double_rn(lmax), mean) : 1.0;
+        const double cm = __ull2double_rn(qmax);
         const double floor = mean > 0.0 ? (cm > mean ? cm : mean) / mean : 1.0;
         const long long n = p.state[kStHist];
         double *row = p.hist + (size_t)(n % kBalHist) * kBalHistCols;
@@ -548,14 +551,14 @@ __global__ void __launch_bounds__(kBalThreads, 1) k_balance(const DevBal p, int 
 }
 
 __global__ void __launch_bounds__(kItemThreads) k_items(const DevBal p) {
-    __shared__ int s_w[kItemThreads / kWarp];
+    __shared__ unsigned long long s_w[kItemThreads / kWarp + 1];
     __shared__ int s_wscan[kItemThreads / kWarp];
     const int b = blockIdx.x;
     const int lane = threadIdx.x % kWarp, warp = threadIdx.x / kWarp;
-    int acc = 0;
+    unsigned long long acc = 0;
     for (int v = threadIdx.x; v < p.nvps; v += kItemThreads)
-        if (p.assign[v] < b) acc += p.nchunks[v];
-    const int start = block_sum_int(acc, s_w);
+        if (p.assign[v] < b) acc += (unsigned long long)p.nchunks[v];
+    const int start = (int)block_sum64(acc, s_w);
     if (threadIdx.x == 0) {
         p.bin_start[b] = start;
         if (b == p.nbins - 1) p.bin_start[p.nbins] = p.nitems;
@@ -586,26 +589,41 @@ __global__ void __launch_bounds__(kItemThreads) k_items(const DevBal p) {
     }
 }
 
+__global__ void k_set_kc(GridDev *g, const int32_t *kc) { g->kc = kc; }
+
 }  // namespace
 
-size_t dev_balance_smem(int nvps, int nbins) {
-    return sizeof(double) * (size_t)nbins + sizeof(int) * 5 * (size_t)nvps;
+cudaError_t dev_set_kc(GridDev *g, const int32_t *kc, cudaStream_t s) {
+    k_set_kc<<<1, 1, 0, s>>>(g, kc);
+    return cudaGetLastError();
 }
 
-// The attribute is per function: set the largest size any ctx can need, so
-// that one ctx never lowers the limit under another.
+size_t dev_balance_smem(int nvps, int nbins) {
+    return sizeof(long long) * (size_t)nvps + sizeof(unsigned long long) * 4 * (size_t)nbins +
+           sizeof(int) * 4 * (size_t)nvps;
+}
+
+static size_t prep_smem(int nvps) { return sizeof(long long) * (size_t)nvps; }
+
+// The attributes are per function: set the largest sizes any ctx can need,
+// so that one ctx never lowers the limit under another.
 cudaError_t dev_balance_init() {
-    return cudaFuncSetAttribute(k_balance, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)dev_balance_smem(kDevBalMaxVps, kDevBalMaxBins));
+    cudaError_t e = cudaFuncSetAttribute(k_balance, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)dev_balance_smem(kDevBalMaxVps, kDevBalMaxBins));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_prep, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)prep_smem(kDevBalMaxVps));
+    return e;
 }
 
 cudaError_t dev_measure(const DevBal &p, cudaStream_t s) {
-    k_measure<<<(p.nvps + 255) / 256, 256, 0, s>>>(p);
+    k_measure<<<(p.nvps + kMeasThreads - 1) / kMeasThreads, kMeasThreads, 0, s>>>(p);
     return cudaGetLastError();
 }
 
 cudaError_t dev_rebalance(const DevBal &p, int strategy, cudaStream_t s) {
-    k_rank<<<(p.nvps + kRankThreads - 1) / kRankThreads, kRankThreads, 0, s>>>(p, strategy);
+    k_prep<<<(p.nvps + kPrepThreads - 1) / kPrepThreads, kPrepThreads, prep_smem(p.nvps), s>>>(
+        p, strategy);
     k_balance<<<1, kBalThreads, dev_balance_smem(p.nvps, p.nbins), s>>>(p, strategy);
     k_items<<<p.nbins, kItemThreads, 0, s>>>(p);
     return cudaGetLastError();

@@ -125,6 +125,7 @@ struct DevBal {
     double *last;                   // [nvps] last measured cost, ns per step
     int32_t *assign;                // [nvps] VP -> processor
     int32_t *order;                 // [nvps] scratch: VPs by (cost desc, id asc)
+    long long *q;                   // [nvps] scratch: costs on the fixed-point grid
     const int32_t *spatial;         // [nvps] VPs in spatial order
     const int32_t *nchunks;         // [nvps] work items per VP
     long long *state;               // [kStWords]
@@ -137,6 +138,8 @@ size_t dev_balance_smem(int nvps, int nbins);
 cudaError_t dev_balance_init();
 cudaError_t dev_measure(const DevBal &p, cudaStream_t s);
 cudaError_t dev_rebalance(const DevBal &p, int strategy, cudaStream_t s);
+// Point a grid's k_c source at a new array, in stream order.
+cudaError_t dev_set_kc(GridDev *g, const int32_t *kc, cudaStream_t s);
 
 // Text returned by lb_last_error(NULL) (calls without a ctx).
 void set_ctxless_error(const char *msg);

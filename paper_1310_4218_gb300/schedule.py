@@ -17,10 +17,17 @@ class Schedule:
     max/mean load of the period exceeds it -- the threshold-triggered
     migration the paper plans as future work (Sec. VII): measurements stay
     on (they are free on the device), migrations happen only when needed.
+
+    device: measure and rebalance with the device balancer
+    (lb_device_measure / lb_device_rebalance): nothing waits for the host
+    between periods; per-period records come from lb_balance_history.
     """
 
     def __init__(self, sim, period, strategy="auto", kc_epochs=None, epoch_steps=0,
-                 threshold=None):
+                 threshold=None, device=False):
+        if device and threshold is not None:
+            raise ValueError("threshold-triggered rebalancing runs on the host balancer")
+        self.device = device
         self.sim = sim
         self.period = int(period)
         self.strategy = strategy
@@ -64,6 +71,12 @@ class Schedule:
 
     def balance(self):
         """Measure the loads of the steps since the last call and rebalance."""
+        if self.device:
+            L.lb_device_measure(self.sim.ctx)
+            L.lb_device_rebalance(self.sim.ctx, self.strategy)
+            rec = {"t": self.t, "device": True}
+            self.history.append(rec)
+            return rec
         cost, busy = self.sim.measure()
         used = busy[busy > 0]
         rec = {"t": self.t,
@@ -80,6 +93,12 @@ class Schedule:
             rec["predicted_max_over_mean"] = pred
         self.history.append(rec)
         return rec
+
+    def device_history(self):
+        """Records of the device rebalances (synchronises): dicts with the
+        columns of lb.BALANCE_HISTORY_COLUMNS."""
+        rows = L.lb_balance_history(self.sim.ctx)
+        return [dict(zip(L.BALANCE_HISTORY_COLUMNS, map(float, r))) for r in rows]
 
     def run_period(self):
         self.run_steps(self.period)

@@ -63,6 +63,8 @@ class Simulation:
 
     def set_kc(self, grid, kc_array):
         t = torch.as_tensor(np.ascontiguousarray(kc_array, dtype=np.int32)).to(self.device)
+        # the copy ran on torch's current stream; the ctx stream reads the array
+        torch.cuda.current_stream(self.device).synchronize()
         L.lb_set_kc(self.ctx, grid, t.data_ptr())
         self.kc[grid] = t
 

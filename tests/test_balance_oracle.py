@@ -136,3 +136,33 @@ def test_ordered_greedy_is_graham_list_scheduling():
         assert max(B.bin_loads(costs, a, m)) <= (2 - 1 / m) * brute_force_makespan(costs, m) + 1e-12
     # equal costs in id order: round robin
     assert B.greedy_ordered([1.0] * 5, 2, list(range(5))) == [0, 1, 0, 1, 0]
+
+
+def test_fixed_point_grid_keeps_small_integer_ratios_exactly():
+    q = B.fixed_point([2.0] * 8 + [1.0] * 8)
+    assert set(q) == {2 ** 47, 2 ** 46}          # 16 VPs: L = 5, max 2.0 = 0.5 * 2^2
+    assert B.fixed_point([0.0, 0.0]) == [0, 0]
+    assert B.fixed_point([0.0, -0.0, 3.0])[:2] == [0, 0]
+
+
+@pytest.mark.parametrize("seed", range(20))
+def test_fixed_point_grid_bounds(seed):
+    """Largest cost in [2^(52-L), 2^(53-L)], every total below 2^53, each
+    cost within half a grid step, order preserved."""
+    rng = random.Random(500 + seed)
+    n = rng.choice([1, 2, 3, 7, 150, 4096, 8191, 8192, 20000])
+    scale = 10.0 ** rng.randint(-300, 300)
+    costs = [rng.lognormvariate(0, 2) * scale for _ in range(n)]
+    if n > 3:
+        costs[rng.randrange(n)] = 0.0
+    q = B.fixed_point(costs)
+    L = n.bit_length()
+    assert 2 ** (52 - L) <= max(q) <= 2 ** (53 - L)
+    assert sum(q) < 2 ** 53
+    import math
+    _, x = math.frexp(max(costs))
+    e = 53 - L - x
+    for c, k in zip(costs[:200], q[:200]):
+        assert abs(math.ldexp(c, e) - k) <= 0.5
+    order = sorted(range(n), key=lambda v: costs[v])
+    assert all(q[order[i]] <= q[order[i + 1]] for i in range(min(n, 500) - 1))

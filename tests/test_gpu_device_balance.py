@@ -292,3 +292,31 @@ def test_device_balancer_refusals():
         lb.lb_device_measure(big.ctx)
     assert ei.value.status == lb.LB_EINVAL
     big.close()
+
+
+def test_schedule_in_device_mode():
+    """Schedule(device=True): periods of steps, device measurement and device
+    rebalancing with a k_c array re-drawn between segments; the values are
+    the oracle's and one history row is kept per period."""
+    from paper_1310_4218_gb300.schedule import Schedule
+    from workloads.kcfield import lognormal_kc
+    g = Grid(96, 64, 32, kc_disk=False)
+    q = round_to_storage(random_field(g, 61), "f32")
+    vps = regular_blocks(96, 64, 8, 8)
+    kcs = {e: [lognormal_kc(96, 64, 99, e)] for e in range(3)}
+    from paper_1310_4218_gb300 import lb
+    from paper_1310_4218_gb300.sim import Simulation
+    sim = Simulation([g], [q], vps, kc_arrays=kcs[0], options=lb.lb_default_options())
+    sch = Schedule(sim, 4, "auto_spatial", kc_epochs=kcs, epoch_steps=5, device=True)
+    sch.run(12)
+    hist = sch.device_history()
+    out = sim.field(0)
+    sim.close()
+    assert [h["step"] for h in hist] == [4, 8, 12]
+    assert [h["strategy"] for h in hist] == [lb.LB_GREEDY_SPATIAL, lb.LB_REFINE_SWAP,
+                                             lb.LB_REFINE_SWAP]
+    kc_of = lambda t: kcs[t // 5][0]
+    ref = q
+    for t in range(12):
+        ref, _ = oracle.run(g.oracle(kc_of(t)), ref, 1, t0=t)
+    assert normwise(out, ref) <= 1e-5

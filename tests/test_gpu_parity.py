@@ -277,8 +277,10 @@ def test_measured_costs_follow_kc():
     assert coef[1] > 0 and r2 > 0.85, (coef, r2)
     _, pred = sim.rebalance("greedy")
     from oracle import balance as B
+    # the mean load is summed per processor, so two assignments at the same
+    # makespan (here: the heaviest VP alone) differ by rounding
     assert pred <= B.max_over_mean(list(cost), B.static_blocks(len(vps), sim.info().nprocs),
-                                   sim.info().nprocs)
+                                   sim.info().nprocs) * (1 + 1e-12)
     sim.close()
 
 
