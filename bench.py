@@ -5,13 +5,19 @@ CPU-oracle baselines.
 One benchmark step = one rebalance period: `period` time steps of every VP
 (advection, k_c Thomas sweeps, store, global sum, per-VP cost stamps, grid
 barrier) in one persistent launch, then the load measurement and the
-rebalance.  The headline strategy is auto_spatial+steal: GreedyLB's rule
-with the VPs in spatial order on the first call, RefineSwapLB after, and
-processors that finish their VPs early taking the next items of the
-processor with the most left.  The static table, the paper-order
-GreedyLB/RefineSwapLB schedule, plain auto_spatial and the atomic queue are
-measured the same way and reported beside it.  The k_c array is
-re-drawn every 50 time steps as the workload prescribes.
+rebalance.  The headline strategy is greedy_blocked+steal+dev: the measured
+costs (Sec. V) feed GreedyLB applied block by block to the VPs in spatial
+order (each processor takes one VP of every block of nprocs, heaviest to
+least loaded), processors that finish early take items of the processor
+with the most left, and measurement and balancer run as device kernels
+behind the step launch (no host round trip).  The static table, the
+paper's GreedyLB-then-RefineSwapLB schedule, its spatial variant and the
+atomic queue, with host or device balancing, are measured the same way and
+reported beside it.  The k_c array is re-drawn every 50 time steps as the
+workload prescribes.
+
+Strategy names: an lb_strategy name, optionally followed by "+steal"
+(end-of-step work stealing) and "+dev" (device balancer).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--workload NAME] [--period P] [--strategy auto|static|queue|...]
@@ -46,7 +52,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--period", type=int, default=10)
-    ap.add_argument("--strategy", default="auto_spatial+steal")
+    ap.add_argument("--strategy", default="greedy_blocked+steal+dev")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--threads", type=int, default=0, help="threads per processor (0: default)")
@@ -292,10 +298,14 @@ class StrategyRun:
     def balance(self, tag):
         """Load measurement (Sec. V) and the balancer call (Sec. VI)."""
         if self.dev_mode:
-            # enqueued only: measurement, rank, balancer, table kernels
+            # enqueued only: measurement, cost rounding and ranks, balancer,
+            # table kernels (the queue has no table: measurement and record)
             self.lb.lb_device_measure(self.sim.ctx)
+            if self.strategy == "queue" and self.info.strategy != self.lb.LB_ATOMIC_QUEUE:
+                self.sim.rebalance("queue")       # enter queue mode once
+                self.info = self.sim.info()
             self.lb.lb_device_rebalance(self.sim.ctx, self.strategy)
-            self.kernels += 4
+            self.kernels += 3 if self.strategy == "queue" else 4
             self.dev_tags.append(tag)
             return
         cost, busy = self.sim.measure()
@@ -462,7 +472,8 @@ def main():
     compare = {}
     if not args.no_compare:
         for st in [x for x in ("static", "auto", "queue", "auto_spatial", "auto_spatial+steal",
-                               "static+steal", "auto_spatial+steal+dev", "auto_spatial+dev")
+                               "static+steal", "queue+dev", "auto+dev", "auto_spatial+steal+dev",
+                               "greedy_blocked+dev", "greedy_blocked+steal+dev")
                    if x != args.strategy]:
             r2 = StrategyRun(w, fields, epochs, kc_dev, args, dev, stream, st)
             r2.warmup(args.warmup)

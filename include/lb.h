@@ -82,6 +82,14 @@ typedef enum { LB_F64 = 0, LB_F32 = 1, LB_BF16 = 2 } lb_dtype;
  *                   still in L2 when it is needed.
  *   LB_AUTO_SPATIAL LB_GREEDY_SPATIAL on the first rebalance, RefineSwapLB
  *                   afterwards
+ *   LB_GREEDY_BLOCKED GreedyLB applied block by block to the VPs in spatial
+ *                   order: within each run of nprocs consecutive VPs, the
+ *                   heaviest goes to the least-loaded processor, the next
+ *                   heaviest to the next, one VP per processor.  Every
+ *                   processor takes one VP of each block, so all sweep the
+ *                   grids in lockstep; the spread of processor loads stays
+ *                   below the largest VP cost.  (With nvps <= nprocs and
+ *                   positive costs it is LB_GREEDY.)
  */
 typedef enum {
     LB_STATIC = 0,
@@ -90,7 +98,8 @@ typedef enum {
     LB_ATOMIC_QUEUE = 3,
     LB_AUTO = 4,
     LB_GREEDY_SPATIAL = 5,
-    LB_AUTO_SPATIAL = 6
+    LB_AUTO_SPATIAL = 6,
+    LB_GREEDY_BLOCKED = 7
 } lb_strategy;
 
 /*
@@ -191,8 +200,9 @@ lb_status lb_rebalance(lb_ctx *ctx, int32_t strategy, int32_t *migrations,
 
 /*
  * Host-only planning with the library's balancers (no ctx, no GPU): the
- * assignment `strategy` (LB_STATIC, LB_GREEDY, LB_REFINE_SWAP or
- * LB_GREEDY_SPATIAL, which here takes the VPs in id order) produces for
+ * assignment `strategy` (LB_STATIC, LB_GREEDY, LB_REFINE_SWAP,
+ * LB_GREEDY_SPATIAL or LB_GREEDY_BLOCKED, the last two taking the VPs in id
+ * order here) produces for
  * FP64 costs[nvps] on nprocs processors.  current[nvps] is the present
  * assignment (needed by LB_REFINE_SWAP and for counting migrations; may be
  * NULL, meaning the static placement).  out[nvps] receives the assignment;
@@ -274,13 +284,17 @@ lb_status lb_graph_destroy(lb_ctx *ctx, void *graph_exec);
  * lb_device_rebalance remaps VPs from the device cost average (Sec. VI)
  * and rewrites the processor tables in device memory; the next step uses
  * them.  strategy: LB_STATIC, LB_GREEDY, LB_REFINE_SWAP, LB_AUTO,
- * LB_GREEDY_SPATIAL or LB_AUTO_SPATIAL (LB_AUTO* decide on the device, from
+ * LB_GREEDY_SPATIAL, LB_AUTO_SPATIAL or LB_GREEDY_BLOCKED (LB_AUTO* decide
+ * on the device, from
  * the number of table rebalances so far).  For equal costs and current
  * assignment the new assignment equals lb_rebalance's bit for bit.  Its
  * migrations and predicted max/mean are recorded in the balance history.
  * Without costs (never measured or set) the next synchronising call
- * returns LB_ESTATE.  Not available in LB_ATOMIC_QUEUE mode (LB_ESTATE) or
- * for more than 8192 VPs or 1024 processors (LB_EINVAL).
+ * returns LB_ESTATE.  In LB_ATOMIC_QUEUE mode only strategy LB_ATOMIC_QUEUE
+ * is accepted (LB_ESTATE otherwise): it changes nothing and records the
+ * period in the balance history, with the granularity floor as its
+ * predicted max/mean.  Not available for more than 8192 VPs or 1024
+ * processors (LB_EINVAL).
  *
  * Host calls that read or change costs or the assignment (lb_measure_loads,
  * lb_rebalance, lb_set_costs, lb_get_assignment, lb_set_assignment,

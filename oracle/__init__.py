@@ -11,9 +11,9 @@ library never calls it.
 from .step import (OracleGrid, kc_field, thomas, advect, step, run, run_window,
                    compensated_sum, build_oracle)
 from .balance import (static_blocks, greedy, greedy_ordered, refine_swap, migrations, bin_loads,
-                      max_over_mean, fixed_point)
+                      max_over_mean, fixed_point, greedy_blocked)
 
 __all__ = ["OracleGrid", "kc_field", "thomas", "advect", "step", "run",
            "run_window", "compensated_sum", "build_oracle", "static_blocks",
            "greedy", "greedy_ordered", "refine_swap", "migrations", "bin_loads", "max_over_mean",
-           "fixed_point"]
+           "fixed_point", "greedy_blocked"]

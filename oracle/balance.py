@@ -20,6 +20,10 @@ whatever order it adds in.
   greedy_ordered -- GreedyLB's rule (each object to the least loaded
                     processor) with the objects taken in a given order
                     instead of heaviest first: Graham's list scheduling.
+  greedy_blocked -- GreedyLB applied to consecutive blocks of nbins objects
+                    of a given order: within a block the heaviest object
+                    goes to the least loaded processor, the next heaviest to
+                    the next, ... (one object per processor per block).
 """
 import heapq
 import math
@@ -79,6 +83,23 @@ def greedy_ordered(costs, nbins, order):
     """Objects in the given order (a permutation of VP ids), each to the bin
     with the least load so far (ties: lowest bin id)."""
     return _list_schedule(fixed_point(costs), nbins, order)
+
+
+def greedy_blocked(costs, nbins, order):
+    """Objects in the given order, in consecutive blocks of nbins: within a
+    block, objects by (cost descending, id ascending) go to the bins by
+    (load ascending, id ascending), one each; loads on the fixed-point grid.
+    A short last block fills the least loaded bins."""
+    q = fixed_point(costs)
+    loads = [0] * nbins
+    assign = [0] * len(q)
+    for base in range(0, len(order), nbins):
+        block = sorted(order[base:base + nbins], key=lambda v: (-q[v], v))
+        bins = sorted(range(nbins), key=lambda b: (loads[b], b))
+        for v, b in zip(block, bins):
+            assign[v] = b
+            loads[b] += q[v]
+    return assign
 
 
 def _list_schedule(q, nbins, order):

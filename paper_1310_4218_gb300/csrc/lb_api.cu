@@ -732,14 +732,20 @@ static DevBal make_devbal(lb_ctx *ctx) {
 
 static bool table_strategy(int s) {
     return s == LB_STATIC || s == LB_GREEDY || s == LB_REFINE_SWAP || s == LB_AUTO ||
-           s == LB_GREEDY_SPATIAL || s == LB_AUTO_SPATIAL;
+           s == LB_GREEDY_SPATIAL || s == LB_AUTO_SPATIAL || s == LB_GREEDY_BLOCKED;
 }
 
 static lb_status devbal_check(lb_ctx *ctx, int strategy, bool need_strategy) {
     if (!ctx->devbal_off.empty())
         return fail(ctx, LB_EINVAL, "device balancer unavailable: " + ctx->devbal_off);
+    if (need_strategy && strategy == LB_ATOMIC_QUEUE) {
+        if (!ctx->queue_mode)
+            return fail(ctx, LB_ESTATE, "device balancer: LB_ATOMIC_QUEUE records queue-mode periods; "
+                                        "enter queue mode with lb_rebalance");
+        return LB_OK;
+    }
     if (need_strategy && !table_strategy(strategy))
-        return fail(ctx, LB_EINVAL, "device balancer: strategy must build a processor table");
+        return fail(ctx, LB_EINVAL, "device balancer: unknown strategy");
     if (need_strategy && ctx->queue_mode)
         return fail(ctx, LB_ESTATE, "device balancer: ctx is in atomic-queue mode (leave it with lb_rebalance)");
     return LB_OK;
@@ -922,13 +928,15 @@ extern "C" lb_status lb_plan(int32_t strategy, const double *costs, int32_t nvps
     if (strategy == LB_STATIC) static_blocks(nvps, nprocs, res);
     else if (strategy == LB_GREEDY) greedy(c, nprocs, res);
     else if (strategy == LB_REFINE_SWAP) refine_swap(c, cur, nprocs, refine_tol, res);
-    else if (strategy == LB_GREEDY_SPATIAL) {
+    else if (strategy == LB_GREEDY_SPATIAL || strategy == LB_GREEDY_BLOCKED) {
         std::vector<int> order(nvps);
         for (int v = 0; v < nvps; ++v) order[v] = v;
-        greedy_ordered(c, nprocs, order, res);
+        if (strategy == LB_GREEDY_SPATIAL) greedy_ordered(c, nprocs, order, res);
+        else greedy_blocked(c, nprocs, order, res);
     } else
         return fail(nullptr, LB_EINVAL,
-                    "lb_plan: strategy must be STATIC, GREEDY, REFINE_SWAP or GREEDY_SPATIAL");
+                    "lb_plan: strategy must be STATIC, GREEDY, REFINE_SWAP, GREEDY_SPATIAL or "
+                    "GREEDY_BLOCKED");
     for (int v = 0; v < nvps; ++v) out[v] = res[v];
     if (mig) *mig = migrations(cur, res);
     if (pred) *pred = max_over_mean(c, res, nprocs);
@@ -948,7 +956,7 @@ extern "C" lb_status lb_set_costs(lb_ctx *ctx, const double *costs) {
 
 extern "C" lb_status lb_rebalance(lb_ctx *ctx, int32_t strategy, int32_t *mig, double *pred) {
     if (!ctx) return fail(nullptr, LB_EINVAL, "ctx is NULL");
-    if (strategy < LB_STATIC || strategy > LB_AUTO_SPATIAL) return fail(ctx, LB_EINVAL, "unknown strategy");
+    if (strategy < LB_STATIC || strategy > LB_GREEDY_BLOCKED) return fail(ctx, LB_EINVAL, "unknown strategy");
     {
         lb_status ps = pull_state(ctx);
         if (ps != LB_OK) return ps;
@@ -957,7 +965,8 @@ extern "C" lb_status lb_rebalance(lb_ctx *ctx, int32_t strategy, int32_t *mig, d
     if (strategy == LB_AUTO_SPATIAL)
         strategy = ctx->rebalances == 0 ? LB_GREEDY_SPATIAL : LB_REFINE_SWAP;
     const int nv = (int)ctx->vps.size();
-    if ((strategy == LB_GREEDY || strategy == LB_REFINE_SWAP || strategy == LB_GREEDY_SPATIAL) &&
+    if ((strategy == LB_GREEDY || strategy == LB_REFINE_SWAP || strategy == LB_GREEDY_SPATIAL ||
+         strategy == LB_GREEDY_BLOCKED) &&
         !ctx->have_costs)
         return fail(ctx, LB_ESTATE, "no measured costs yet");
     std::vector<int> res;
@@ -977,6 +986,7 @@ extern "C" lb_status lb_rebalance(lb_ctx *ctx, int32_t strategy, int32_t *mig, d
         if (strategy == LB_STATIC) static_blocks(nv, ctx->nbins, res);
         else if (strategy == LB_GREEDY) greedy(ctx->cost, ctx->nbins, res);
         else if (strategy == LB_GREEDY_SPATIAL) greedy_ordered(ctx->cost, ctx->nbins, spatial_order(ctx), res);
+        else if (strategy == LB_GREEDY_BLOCKED) greedy_blocked(ctx->cost, ctx->nbins, spatial_order(ctx), res);
         else refine_swap(ctx->cost, ctx->assign, ctx->nbins, ctx->opt.refine_tol, res);
         m = migrations(ctx->assign, res);
         pr = ctx->have_costs ? max_over_mean(ctx->cost, res, ctx->nbins) : 1.0;

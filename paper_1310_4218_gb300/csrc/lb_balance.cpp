@@ -105,6 +105,36 @@ void greedy_ordered(const std::vector<double> &costs, int nbins, const std::vect
     list_schedule(q, nbins, order, out);
 }
 
+// GreedyLB over consecutive blocks of nbins objects of `order`: within a
+// block, objects by (cost desc, id asc) to bins by (load asc, id asc), one
+// each.  Every processor takes one object of each full block, so with the
+// VPs in spatial order all processors sweep the grid in lockstep; the load
+// spread stays below the largest cost.
+void greedy_blocked(const std::vector<double> &costs, int nbins, const std::vector<int> &order,
+                    std::vector<int> &out) {
+    std::vector<long long> q, loads(nbins, 0);
+    fixed_point(costs, q);
+    out.assign(q.size(), 0);
+    std::vector<int> block, bins(nbins);
+    for (size_t base = 0; base < order.size(); base += (size_t)nbins) {
+        const size_t end = std::min(order.size(), base + (size_t)nbins);
+        block.assign(order.begin() + base, order.begin() + end);
+        std::sort(block.begin(), block.end(), [&](int a, int b) {
+            if (q[a] != q[b]) return q[a] > q[b];
+            return a < b;
+        });
+        std::iota(bins.begin(), bins.end(), 0);
+        std::sort(bins.begin(), bins.end(), [&](int a, int b) {
+            if (loads[a] != loads[b]) return loads[a] < loads[b];
+            return a < b;
+        });
+        for (size_t k = 0; k < block.size(); ++k) {
+            out[block[k]] = bins[k];
+            loads[bins[k]] += q[block[k]];
+        }
+    }
+}
+
 // RefineSwapLB (Sec. VI-B): move objects off the most loaded processor
 // toward the mean; swap when no single move fits.  The paper gives no
 // constants; the reading implemented (q: fixed-point costs):

@@ -16,6 +16,8 @@ int migrations(const std::vector<int> &a, const std::vector<int> &b);
 void greedy(const std::vector<double> &costs, int nbins, std::vector<int> &out);
 void greedy_ordered(const std::vector<double> &costs, int nbins, const std::vector<int> &order,
                     std::vector<int> &out);
+void greedy_blocked(const std::vector<double> &costs, int nbins, const std::vector<int> &order,
+                    std::vector<int> &out);
 void refine_swap(const std::vector<double> &costs, const std::vector<int> &assign_in, int nbins,
                  double tol, std::vector<int> &assign);
 

@@ -8,17 +8,18 @@
 // cost rounded once to an integer, every load and total an integer below
 // 2^53.  Loads are int64 sums (exact in any order), so the device reproduces
 // the host balancers' assignments bit for bit while adding in parallel, and
-// no sequential FP64 chain is needed (a dependent FP64 add costs ~64 cycles
-// on GB300, an integer add a few).  The cost average itself stays FP64, with
-// the host's operations in the host's order (explicitly rounded intrinsics,
-// never contracted into FMAs).
+// no FP64 work is needed (a dependent FP64 add costs ~64 cycles on GB300
+// and the FP64 pipe is narrow; integer ops cost a few).  The cost average
+// itself stays FP64, with the host's operations in the host's order
+// (explicitly rounded intrinsics, never contracted into FMAs).
 //
 // Kernels (all on the ctx stream):
 //   k_measure  one thread per VP: cycles -> ns per step -> cost average;
 //              the last block to finish (threadfence ticket) records SM
 //              busy times and the measurement step
 //   k_prep     one thread per VP: costs on the fixed-point grid; for
-//              GreedyLB also each VP's rank by (cost desc, id asc)
+//              GreedyLB each VP's rank by (cost desc, id asc), for the
+//              blocked variant its rank inside its block
 //   k_balance  one CTA of 1024 threads: static / GreedyLB / list scheduling
 //              in spatial order (one warp) / RefineSwapLB (whole CTA) on
 //              shared-memory copies of the assignment and the costs;
@@ -37,22 +38,11 @@ constexpr unsigned kFull = 0xffffffffu;
 constexpr int kBalThreads = 1024;
 constexpr int kBalWarps = kBalThreads / kWarp;
 constexpr int kPrepThreads = 256;
-constexpr int kItemThreads = 256;
+constexpr int kItemThreads = 1024;
 constexpr int kMeasThreads = 256;
 constexpr unsigned kNone = 0x7fffffffu;
 constexpr int kIdBits = 10;                   // bins < 1024 = 2^kIdBits
 constexpr unsigned long long kIdMask = (1ull << kIdBits) - 1;
-
-// a < b (IEEE, -0 == +0, no NaN) iff okey(a) < okey(b)
-__device__ __forceinline__ unsigned long long okey(double x) {
-    unsigned long long b = (unsigned long long)__double_as_longlong(x);
-    if (b == 0x8000000000000000ull) b = 0ull;
-    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
-}
-
-__device__ __forceinline__ double from_okey(unsigned long long k) {
-    return __longlong_as_double((long long)((k >> 63) ? (k & 0x7fffffffffffffffull) : ~k));
-}
 
 __device__ __forceinline__ int resolve(int s, long long rebalances) {
     if (s == LB_AUTO) return rebalances == 0 ? LB_GREEDY : LB_REFINE_SWAP;
@@ -61,6 +51,33 @@ __device__ __forceinline__ int resolve(int s, long long rebalances) {
 }
 
 __device__ __forceinline__ int bit_length(long long n) { return n > 0 ? 64 - __clzll(n) : 0; }
+
+// x with 2^(x-1) <= c < 2^x, for c > 0 (frexp's exponent), from the bits.
+__device__ __forceinline__ int exponent_of(double c) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(c) & 0x7fffffffffffffffull;
+    const int E = (int)(b >> 52);
+    return E ? E - 1022 : bit_length((long long)(b & ((1ull << 52) - 1))) - 1074;
+}
+
+// round-half-even(c * 2^e) for c >= 0 with c * 2^e < 2^53, in integer
+// arithmetic: c = M * 2^(E - 1075), so the result is M shifted by
+// E - 1075 + e with the bits shifted out rounded.  Equal to
+// llrint(ldexp(c, e)); FP64 work would run on GB300's narrow FP64 pipe.
+__device__ __forceinline__ long long fixed_q(double c, int e) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(c) & 0x7fffffffffffffffull;
+    if (b == 0ull) return 0;
+    int E = (int)(b >> 52);
+    unsigned long long M = b & ((1ull << 52) - 1);
+    if (E == 0) E = 1;
+    else M |= 1ull << 52;
+    const int s = E - 1075 + e;
+    if (s >= 0) return (long long)(M << s);
+    const int sh = -s;
+    if (sh >= 64) return 0;
+    const unsigned long long qf = M >> sh;
+    const unsigned long long rem = M & ((1ull << sh) - 1), half = 1ull << (sh - 1);
+    return (long long)(qf + (unsigned long long)(rem > half || (rem == half && (qf & 1ull))));
+}
 
 // Warp minimum / maximum of a 64-bit key; every lane gets it.
 __device__ __forceinline__ unsigned long long warp_min64(unsigned long long k) {
@@ -270,43 +287,50 @@ __global__ void __launch_bounds__(kMeasThreads) k_measure(const DevBal p) {
     }
 }
 
-// Costs on the fixed-point grid (lb_balance.cpp: fixed_point), and for
-// GreedyLB each VP's position in (cost desc, id asc) order.  Every block
-// rounds all costs into shared memory and writes its own range.
+// Costs on the fixed-point grid (lb_balance.cpp: fixed_point) into p.q,
+// and the orders that do not depend on loads: GreedyLB's (cost desc, id
+// asc) over all VPs, or for the blocked variant the same order inside each
+// block of nbins VPs in spatial order.  Every block rounds all costs into
+// shared memory and handles its own range.
 __global__ void __launch_bounds__(kPrepThreads) k_prep(const DevBal p, int strategy) {
     extern __shared__ long long s_qall[];          // [nvps]
     __shared__ unsigned long long s_w[kPrepThreads / kWarp + 1];
-    __shared__ int s_e, s_any;
-    const int nv = p.nvps;
-    unsigned long long kmax = okey(0.0);
+    const int nv = p.nvps, nb = p.nbins;
+    unsigned long long kmax = 0ull;                // costs >= 0: bit patterns order them
     for (int v = threadIdx.x; v < nv; v += blockDim.x) {
-        const unsigned long long k = okey(p.cost[v]);
+        const unsigned long long k =
+            (unsigned long long)__double_as_longlong(p.cost[v]) & 0x7fffffffffffffffull;
         kmax = k > kmax ? k : kmax;
     }
     kmax = ~block_min64(~kmax, s_w);
-    if (threadIdx.x == 0) {
-        const double cmax = from_okey(kmax);
-        int x = 0;
-        if (cmax > 0.0) frexp(cmax, &x);
-        s_e = cmax > 0.0 ? 53 - bit_length(nv) - x : 0;
-        s_any = cmax > 0.0;
-    }
+    const double cmax = __longlong_as_double((long long)kmax);
+    const int e = kmax ? 53 - bit_length(nv) - exponent_of(cmax) : 0;
+    for (int v = threadIdx.x; v < nv; v += blockDim.x) s_qall[v] = kmax ? fixed_q(p.cost[v], e) : 0;
     __syncthreads();
-    const bool any = s_any != 0;
-    const int e = s_e;
-    for (int v = threadIdx.x; v < nv; v += blockDim.x)
-        s_qall[v] = any ? __double2ll_rn(ldexp(p.cost[v], e)) : 0ll;
-    __syncthreads();
-    const int v = blockIdx.x * blockDim.x + threadIdx.x;
-    if (v < nv) p.q[v] = s_qall[v];
-    if (resolve(strategy, p.state[kStRebal]) != LB_GREEDY || v >= nv) return;
-    const long long qv = s_qall[v];
-    int rank = 0;
-    for (int u = 0; u < nv; ++u) {
-        const long long qu = s_qall[u];
-        rank += (qu > qv) || (qu == qv && u < v);
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nv) return;
+    p.q[t] = s_qall[t];
+    const int st = resolve(strategy, p.state[kStRebal]);
+    if (st == LB_GREEDY) {
+        const long long qv = s_qall[t];
+        int rank = 0;
+        for (int u = 0; u < nv; ++u) {
+            const long long qu = s_qall[u];
+            rank += (int)((qu > qv) | ((qu == qv) & (u < t)));
+        }
+        p.order[rank] = t;
+    } else if (st == LB_GREEDY_BLOCKED) {
+        const int base = (t / nb) * nb, m = min(nb, nv - base);
+        const int v = p.spatial[t];
+        const long long qv = s_qall[v];
+        int rank = 0;
+        for (int c = 0; c < m; ++c) {
+            const int u = p.spatial[base + c];
+            const long long qu = s_qall[u];
+            rank += (int)((qu > qv) | ((qu == qv) & (u < v)));
+        }
+        p.order[base + rank] = v;
     }
-    p.order[rank] = v;
 }
 
 __global__ void __launch_bounds__(kBalThreads, 1) k_balance(const DevBal p, int strategy) {
@@ -330,7 +354,7 @@ __global__ void __launch_bounds__(kBalThreads, 1) k_balance(const DevBal p, int 
     if (tid == 0) {
         const int st = resolve(strategy, p.state[kStRebal]);
         s_strat = st;
-        s_skip = st != LB_STATIC && !p.state[kStHave];
+        s_skip = st != LB_STATIC && st != LB_ATOMIC_QUEUE && !p.state[kStHave];
         if (s_skip) atomicCAS(p.status, 0, (int)LB_ESTATE);
         s_iters = 0;
     }
@@ -343,7 +367,9 @@ __global__ void __launch_bounds__(kBalThreads, 1) k_balance(const DevBal p, int 
     }
     __syncthreads();
 
-    if (st == LB_STATIC) {
+    if (st == LB_ATOMIC_QUEUE) {
+        // no table: the period is only recorded
+    } else if (st == LB_STATIC) {
         for (int v = tid; v < nv; v += kBalThreads) s_assign[v] = (int)(((long long)v * nb) / nv);
     } else if (st == LB_GREEDY || st == LB_GREEDY_SPATIAL) {
         if (warp == 0) {
@@ -351,6 +377,45 @@ __global__ void __launch_bounds__(kBalThreads, 1) k_balance(const DevBal p, int 
             if (nb <= 5 * kWarp) list_schedule<5>(ord, s_q, nv, nb, s_assign, s_k0, s_k1, s_t);
             else if (nb <= 8 * kWarp) list_schedule<8>(ord, s_q, nv, nb, s_assign, s_k0, s_k1, s_t);
             else list_schedule<kDevBalMaxBins / kWarp>(ord, s_q, nv, nb, s_assign, s_k0, s_k1, s_t);
+        }
+    } else if (st == LB_GREEDY_BLOCKED) {
+        // GreedyLB block by block over the VPs in spatial order
+        // (lb_balance.cpp: greedy_blocked).  The order of the VPs inside
+        // each block (cost desc, id asc) does not depend on the loads:
+        // k_prep ranked all blocks at once.  Block by block, the bins are
+        // ranked by (load asc, id asc) and the VP of rank r goes to the bin
+        // of rank r.
+        const int32_t *s_byr = p.order;   // VPs of each block by rank (k_prep)
+        int *s_bin = s_qs;                // [nb] bins by rank (first m used)
+        for (int b = tid; b < nb; b += kBalThreads) s_load[b] = 0ull;
+        // bin ranks: G threads per bin (a power of two dividing 32)
+        const int G = nb * 8 <= kBalThreads ? 8 : (nb * 4 <= kBalThreads ? 4
+                    : (nb * 2 <= kBalThreads ? 2 : 1));
+        for (int base = 0; base < nv; base += nb) {
+            const int m = min(nb, nv - base);
+            for (int b = tid; b < nb; b += kBalThreads)
+                s_k0[b] = (s_load[b] << kIdBits) | (unsigned long long)b;
+            __syncthreads();
+            for (int g0 = 0; g0 < nb * G; g0 += kBalThreads) {
+                const int gi = g0 + tid;
+                const int b = gi / G, sub = gi % G;
+                int r = 0;
+                if (b < nb) {
+                    const unsigned long long kb = s_k0[b];
+                    const int c0 = (nb * sub) / G, c1 = (nb * (sub + 1)) / G;
+#pragma unroll 8
+                    for (int c = c0; c < c1; ++c) r += (int)(s_k0[c] < kb);
+                }
+                for (int o = 1; o < G; o <<= 1) r += __shfl_xor_sync(kFull, r, o);
+                if (b < nb && sub == 0 && r < m) s_bin[r] = b;
+            }
+            __syncthreads();
+            for (int r = tid; r < m; r += kBalThreads) {
+                const int v = s_byr[base + r], b = s_bin[r];
+                s_assign[v] = b;
+                s_load[b] += (unsigned long long)s_q[v];
+            }
+            __syncthreads();
         }
     } else {
         // RefineSwapLB (lb_balance.cpp: refine_swap); loads are exact
@@ -531,9 +596,12 @@ __global__ void __launch_bounds__(kBalThreads, 1) k_balance(const DevBal p, int 
     for (int v = tid; v < nv; v += kBalThreads) p.assign[v] = s_assign[v];
     if (tid == 0) {
         const double mean = __ddiv_rn(__ull2double_rn(tot), (double)nb);
-        const double pred = mean > 0.0 ? __ddiv_rn(__ull2double_rn(lmax), mean) : 1.0;
         const double cm = __ull2double_rn(qmax);
         const double floor = mean > 0.0 ? (cm > mean ? cm : mean) / mean : 1.0;
+        // the queue's prediction is its granularity floor
+        const double pred = st == LB_ATOMIC_QUEUE
+                                ? floor
+                                : (mean > 0.0 ? __ddiv_rn(__ull2double_rn(lmax), mean) : 1.0);
         const long long n = p.state[kStHist];
         double *row = p.hist + (size_t)(n % kBalHist) * kBalHistCols;
         row[0] = (double)p.dclock[0];
@@ -545,8 +613,10 @@ __global__ void __launch_bounds__(kBalThreads, 1) k_balance(const DevBal p, int 
         row[6] = (double)s_iters;
         row[7] = 0.0;
         p.state[kStHist] = n + 1;
-        if (st != LB_STATIC) p.state[kStRebal] += 1;
-        p.state[kStStrategy] = st;
+        if (st != LB_STATIC && st != LB_ATOMIC_QUEUE) {
+            p.state[kStRebal] += 1;
+            p.state[kStStrategy] = st;
+        }
     }
 }
 
@@ -625,7 +695,7 @@ cudaError_t dev_rebalance(const DevBal &p, int strategy, cudaStream_t s) {
     k_prep<<<(p.nvps + kPrepThreads - 1) / kPrepThreads, kPrepThreads, prep_smem(p.nvps), s>>>(
         p, strategy);
     k_balance<<<1, kBalThreads, dev_balance_smem(p.nvps, p.nbins), s>>>(p, strategy);
-    k_items<<<p.nbins, kItemThreads, 0, s>>>(p);
+    if (strategy != LB_ATOMIC_QUEUE) k_items<<<p.nbins, kItemThreads, 0, s>>>(p);
     return cudaGetLastError();
 }
 

@@ -17,14 +17,14 @@ LIB_PATH = os.path.join(_PKG, "_build", "liblb.so")
 LB_OK, LB_EINVAL, LB_ECUDA, LB_ETIMEOUT, LB_ENUMERIC, LB_ESTATE, LB_ENORESIDENT, LB_EIO = range(8)
 LB_F64, LB_F32, LB_BF16 = 0, 1, 2
 (LB_STATIC, LB_GREEDY, LB_REFINE_SWAP, LB_ATOMIC_QUEUE, LB_AUTO, LB_GREEDY_SPATIAL,
- LB_AUTO_SPATIAL) = range(7)
+ LB_AUTO_SPATIAL, LB_GREEDY_BLOCKED) = range(8)
 
 STATUS_NAMES = {0: "LB_OK", 1: "LB_EINVAL", 2: "LB_ECUDA", 3: "LB_ETIMEOUT", 4: "LB_ENUMERIC",
                 5: "LB_ESTATE", 6: "LB_ENORESIDENT", 7: "LB_EIO"}
 DTYPES = {"f64": LB_F64, "f32": LB_F32, "bf16": LB_BF16}
 STRATEGIES = {"static": LB_STATIC, "greedy": LB_GREEDY, "refine_swap": LB_REFINE_SWAP,
               "queue": LB_ATOMIC_QUEUE, "auto": LB_AUTO, "greedy_spatial": LB_GREEDY_SPATIAL,
-              "auto_spatial": LB_AUTO_SPATIAL}
+              "auto_spatial": LB_AUTO_SPATIAL, "greedy_blocked": LB_GREEDY_BLOCKED}
 
 
 class LBError(RuntimeError):

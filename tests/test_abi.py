@@ -104,3 +104,15 @@ def test_plan_greedy_spatial_matches_oracle(lbmod, seed):
     costs = [rng.lognormvariate(0, 1) for _ in range(nv)]
     g, _, _ = lbmod.lb_plan("greedy_spatial", costs, nb)
     assert list(g) == B.greedy_ordered(costs, nb, list(range(nv)))
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_plan_greedy_blocked_matches_oracle(lbmod, seed):
+    rng = random.Random(700 + seed)
+    nb = rng.randint(2, 30)
+    nv = rng.randint(1, 400)
+    costs = [rng.lognormvariate(0, 1) for _ in range(nv)]
+    g, mig, pred = lbmod.lb_plan("greedy_blocked", costs, nb)
+    ref = B.greedy_blocked(costs, nb, list(range(nv)))
+    assert list(g) == ref
+    assert pred == B.max_over_mean(costs, ref, nb)

@@ -166,3 +166,34 @@ def test_fixed_point_grid_bounds(seed):
         assert abs(math.ldexp(c, e) - k) <= 0.5
     order = sorted(range(n), key=lambda v: costs[v])
     assert all(q[order[i]] <= q[order[i + 1]] for i in range(min(n, 500) - 1))
+
+
+def test_blocked_greedy_is_greedy_for_one_block():
+    """No more objects than bins, all costs positive: one block, GreedyLB
+    itself (with zero costs GreedyLB may stack objects on bin 0, whose
+    (load, id) stays the lowest)."""
+    rng = random.Random(9)
+    for _ in range(20):
+        nb = rng.randint(1, 12)
+        n = rng.randint(1, nb)
+        costs = [float(rng.randint(1, 9)) for _ in range(n)]
+        assert B.greedy_blocked(costs, nb, list(range(n))) == B.greedy(costs, nb)
+
+
+@pytest.mark.parametrize("seed", range(25))
+def test_blocked_greedy_one_per_block_and_spread_below_largest_cost(seed):
+    """Every processor gets exactly one object of each full block (the
+    processors sweep the order in lockstep), and the load spread never
+    exceeds the largest cost: heaviest to lightest keeps it bounded."""
+    rng = random.Random(300 + seed)
+    nb = rng.randint(2, 20)
+    n = rng.randint(nb, 12 * nb)
+    costs = [rng.lognormvariate(0, 1.5) for _ in range(n)]
+    order = list(range(n))
+    rng.shuffle(order)
+    a = B.greedy_blocked(costs, nb, order)
+    for base in range(0, n - nb + 1, nb):
+        assert sorted(a[v] for v in order[base:base + nb]) == list(range(nb))
+    q = B.fixed_point(costs)
+    loads = B.bin_loads(q, a, nb)
+    assert max(loads) - min(loads) <= max(q)

@@ -81,7 +81,8 @@ def hist_last(ctx):
 
 @pytest.mark.parametrize("layout", list(LAYOUTS))
 @pytest.mark.parametrize("kind", ["uniform", "ties", "heavy", "zeros"])
-@pytest.mark.parametrize("strategy", ["greedy", "greedy_spatial", "refine_swap", "static"])
+@pytest.mark.parametrize("strategy", ["greedy", "greedy_spatial", "greedy_blocked", "refine_swap",
+                                      "static"])
 def test_device_balancer_equals_host(layout, kind, strategy):
     from paper_1310_4218_gb300 import lb
     g, q, vps, dev, host = twin(layout)
@@ -107,6 +108,8 @@ def test_device_balancer_equals_host(layout, kind, strategy):
         ref = B.greedy(c, nb)
     elif strategy == "greedy_spatial":
         ref = B.greedy_ordered(c, nb, spatial_order(vps))
+    elif strategy == "greedy_blocked":
+        ref = B.greedy_blocked(c, nb, spatial_order(vps))
     elif strategy == "refine_swap":
         ref = B.refine_swap(c, list(map(int, cur)), nb, tol=0.05)
     else:
@@ -155,7 +158,7 @@ def test_more_processors_than_the_register_greedy():
     nb = dev.info().nprocs
     assert nb > 256
     costs = costs_of("ties", len(vps), 5)
-    for strategy in ("greedy", "greedy_spatial", "refine_swap"):
+    for strategy in ("greedy", "greedy_spatial", "greedy_blocked", "refine_swap"):
         dev.set_costs(costs)
         host.set_costs(costs)
         lb.lb_device_rebalance(dev.ctx, strategy)
@@ -216,7 +219,7 @@ def test_device_tables_drive_steps_with_unchanged_values():
     base.close()
     for steal in (0, 1):
         sim = make_sim([g], [q], vps, steal=steal)
-        for strategy in ("greedy", "refine_swap", "greedy_spatial", "auto"):
+        for strategy in ("greedy", "refine_swap", "greedy_spatial", "greedy_blocked"):
             sim.step(3)
             lb.lb_device_measure(sim.ctx)
             lb.lb_device_rebalance(sim.ctx, strategy)
@@ -276,13 +279,22 @@ def test_device_balancer_refusals():
     assert np.array_equal(sim.assignment()[0], before)
     with pytest.raises(lb.LBError) as ei:
         lb.lb_device_rebalance(sim.ctx, "queue")
-    assert ei.value.status == lb.LB_EINVAL
+    assert ei.value.status == lb.LB_ESTATE
     sim.step(1)
     sim.measure()
     sim.rebalance("queue")
     with pytest.raises(lb.LBError) as ei:
         lb.lb_device_rebalance(sim.ctx, "greedy")
     assert ei.value.status == lb.LB_ESTATE
+    # queue mode: device measurement and a record of the period, no table
+    before = sim.assignment()[0]
+    sim.step(2)
+    lb.lb_device_measure(sim.ctx)
+    lb.lb_device_rebalance(sim.ctx, "queue")
+    row = lb.lb_balance_history(sim.ctx)[-1]
+    assert row[1] == lb.LB_ATOMIC_QUEUE and row[2] == 0 and row[3] == row[5] >= 1.0
+    assert np.array_equal(sim.assignment()[0], before)
+    assert sim.info().strategy == lb.LB_ATOMIC_QUEUE
     sim.close()
     # more VPs than the device balancer takes
     g2 = Grid(2, 4097, 4, disk=(0, 0, 0, 0, 1), k_in=1, k_out=1)

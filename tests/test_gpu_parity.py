@@ -75,8 +75,9 @@ def test_general_advection(cx, cy, cz):
 
 
 @pytest.mark.parametrize("strategy", ["static", "greedy", "refine_swap", "queue", "auto",
-                                      "greedy_spatial", "auto_spatial", "static+steal",
-                                      "auto_spatial+steal"])
+                                      "greedy_spatial", "auto_spatial", "greedy_blocked",
+                                      "static+steal", "auto_spatial+steal",
+                                      "greedy_blocked+steal"])
 def test_strategies_give_identical_fields(strategy):
     """Balancing changes only where columns run, never their values: every
     strategy (with or without work stealing) yields the same bits, and they
