@@ -5,19 +5,23 @@ CPU-oracle baselines.
 One benchmark step = one rebalance period: `period` time steps of every VP
 (advection, k_c Thomas sweeps, store, global sum, per-VP cost stamps, grid
 barrier) in one persistent launch, then the load measurement and the
-rebalance.  The headline strategy is greedy_blocked+steal+dev: the measured
-costs (Sec. V) feed GreedyLB applied block by block to the VPs in spatial
-order (each processor takes one VP of every block of nprocs, heaviest to
-least loaded), processors that finish early take items of the processor
-with the most left, and measurement and balancer run as device kernels
-behind the step launch (no host round trip).  The static table, the
-paper's GreedyLB-then-RefineSwapLB schedule, its spatial variant and the
-atomic queue, with host or device balancing, are measured the same way and
-reported beside it.  The k_c array is re-drawn every 50 time steps as the
-workload prescribes.
+rebalance.  The headline strategy is greedy_blocked+steal+dev+pred+thr:
+the measured costs (Sec. V) feed GreedyLB applied block by block to the VPs
+in spatial order (each processor takes one VP of every block of nprocs,
+heaviest to least loaded); processors that finish early take items of the
+processor with the most left; measurement and balancer run as device
+kernels behind the step launch (no host round trip); at a k_c re-draw the
+costs are rescaled for the new array before the balancer runs; and the
+table is kept while its predicted max/mean stays within 1.15.  The static
+table, the paper's GreedyLB-then-RefineSwapLB schedule, its spatial
+variant and the atomic queue, with host or device balancing, are measured
+the same way and reported beside it.  The k_c array is re-drawn every 50
+time steps as the workload prescribes.
 
 Strategy names: an lb_strategy name, optionally followed by "+steal"
-(end-of-step work stealing) and "+dev" (device balancer).
+(end-of-step work stealing), "+dev" (device balancer), "+pred" (cost
+rescale at k_c re-draws, with +dev) and "+thr" (keep a table within the
+1.15 threshold, with +dev).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--workload NAME] [--period P] [--strategy auto|static|queue|...]
@@ -52,7 +56,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--period", type=int, default=10)
-    ap.add_argument("--strategy", default="greedy_blocked+steal+dev")
+    ap.add_argument("--strategy", default="greedy_blocked+steal+dev+pred+thr")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--threads", type=int, default=0, help="threads per processor (0: default)")
@@ -261,6 +265,11 @@ class StrategyRun:
         strategy, flags = parts[0], set(parts[1:])
         steal = "steal" in flags
         self.dev_mode = "dev" in flags
+        # "+pred": at a k_c re-draw the new array is installed before the
+        # balancer runs and the costs are rescaled by the fitted model
+        self.predict = "pred" in flags and self.dev_mode
+        self.threshold = "thr" in flags and self.dev_mode
+        self.kc_epoch = None
         self.dev_tags = []
         self.kernels = 0             # our kernel launches (step, k_c switch, balancer)
         self.P, self.strategy, self.dev, self.stream = args.period, strategy, dev, stream
@@ -268,6 +277,7 @@ class StrategyRun:
         opt.threads_hint = args.threads
         opt.queue_order = 0
         opt.steal = 1 if steal else 0
+        opt.predict_kc = 1 if self.predict else 0
         kc0 = [epochs[0][gi] for gi in range(len(w.grids))] if epochs else None
         self.sim = Simulation(w.grids, fields, w.vps, kc_arrays=kc0, options=opt, device=dev,
                               stream=stream)
@@ -284,10 +294,7 @@ class StrategyRun:
             n = t1 - t
             if self.epochs:
                 e = t // w.kc_epoch_steps
-                if t % w.kc_epoch_steps == 0 or t == t0:
-                    for gi in range(len(w.grids)):
-                        self.lb.lb_set_kc(self.sim.ctx, gi, self.kc_dev[e][gi].data_ptr())
-                        self.kernels += 1
+                self.set_epoch(e)
                 n = min(n, (e + 1) * w.kc_epoch_steps - t)
             self.sim.step(n)
             t += n
@@ -295,16 +302,30 @@ class StrategyRun:
         self.kernels += n_launch
         return n_launch
 
-    def balance(self, tag):
-        """Load measurement (Sec. V) and the balancer call (Sec. VI)."""
+    def set_epoch(self, e):
+        """Install the k_c arrays of epoch e (once)."""
+        if e == self.kc_epoch:
+            return
+        for gi in range(len(self.w.grids)):
+            self.lb.lb_set_kc(self.sim.ctx, gi, self.kc_dev[e][gi].data_ptr())
+            self.kernels += 3 if self.predict else 1
+        self.kc_epoch = e
+
+    def balance(self, tag, t_next):
+        """Load measurement (Sec. V) and the balancer call (Sec. VI) before
+        time step t_next."""
         if self.dev_mode:
             # enqueued only: measurement, cost rounding and ranks, balancer,
             # table kernels (the queue has no table: measurement and record)
             self.lb.lb_device_measure(self.sim.ctx)
+            if self.predict and self.epochs:
+                self.set_epoch(t_next // self.w.kc_epoch_steps)
             if self.strategy == "queue" and self.info.strategy != self.lb.LB_ATOMIC_QUEUE:
                 self.sim.rebalance("queue")       # enter queue mode once
                 self.info = self.sim.info()
-            self.lb.lb_device_rebalance(self.sim.ctx, self.strategy)
+            # "+thr": keep the table while its predicted max/mean <= 1.15
+            self.lb.lb_device_rebalance_if(self.sim.ctx, self.strategy,
+                                           1.15 if self.threshold else 0.0)
             self.kernels += 3 if self.strategy == "queue" else 4
             self.dev_tags.append(tag)
             return
@@ -334,7 +355,7 @@ class StrategyRun:
         for wi in range(nper):
             self.launches(self.t, self.t + self.P)
             self.t += self.P
-            self.balance("first" if wi == 0 else "warmup")
+            self.balance("first" if wi == 0 else "warmup", self.t)
         torch.cuda.synchronize(self.dev)
         self.collect()
 
@@ -359,7 +380,7 @@ class StrategyRun:
             nl = self.launches(self.t, self.t + self.P)
             b.record(stream)
             kev.append((a, b, nl))
-            self.balance("timed")
+            self.balance("timed", self.t + self.P)
             self.t += self.P
         e1.record(stream)
         torch.cuda.synchronize(self.dev)
@@ -392,7 +413,7 @@ class StrategyRun:
                 for gi in range(len(self.w.grids)):
                     sim.field_tensor(gi).view(-1).copy_(h_in[gi].view(-1), non_blocking=True)
             self.launches(self.t, self.t + self.P)
-            self.balance("e2e")
+            self.balance("e2e", self.t + self.P)
             self.t += self.P
             with torch.cuda.stream(stream):
                 for gi in range(len(self.w.grids)):
@@ -471,9 +492,9 @@ def main():
     # the other assignments, measured the same way (device-resident inputs)
     compare = {}
     if not args.no_compare:
-        for st in [x for x in ("static", "auto", "queue", "auto_spatial", "auto_spatial+steal",
-                               "static+steal", "queue+dev", "auto+dev", "auto_spatial+steal+dev",
-                               "greedy_blocked+dev", "greedy_blocked+steal+dev")
+        for st in [x for x in ("static", "static+steal", "auto", "auto+dev", "auto_spatial+steal",
+                               "auto_spatial+steal+dev", "greedy_blocked+steal+dev",
+                               "greedy_blocked+steal+dev+pred", "queue", "queue+dev")
                    if x != args.strategy]:
             r2 = StrategyRun(w, fields, epochs, kc_dev, args, dev, stream, st)
             r2.warmup(args.warmup)

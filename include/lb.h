@@ -147,7 +147,10 @@ typedef struct {
                                      that finishes its VPs takes the next
                                      work items of the processor with the
                                      most left (default 0) */
-    int32_t reserved[6];          /* must be 0 */
+    int32_t predict_kc;           /* 1: lb_set_kc also rescales each VP's cost
+                                     average for the new k_c array (see
+                                     lb_set_kc); default 0 */
+    int32_t reserved[5];          /* must be 0 */
 } lb_options;
 
 /* Fill *opt with the defaults listed above. */
@@ -228,7 +231,19 @@ lb_status lb_set_assignment(lb_ctx *ctx, const int32_t *vp_to_proc);
 /* Point grid `grid`'s k_c source at a new device array int32[ny*nx] (the
    load array re-drawn between segments).  The switch is enqueued on the
    ctx stream (no synchronisation): steps enqueued after this call read the
-   new array, which stays caller-owned and must stay valid while they run. */
+   new array, which stays caller-owned and must stay valid while they run.
+
+   With lb_options.predict_kc (and the device balancer available), the call
+   also predicts the costs the new array will cause, so that a rebalance
+   made before any step has run on it is already right -- the predictive
+   cost model of measured load balancing with a known load change.  Each
+   VP's work is modelled as kappa * f1 + f2 with f1 = items * nz and f2 =
+   sum over its work items of (largest k_c among the item's columns) * nz;
+   kappa (per-item overhead in sweeps) is fitted by least squares to the
+   last measured per-VP costs against (f1, f2) of the old array, or 6 when
+   that fit is ill-posed.  Every cost average of the grid's VPs is then
+   multiplied by (kappa f1 + f2_new) / (kappa f1 + f2_old).  Enqueued on
+   the ctx stream; host calls that read costs see the result. */
 lb_status lb_set_kc(lb_ctx *ctx, int32_t grid, const int32_t *dev_kc);
 
 /* Compensated FP64 global sum of grid `grid` after the latest step that
@@ -304,6 +319,18 @@ lb_status lb_graph_destroy(lb_ctx *ctx, void *graph_exec);
 lb_status lb_device_measure(lb_ctx *ctx);
 lb_status lb_device_rebalance(lb_ctx *ctx, int32_t strategy);
 
+/*
+ * Threshold-triggered rebalancing (the paper's future-work item, Sec. VII)
+ * on the device: like lb_device_rebalance, but the current table is kept
+ * when its predicted max/mean processor load under the current cost
+ * averages is at most threshold -- unless lb_set_kc rescaled the costs
+ * since the last rebalance, which forces one.  A kept table is recorded in
+ * the balance history (migrations 0, last column 1).  threshold <= 0:
+ * always rebalance.  (Measured SM busy times are no criterion with work
+ * stealing, which evens them out whatever the table.)
+ */
+lb_status lb_device_rebalance_if(lb_ctx *ctx, int32_t strategy, double threshold);
+
 /* Per-VP costs, ns per step (host double[nvps] each, may be NULL): the
    cost average balancers use and the last measurement.  Synchronises. */
 lb_status lb_get_costs(lb_ctx *ctx, double *avg_ns, double *last_ns);
@@ -313,7 +340,8 @@ lb_status lb_get_costs(lb_ctx *ctx, double *avg_ns, double *last_ns);
  * first, 8 doubles each: step index, strategy applied (LB_AUTO* resolved),
  * migrations, predicted max/mean processor load, measured SM busy max/mean
  * of the preceding measurement, granularity floor max(max cost, mean)/mean,
- * RefineSwapLB iterations, 0.  rows: host double[max*8].  Synchronises.
+ * RefineSwapLB iterations, 1 if the table was kept by
+ * lb_device_rebalance_if (else 0).  rows: host double[max*8].  Synchronises.
  */
 lb_status lb_balance_history(lb_ctx *ctx, double *rows, int32_t max, int32_t *n);
 

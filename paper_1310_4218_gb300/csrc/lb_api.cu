@@ -61,6 +61,8 @@ struct lb_ctx {
     double *d_pend = nullptr;
     double *d_bhist = nullptr;
     unsigned *d_ticket = nullptr;
+    double *d_feat1 = nullptr, *d_feat2 = nullptr, *d_featn = nullptr;   // predictive cost model
+    bool predict = false;              // predict_kc active
     bool dev_newer = false;            // device balancer state newer than the host copy
     std::string devbal_off;            // why the device balancer is unavailable ("" = available)
     double fallback_npc = 1.0;
@@ -142,6 +144,8 @@ static double last_pivot(double r, int nz) {
     for (int k = 1; k < nz - 1; ++k) m = 1.0 / (1.0 + 2.0 * r - r * r * m);
     return 1.0 / (1.0 + r - r * r * m);
 }
+
+static DevBal make_devbal(lb_ctx *ctx);
 
 static lb_status check_status(lb_ctx *ctx) {
     int32_t st = 0;
@@ -273,7 +277,8 @@ static void free_ctx(lb_ctx *ctx) {
                     ctx->d_sweeps,    ctx->d_clock,    ctx->d_bin_ctr,   ctx->d_cost,
                     ctx->d_last,      ctx->d_assign,   ctx->d_order,     ctx->d_spatial,
                     ctx->d_nchunks,   ctx->d_bstate,   ctx->d_pend,      ctx->d_bhist,
-                    ctx->d_ticket,    ctx->d_q};
+                    ctx->d_ticket,    ctx->d_q,        ctx->d_feat1,     ctx->d_feat2,
+                    ctx->d_featn};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete ctx;
@@ -520,6 +525,9 @@ extern "C" lb_status lb_create(const lb_grid_desc *grids, int32_t ngrids, const 
     if (e == cudaSuccess) e = dalloc(&ctx->d_assign, nvps);
     if (e == cudaSuccess) e = dalloc(&ctx->d_order, nvps);
     if (e == cudaSuccess) e = dalloc(&ctx->d_q, nvps);
+    if (e == cudaSuccess) e = dalloc(&ctx->d_feat1, nvps);
+    if (e == cudaSuccess) e = dalloc(&ctx->d_feat2, nvps);
+    if (e == cudaSuccess) e = dalloc(&ctx->d_featn, nvps);
     if (e == cudaSuccess) e = dalloc(&ctx->d_spatial, nvps);
     if (e == cudaSuccess) e = dalloc(&ctx->d_nchunks, nvps);
     if (e == cudaSuccess) e = dalloc(&ctx->d_bstate, kStWords);
@@ -568,6 +576,22 @@ extern "C" lb_status lb_create(const lb_grid_desc *grids, int32_t ngrids, const 
     }
     st = upload_items(ctx);
     if (st != LB_OK) return bail(st);
+    if (ctx->opt.predict_kc && ctx->devbal_off.empty()) {
+        // item features: f1 = items * nz per VP, f2 under each array's k_c
+        std::vector<double> f1(nvps), zero(nvps, 0.0);
+        for (int v = 0; v < nvps; ++v) f1[v] = (double)ctx->vp_nchunks[v] * grids[vps[v].grid].nz;
+        e = cudaMemcpyAsync(ctx->d_feat1, f1.data(), sizeof(double) * nvps, cudaMemcpyHostToDevice, sm);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(ctx->d_feat2, zero.data(), sizeof(double) * nvps, cudaMemcpyHostToDevice, sm);
+        for (int g = 0; g < ngrids && e == cudaSuccess; ++g)
+            if (!grids[g].kc_disk) e = dev_kc_features(make_devbal(ctx), g, grids[g].kc, true, sm);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(sm);
+        if (e != cudaSuccess) {
+            ctx->err = std::string("cost model features: ") + cudaGetErrorString(e);
+            return bail(LB_ECUDA);
+        }
+        ctx->predict = true;
+    }
     *out = ctx;
     return LB_OK;
 }
@@ -727,6 +751,13 @@ static DevBal make_devbal(lb_ctx *ctx) {
     p.hist = ctx->d_bhist;
     p.items = ctx->d_items;
     p.bin_start = ctx->d_bin_start;
+    p.vps = ctx->d_vps;
+    p.grids = ctx->d_grids;
+    p.cols_per_item = ctx->kinfo.cols_per_item;
+    p.kc_overhead = 6.0;
+    p.feat1 = ctx->d_feat1;
+    p.feat2 = ctx->d_feat2;
+    p.feat_new = ctx->d_featn;
     return p;
 }
 
@@ -760,13 +791,18 @@ extern "C" lb_status lb_device_measure(lb_ctx *ctx) {
     return LB_OK;
 }
 
-extern "C" lb_status lb_device_rebalance(lb_ctx *ctx, int32_t strategy) {
+extern "C" lb_status lb_device_rebalance_if(lb_ctx *ctx, int32_t strategy, double threshold) {
     if (!ctx) return fail(nullptr, LB_EINVAL, "ctx is NULL");
+    if (!(threshold == threshold)) return fail(ctx, LB_EINVAL, "threshold is NaN");
     lb_status st = devbal_check(ctx, strategy, true);
     if (st != LB_OK) return st;
-    CK(dev_rebalance(make_devbal(ctx), strategy, ctx->stream));
+    CK(dev_rebalance(make_devbal(ctx), strategy, threshold, ctx->stream));
     ctx->dev_newer = true;
     return LB_OK;
+}
+
+extern "C" lb_status lb_device_rebalance(lb_ctx *ctx, int32_t strategy) {
+    return lb_device_rebalance_if(ctx, strategy, 0.0);
 }
 
 extern "C" lb_status lb_get_costs(lb_ctx *ctx, double *avg_ns, double *last_ns) {
@@ -826,7 +862,7 @@ extern "C" lb_status lb_graph_create_periods(lb_ctx *ctx, int32_t nsteps, int32_
             st = ctx->compute == LB_F64 ? launch<double>(ctx, nsteps, ctx->coef_d)
                                         : launch<float>(ctx, nsteps, ctx->coef_f);
             if (st == LB_OK) e = dev_measure(db, cap);
-            if (st == LB_OK && e == cudaSuccess) e = dev_rebalance(db, strategy, cap);
+            if (st == LB_OK && e == cudaSuccess) e = dev_rebalance(db, strategy, 0.0, cap);
         }
         ctx->stream = own;
         cudaError_t e2 = cudaStreamEndCapture(cap, &graph);
@@ -1035,6 +1071,10 @@ extern "C" lb_status lb_set_kc(lb_ctx *ctx, int32_t grid, const int32_t *dev_kc)
     ctx->h_grids[grid].kc = dev_kc;
     // a one-thread kernel, so the switch is stream-ordered and needs no sync
     CK(dev_set_kc(&ctx->d_grids[grid], dev_kc, ctx->stream));
+    if (ctx->predict) {
+        CK(dev_kc_features(make_devbal(ctx), grid, dev_kc, false, ctx->stream));
+        ctx->dev_newer = true;
+    }
     return LB_OK;
 }
 

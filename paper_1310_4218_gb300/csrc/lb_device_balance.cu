@@ -333,7 +333,8 @@ __global__ void __launch_bounds__(kPrepThreads) k_prep(const DevBal p, int strat
     }
 }
 
-__global__ void __launch_bounds__(kBalThreads, 1) k_balance(const DevBal p, int strategy) {
+__global__ void __launch_bounds__(kBalThreads, 1) k_balance(const DevBal p, int strategy,
+                                                            double threshold) {
     extern __shared__ long long s_dyn[];
     const int nv = p.nvps, nb = p.nbins;
     long long *s_q = s_dyn;                                          // [nv] fixed-point costs
@@ -366,6 +367,46 @@ __global__ void __launch_bounds__(kBalThreads, 1) k_balance(const DevBal p, int 
         s_q[v] = p.q[v];
     }
     __syncthreads();
+
+    // threshold-triggered rebalancing: keep the table while its predicted
+    // max/mean under the current costs stays at or below the threshold
+    // (unless the costs were just rescaled for a new k_c array)
+    if (threshold > 0.0 && st != LB_STATIC && st != LB_ATOMIC_QUEUE && !p.state[kStForce]) {
+        for (int b = tid; b < nb; b += kBalThreads) s_load[b] = 0ull;
+        __syncthreads();
+        unsigned long long tot = 0, qmax = 0;
+        for (int v = tid; v < nv; v += kBalThreads) {
+            const unsigned long long q = (unsigned long long)s_q[v];
+            atomicAdd(&s_load[s_assign[v]], q);
+            tot += q;
+            qmax = q > qmax ? q : qmax;
+        }
+        tot = block_sum64(tot, s_w);
+        qmax = ~block_min64(~qmax, s_w);
+        unsigned long long lmax = 0;
+        for (int b = tid; b < nb; b += kBalThreads) lmax = s_load[b] > lmax ? s_load[b] : lmax;
+        lmax = ~block_min64(~lmax, s_w);
+        const double mean = __ddiv_rn(__ull2double_rn(tot), (double)nb);
+        const double pred = mean > 0.0 ? __ddiv_rn(__ull2double_rn(lmax), mean) : 1.0;
+        if (pred <= threshold) {
+            if (tid == 0) {
+                const double cm = __ull2double_rn(qmax);
+                const long long n = p.state[kStHist];
+                double *row = p.hist + (size_t)(n % kBalHist) * kBalHistCols;
+                row[0] = (double)p.dclock[0];
+                row[1] = (double)st;
+                row[2] = 0.0;
+                row[3] = pred;
+                row[4] = p.pend[0];
+                row[5] = mean > 0.0 ? (cm > mean ? cm : mean) / mean : 1.0;
+                row[6] = 0.0;
+                row[7] = 1.0;
+                p.state[kStHist] = n + 1;
+                p.state[kStKept] = 1;
+            }
+            return;
+        }
+    }
 
     if (st == LB_ATOMIC_QUEUE) {
         // no table: the period is only recorded
@@ -613,6 +654,8 @@ __global__ void __launch_bounds__(kBalThreads, 1) k_balance(const DevBal p, int 
         row[6] = (double)s_iters;
         row[7] = 0.0;
         p.state[kStHist] = n + 1;
+        p.state[kStKept] = 0;
+        p.state[kStForce] = 0;
         if (st != LB_STATIC && st != LB_ATOMIC_QUEUE) {
             p.state[kStRebal] += 1;
             p.state[kStStrategy] = st;
@@ -625,6 +668,7 @@ __global__ void __launch_bounds__(kItemThreads) k_items(const DevBal p) {
     __shared__ int s_wscan[kItemThreads / kWarp];
     const int b = blockIdx.x;
     const int lane = threadIdx.x % kWarp, warp = threadIdx.x / kWarp;
+    if (p.state[kStKept]) return;     // table unchanged
     unsigned long long acc = 0;
     for (int v = threadIdx.x; v < p.nvps; v += kItemThreads)
         if (p.assign[v] < b) acc += (unsigned long long)p.nchunks[v];
@@ -661,10 +705,112 @@ __global__ void __launch_bounds__(kItemThreads) k_items(const DevBal p) {
 
 __global__ void k_set_kc(GridDev *g, const int32_t *kc) { g->kc = kc; }
 
+// Item features of grid `grid`'s VPs under k_c array kc, one warp per VP:
+// out[v] = nz * sum over the VP's work items of the largest k_c among the
+// item's columns (the sweeps a warp runs for it).  Work items are runs of
+// cols_per_item (16 or 32) columns of the VP in row-major order, so each
+// warp pass over 32 columns covers whole items.
+__global__ void __launch_bounds__(256) k_features(const DevBal p, int grid, const int32_t *kc,
+                                                  double *out) {
+    const int v = (int)((blockIdx.x * blockDim.x + threadIdx.x) / kWarp);
+    const int lane = threadIdx.x % kWarp;
+    if (v >= p.nvps) return;                 // whole warps
+    const VPDev vp = p.vps[v];
+    if (vp.grid != grid) return;
+    const GridDev &g = p.grids[grid];
+    const int cpi = p.cols_per_item;
+    long long sum = 0;
+    for (int base = 0; base < vp.ncols; base += kWarp) {
+        const int q = base + lane;
+        int k = 0;
+        if (q < vp.ncols) {
+            const int ly = q / vp.w;
+            const int i = vp.x0 + (q - ly * vp.w), j = vp.y0 + ly;
+            const int kv = kc[(size_t)j * g.nx + i];
+            k = kv > 0 ? kv : 0;
+        }
+        for (int o = cpi / 2; o > 0; o >>= 1) {
+            const int k2 = __shfl_xor_sync(kFull, k, o);
+            k = k2 > k ? k2 : k;
+        }
+        if (lane % cpi == 0) sum += k;
+    }
+    sum = (long long)__reduce_add_sync(kFull, (unsigned)sum);
+    if (lane == 0) out[v] = (double)sum * (double)g.nz;
+}
+
+__device__ double block_sum_f64(double x, double *s_d) {
+    const int lane = threadIdx.x % kWarp, warp = threadIdx.x / kWarp;
+    const int nw = blockDim.x / kWarp;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
+    if (lane == 0) s_d[warp] = x;
+    __syncthreads();
+    double t = 0.0;
+    for (int w = 0; w < nw; ++w) t += s_d[w];
+    __syncthreads();
+    return t;
+}
+
+// Rescale the cost averages of grid `grid`'s VPs for a new k_c array: work
+// modelled as kappa f1 + f2; kappa = a / b from the least-squares fit of the
+// last measured costs to a f1 + b f2 (old array), p.kc_overhead when the
+// fit is ill-posed; cost *= (kappa f1 + f2_new) / (kappa f1 + f2_old).
+// Then the new features become the current ones.
+__global__ void __launch_bounds__(kBalThreads) k_rescale(const DevBal p, int grid) {
+    __shared__ double s_d[kBalWarps];
+    __shared__ double s_kappa;
+    const int tid = threadIdx.x;
+    const bool have = p.state[kStHave] != 0;
+    double a11 = 0.0, a12 = 0.0, a22 = 0.0, b1 = 0.0, b2 = 0.0;
+    for (int v = tid; v < p.nvps; v += kBalThreads) {
+        if (p.vps[v].grid != grid) continue;
+        const double x1 = p.feat1[v], x2 = p.feat2[v], y = p.last[v];
+        a11 += x1 * x1;
+        a12 += x1 * x2;
+        a22 += x2 * x2;
+        b1 += x1 * y;
+        b2 += x2 * y;
+    }
+    a11 = block_sum_f64(a11, s_d);
+    a12 = block_sum_f64(a12, s_d);
+    a22 = block_sum_f64(a22, s_d);
+    b1 = block_sum_f64(b1, s_d);
+    b2 = block_sum_f64(b2, s_d);
+    if (tid == 0) {
+        double kappa = p.kc_overhead;
+        const double det = a11 * a22 - a12 * a12;
+        if (det > 1e-9 * a11 * a22 && a22 > 0.0) {
+            const double a = (b1 * a22 - b2 * a12) / det, b = (a11 * b2 - a12 * b1) / det;
+            if (b > 0.0 && a >= 0.0) kappa = a / b;
+        }
+        s_kappa = kappa;
+        p.pend[1] = kappa;
+    }
+    __syncthreads();
+    const double kappa = s_kappa;
+    for (int v = tid; v < p.nvps; v += kBalThreads) {
+        if (p.vps[v].grid != grid) continue;
+        const double f1 = p.feat1[v], fo = p.feat2[v], fn = p.feat_new[v];
+        const double den = kappa * f1 + fo;
+        if (have && den > 0.0) p.cost[v] = p.cost[v] * ((kappa * f1 + fn) / den);
+        p.feat2[v] = fn;
+    }
+    if (tid == 0 && have) p.state[kStForce] = 1;
+}
+
 }  // namespace
 
 cudaError_t dev_set_kc(GridDev *g, const int32_t *kc, cudaStream_t s) {
     k_set_kc<<<1, 1, 0, s>>>(g, kc);
+    return cudaGetLastError();
+}
+
+cudaError_t dev_kc_features(const DevBal &p, int grid, const int32_t *kc, bool initial,
+                            cudaStream_t s) {
+    const int blocks = (p.nvps * kWarp + 255) / 256;
+    k_features<<<blocks, 256, 0, s>>>(p, grid, kc, initial ? p.feat2 : p.feat_new);
+    if (!initial) k_rescale<<<1, kBalThreads, 0, s>>>(p, grid);
     return cudaGetLastError();
 }
 
@@ -691,10 +837,10 @@ cudaError_t dev_measure(const DevBal &p, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t dev_rebalance(const DevBal &p, int strategy, cudaStream_t s) {
+cudaError_t dev_rebalance(const DevBal &p, int strategy, double threshold, cudaStream_t s) {
     k_prep<<<(p.nvps + kPrepThreads - 1) / kPrepThreads, kPrepThreads, prep_smem(p.nvps), s>>>(
         p, strategy);
-    k_balance<<<1, kBalThreads, dev_balance_smem(p.nvps, p.nbins), s>>>(p, strategy);
+    k_balance<<<1, kBalThreads, dev_balance_smem(p.nvps, p.nbins), s>>>(p, strategy, threshold);
     if (strategy != LB_ATOMIC_QUEUE) k_items<<<p.nbins, kItemThreads, 0, s>>>(p);
     return cudaGetLastError();
 }

@@ -101,13 +101,16 @@ constexpr int kDevBalMaxSms = 1024;
 constexpr int kBalHist = 1024;        // rows kept
 constexpr int kBalHistCols = 8;       // step, strategy, migrations, predicted
                                       // max/mean, measured SM max/mean,
-                                      // granularity floor, refine iterations, 0
+                                      // granularity floor, refine iterations,
+                                      // 1 if the table was kept (threshold)
 enum {
     kStHave = 0,       // 1 once costs exist (measured or set)
     kStRebal = 1,      // table rebalances so far (decides LB_AUTO*)
     kStMeasStep = 2,   // step index of the last measurement
     kStStrategy = 3,   // strategy of the current table
     kStHist = 4,       // history rows written
+    kStForce = 5,      // 1: costs were rescaled, the next threshold test must rebalance
+    kStKept = 6,       // 1: the last call kept the table (the table kernel skips)
     kStWords = 8
 };
 
@@ -129,17 +132,30 @@ struct DevBal {
     const int32_t *spatial;         // [nvps] VPs in spatial order
     const int32_t *nchunks;         // [nvps] work items per VP
     long long *state;               // [kStWords]
-    double *pend;                   // [2] measured SM max/mean of the last measurement
+    double *pend;                   // [2] measured SM max/mean of the last measurement,
+                                    // kappa of the last cost rescale
     double *hist;                   // [kBalHist][kBalHistCols]
     int2 *items;                    // processor tables (written)
     int32_t *bin_start;             // [nbins + 1] (written)
+    // predictive cost model (lb_set_kc with predict_kc)
+    const VPDev *vps;
+    const GridDev *grids;
+    int32_t cols_per_item;
+    double kc_overhead;             // fallback per-item overhead, in k_c sweeps
+    double *feat1;                  // [nvps] items * nz
+    double *feat2;                  // [nvps] sum over items of max k_c * nz (current array)
+    double *feat_new;               // [nvps] the same for a new array
 };
 size_t dev_balance_smem(int nvps, int nbins);
 cudaError_t dev_balance_init();
 cudaError_t dev_measure(const DevBal &p, cudaStream_t s);
-cudaError_t dev_rebalance(const DevBal &p, int strategy, cudaStream_t s);
+cudaError_t dev_rebalance(const DevBal &p, int strategy, double threshold, cudaStream_t s);
 // Point a grid's k_c source at a new array, in stream order.
 cudaError_t dev_set_kc(GridDev *g, const int32_t *kc, cudaStream_t s);
+// Predictive cost model: item features of `grid`'s VPs under array kc
+// (into feat2 when initial, else feat_new and then rescale the averages).
+cudaError_t dev_kc_features(const DevBal &p, int grid, const int32_t *kc, bool initial,
+                            cudaStream_t s);
 
 // Text returned by lb_last_error(NULL) (calls without a ctx).
 void set_ctxless_error(const char *msg);

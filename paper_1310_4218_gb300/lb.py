@@ -54,7 +54,8 @@ class lb_options(ctypes.Structure):
                 ("mass_every", ctypes.c_int32), ("device_balancer", ctypes.c_int32),
                 ("ema_alpha", ctypes.c_double), ("refine_tol", ctypes.c_double),
                 ("barrier_timeout_ns", ctypes.c_int64), ("threads_hint", ctypes.c_int32),
-                ("steal", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
+                ("steal", ctypes.c_int32), ("predict_kc", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 5)]
 
 
 class lb_info(ctypes.Structure):
@@ -94,6 +95,7 @@ _SIG = {
     "lb_destroy": (None, [_P]),
     "lb_device_measure": (_I32, [_P]),
     "lb_device_rebalance": (_I32, [_P, _I32]),
+    "lb_device_rebalance_if": (_I32, [_P, _I32, ctypes.c_double]),
     "lb_get_costs": (_I32, [_P, _P, _P]),
     "lb_balance_history": (_I32, [_P, _P, _I32, _P]),
     "lb_graph_create_periods": (_I32, [_P, _I32, _I32, _I32, ctypes.POINTER(_P)]),
@@ -262,6 +264,11 @@ def lb_device_rebalance(ctx, strategy):
     _check(load_library().lb_device_rebalance(ctx, int(s)), ctx)
 
 
+def lb_device_rebalance_if(ctx, strategy, threshold):
+    s = STRATEGIES.get(strategy, strategy)
+    _check(load_library().lb_device_rebalance_if(ctx, int(s), float(threshold)), ctx)
+
+
 def lb_get_costs(ctx, nvps):
     """(cost average, last measurement) per VP, ns per step."""
     a = np.zeros(nvps, np.float64)
@@ -271,7 +278,7 @@ def lb_get_costs(ctx, nvps):
 
 
 BALANCE_HISTORY_COLUMNS = ("step", "strategy", "migrations", "predicted_max_over_mean",
-                           "sm_max_over_mean", "granularity_floor", "refine_iterations", "zero")
+                           "sm_max_over_mean", "granularity_floor", "refine_iterations", "kept")
 
 
 def lb_balance_history(ctx, max_rows=1024):

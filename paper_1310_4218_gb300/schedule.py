@@ -21,6 +21,9 @@ class Schedule:
     device: measure and rebalance with the device balancer
     (lb_device_measure / lb_device_rebalance): nothing waits for the host
     between periods; per-period records come from lb_balance_history.
+    With a ctx created with lb_options.predict_kc, the k_c arrays of the
+    next segment are installed between the measurement and the balancer
+    call, so the balancer sees costs rescaled for the coming array.
     """
 
     def __init__(self, sim, period, strategy="auto", kc_epochs=None, epoch_steps=0,
@@ -58,14 +61,17 @@ class Schedule:
         t0 = self.t if t0 is None else t0
         return sum(1 for _ in self._segments(t0, t0 + self.period))
 
+    def _install(self, e):
+        if e is not None and e != self._epoch_set and e in self.kc_dev:
+            for gi, d in enumerate(self.kc_dev[e]):
+                if d is not None:
+                    L.lb_set_kc(self.sim.ctx, gi, d.data_ptr())
+            self._epoch_set = e
+
     def run_steps(self, n):
         """n time steps without a balancer call."""
         for t, m, e in self._segments(self.t, self.t + n):
-            if e is not None and e != self._epoch_set and e in self.kc_dev:
-                for gi, d in enumerate(self.kc_dev[e]):
-                    if d is not None:
-                        L.lb_set_kc(self.sim.ctx, gi, d.data_ptr())
-                self._epoch_set = e
+            self._install(e)
             self.sim.step(m)
         self.t += n
 
@@ -73,6 +79,9 @@ class Schedule:
         """Measure the loads of the steps since the last call and rebalance."""
         if self.device:
             L.lb_device_measure(self.sim.ctx)
+            if self.epoch_steps and getattr(self.sim, "options", None) is not None and \
+                    self.sim.options.predict_kc:
+                self._install(self.t // self.epoch_steps)
             L.lb_device_rebalance(self.sim.ctx, self.strategy)
             rec = {"t": self.t, "device": True}
             self.history.append(rec)

@@ -18,6 +18,7 @@ class Simulation:
     def __init__(self, grids, fields, vps, kc_arrays=None, options=None, device="cuda:0",
                  stream=None):
         self.device = torch.device(device)
+        self.options = options
         self.grids = list(grids)
         self.vps = list(vps)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)

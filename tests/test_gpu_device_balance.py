@@ -332,3 +332,109 @@ def test_schedule_in_device_mode():
     for t in range(12):
         ref, _ = oracle.run(g.oracle(kc_of(t)), ref, 1, t0=t)
     assert normwise(out, ref) <= 1e-5
+
+
+def test_kc_redraw_rescales_costs_by_the_fitted_model():
+    """lb_set_kc with predict_kc: every cost average is multiplied by
+    (kappa f1 + f2_new) / (kappa f1 + f2_old), f1 = items * nz, f2 = nz *
+    sum over items of the largest k_c, kappa from the least-squares fit of
+    the last measured costs to (f1, f2_old).  Checked against a numpy
+    restatement (FP64; the device sums in another order, hence rtol)."""
+    from paper_1310_4218_gb300 import lb
+    from paper_1310_4218_gb300.sim import Simulation
+    from workloads.kcfield import lognormal_kc
+    g = Grid(96, 64, 32, kc_disk=False)
+    q = round_to_storage(random_field(g, 81), "f32")
+    vps = regular_blocks(96, 64, 8, 8)
+    kc0 = lognormal_kc(96, 64, 5, 0)
+    kc1 = lognormal_kc(96, 64, 5, 1)
+    o = lb.lb_default_options()
+    o.predict_kc = 1
+    sim = Simulation([g], [q], vps, kc_arrays=[kc0], options=o)
+    nv = len(vps)
+    sim.step(4)
+    lb.lb_device_measure(sim.ctx)
+    avg0, last0 = lb.lb_get_costs(sim.ctx, nv)
+    sim.set_kc(0, kc1)
+    avg1, _ = lb.lb_get_costs(sim.ctx, nv)
+    items_total = sim.info().work_items
+    sim.step(2)
+    out = sim.field(0)
+    sim.close()
+    ncols = [w * h for (_, _, _, w, h) in vps]
+    cpi = 16 if sum(-(-c // 16) for c in ncols) == items_total else 32
+
+    def feats(kc):
+        f1, f2 = [], []
+        for (_, x0, y0, w, h) in vps:
+            flat = np.maximum(kc[y0:y0 + h, x0:x0 + w].ravel(), 0)
+            chunks = [flat[c:c + cpi] for c in range(0, flat.size, cpi)]
+            f1.append(len(chunks) * g.nz)
+            f2.append(sum(int(c.max()) for c in chunks) * g.nz)
+        return np.array(f1, float), np.array(f2, float)
+    f1, f2o = feats(kc0)
+    _, f2n = feats(kc1)
+    a11, a12, a22 = (f1 * f1).sum(), (f1 * f2o).sum(), (f2o * f2o).sum()
+    b1, b2 = (f1 * last0).sum(), (f2o * last0).sum()
+    det = a11 * a22 - a12 * a12
+    kappa = 6.0
+    if det > 1e-9 * a11 * a22 and a22 > 0:
+        a, b = (b1 * a22 - b2 * a12) / det, (a11 * b2 - a12 * b1) / det
+        if b > 0 and a >= 0:
+            kappa = a / b
+    expect = avg0 * ((kappa * f1 + f2n) / (kappa * f1 + f2o))
+    assert np.allclose(avg1, expect, rtol=1e-9, atol=0.0)
+    assert not np.allclose(avg1, avg0)
+    # values are unaffected by the cost model
+    ref, _ = oracle.run(g.oracle(kc0), q, 4)
+    ref, _ = oracle.run(g.oracle(kc1), ref, 2, t0=4)
+    assert normwise(out, ref) <= 1e-5
+
+
+def test_device_threshold_keeps_a_good_table():
+    """lb_device_rebalance_if keeps the table while its predicted max/mean
+    under the current costs is within the threshold, rebalances (exactly as
+    the host balancer) once it is not, and is forced to rebalance after a
+    k_c rescale; steps under kept tables keep their values."""
+    from paper_1310_4218_gb300 import lb
+    from paper_1310_4218_gb300.sim import Simulation
+    from workloads.kcfield import lognormal_kc
+    g = Grid(96, 64, 32, kc_disk=False)
+    q = round_to_storage(random_field(g, 91), "f32")
+    vps = regular_blocks(96, 64, 4, 4)
+    kc0 = lognormal_kc(96, 64, 8, 0)
+    kc1 = lognormal_kc(96, 64, 8, 1)
+    o = lb.lb_default_options()
+    o.predict_kc = 1
+    sim = Simulation([g], [q], vps, kc_arrays=[kc0], options=o)
+    nv, nb = len(vps), sim.info().nprocs
+    c1 = costs_of("uniform", nv, 3)
+    sim.set_costs(c1)
+    lb.lb_device_rebalance(sim.ctx, "greedy_blocked")
+    t1 = sim.assignment()[0]
+    # 2-3 VPs per processor: the table just made predicts well below 3
+    lb.lb_device_rebalance_if(sim.ctx, "greedy_blocked", 3.0)      # good enough: kept
+    row = lb.lb_balance_history(sim.ctx)[-1]
+    assert row[7] == 1 and row[2] == 0 and row[3] <= 3.0
+    assert np.array_equal(sim.assignment()[0], t1)
+    sim.step(2)
+    c2 = costs_of("heavy", nv, 4)
+    sim.set_costs(c2)
+    lb.lb_device_rebalance_if(sim.ctx, "greedy_blocked", 1.01)     # unbalanced: rebalanced
+    row = lb.lb_balance_history(sim.ctx)[-1]
+    ref = B.greedy_blocked(list(map(float, c2)), nb, spatial_order(vps))
+    assert row[7] == 0 and list(sim.assignment()[0]) == ref
+    sim.step(2)
+    lb.lb_device_measure(sim.ctx)
+    sim.set_kc(0, kc1)                                             # rescale forces
+    lb.lb_device_rebalance_if(sim.ctx, "greedy_blocked", 1e9)
+    row = lb.lb_balance_history(sim.ctx)[-1]
+    assert row[7] == 0
+    lb.lb_device_rebalance_if(sim.ctx, "greedy_blocked", 1e9)      # then kept again
+    assert lb.lb_balance_history(sim.ctx)[-1][7] == 1
+    sim.step(3)
+    out = sim.field(0)
+    sim.close()
+    ref, _ = oracle.run(g.oracle(kc0), q, 4)
+    ref, _ = oracle.run(g.oracle(kc1), ref, 3, t0=4)
+    assert normwise(out, ref) <= 1e-5
