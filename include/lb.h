@@ -379,6 +379,9 @@ typedef struct {
     int64_t work_items;       /* items of 32 columns per step */
     int32_t strategy;         /* strategy of the current table */
     int32_t regs_per_thread;
+    int32_t item_w, item_h;   /* work item shape: an item_w x item_h tile of a
+                                 VP (tiles row-major), or item_h == 0: runs of
+                                 item_w columns of the VP in row-major order */
 } lb_info;
 
 lb_status lb_get_info(lb_ctx *ctx, lb_info *info);

@@ -493,7 +493,7 @@ extern "C" lb_status lb_create(const lb_grid_desc *grids, int32_t ngrids, const 
     for (int v = 0; v < nvps; ++v) {
         const lb_vp &p = vps[v];
         hv[v] = VPDev{p.grid, p.x0, p.y0, p.w, p.h, p.w * p.h, 0, 0};
-        ctx->vp_nchunks[v] = (p.w * p.h + ctx->kinfo.cols_per_item - 1) / ctx->kinfo.cols_per_item;
+        ctx->vp_nchunks[v] = items_of_vp(ctx->kinfo, p.w, p.h);
         ctx->nitems += ctx->vp_nchunks[v];
     }
     static_blocks(nvps, ctx->nbins, ctx->assign);
@@ -754,6 +754,8 @@ static DevBal make_devbal(lb_ctx *ctx) {
     p.vps = ctx->d_vps;
     p.grids = ctx->d_grids;
     p.cols_per_item = ctx->kinfo.cols_per_item;
+    p.tile_w = ctx->kinfo.tile_w;
+    p.tile_h = ctx->kinfo.tile_h;
     p.kc_overhead = 6.0;
     p.feat1 = ctx->d_feat1;
     p.feat2 = ctx->d_feat2;
@@ -1274,6 +1276,8 @@ extern "C" lb_status lb_get_info(lb_ctx *ctx, lb_info *info) {
     info->work_items = ctx->nitems;
     info->strategy = ctx->queue_mode ? LB_ATOMIC_QUEUE : ctx->strategy;
     info->regs_per_thread = ctx->regs;
+    info->item_w = ctx->kinfo.tile_w ? ctx->kinfo.tile_w : ctx->kinfo.cols_per_item;
+    info->item_h = ctx->kinfo.tile_w ? ctx->kinfo.tile_h : 0;
     return LB_OK;
 }
 

@@ -707,9 +707,10 @@ __global__ void k_set_kc(GridDev *g, const int32_t *kc) { g->kc = kc; }
 
 // Item features of grid `grid`'s VPs under k_c array kc, one warp per VP:
 // out[v] = nz * sum over the VP's work items of the largest k_c among the
-// item's columns (the sweeps a warp runs for it).  Work items are runs of
-// cols_per_item (16 or 32) columns of the VP in row-major order, so each
-// warp pass over 32 columns covers whole items.
+// item's columns (the sweeps a warp runs for it).  Items are the kernel's:
+// tile_w x tile_h tiles (row-major over tiles), or runs of cols_per_item
+// columns in row-major order; either way a warp pass over 32 item slots
+// covers whole items (32 is a multiple of the item size).
 __global__ void __launch_bounds__(256) k_features(const DevBal p, int grid, const int32_t *kc,
                                                   double *out) {
     const int v = (int)((blockIdx.x * blockDim.x + threadIdx.x) / kWarp);
@@ -718,22 +719,38 @@ __global__ void __launch_bounds__(256) k_features(const DevBal p, int grid, cons
     const VPDev vp = p.vps[v];
     if (vp.grid != grid) return;
     const GridDev &g = p.grids[grid];
-    const int cpi = p.cols_per_item;
+    const bool tiles = p.tile_w > 0;
+    const int isz = tiles ? p.tile_w * p.tile_h : p.cols_per_item;
+    const int tiles_x = tiles ? (vp.w + p.tile_w - 1) / p.tile_w : 1;
+    const int nitems = tiles ? tiles_x * ((vp.h + p.tile_h - 1) / p.tile_h)
+                             : (vp.ncols + isz - 1) / isz;
     long long sum = 0;
-    for (int base = 0; base < vp.ncols; base += kWarp) {
-        const int q = base + lane;
+    for (int base = 0; base < nitems * isz; base += kWarp) {
+        const int slot = base + lane;
+        const int it = slot / isz, c = slot - it * isz;
+        int xi, yi;
+        bool ok;
+        if (tiles) {
+            const int ty = it / tiles_x, tx = it - ty * tiles_x;
+            xi = tx * p.tile_w + c % p.tile_w;
+            yi = ty * p.tile_h + c / p.tile_w;
+            ok = it < nitems && xi < vp.w && yi < vp.h;
+        } else {
+            const int q = it * isz + c;
+            yi = q / vp.w;
+            xi = q - yi * vp.w;
+            ok = q < vp.ncols;
+        }
         int k = 0;
-        if (q < vp.ncols) {
-            const int ly = q / vp.w;
-            const int i = vp.x0 + (q - ly * vp.w), j = vp.y0 + ly;
-            const int kv = kc[(size_t)j * g.nx + i];
+        if (ok) {
+            const int kv = kc[(size_t)(vp.y0 + yi) * g.nx + vp.x0 + xi];
             k = kv > 0 ? kv : 0;
         }
-        for (int o = cpi / 2; o > 0; o >>= 1) {
+        for (int o = isz / 2; o > 0; o >>= 1) {
             const int k2 = __shfl_xor_sync(kFull, k, o);
             k = k2 > k ? k2 : k;
         }
-        if (lane % cpi == 0) sum += k;
+        if (lane % isz == 0) sum += k;
     }
     sum = (long long)__reduce_add_sync(kFull, (unsigned)sum);
     if (lane == 0) out[v] = (double)sum * (double)g.nz;

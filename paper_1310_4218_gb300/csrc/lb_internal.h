@@ -83,7 +83,22 @@ struct KernelInfo {
     int exact;
     int split;          // 1: two lanes per column (twisted factorisation)
     int cols_per_item;  // columns of one work item: 32, or 16 when split
+    int tile_w, tile_h; // split kernels: an item is a tile_w x tile_h tile of
+                        // the VP (row-major over tiles); 0: runs of
+                        // cols_per_item columns in the VP's row-major order
 };
+
+// Split kernels' work items: 8 x 2 column tiles.  A compact tile spans less
+// of a smooth k_c field than a 16 x 1 run, so its lanes' sweep counts differ
+// less (the warp runs the largest); each row of 8 FP32 columns is one
+// 32-byte sector when the VP's x extent is a multiple of 8.
+constexpr int kTileW = 8, kTileH = 2;
+
+// Work items of a w x h VP.
+inline int items_of_vp(const KernelInfo &k, int w, int h) {
+    if (k.tile_w > 0) return ((w + k.tile_w - 1) / k.tile_w) * ((h + k.tile_h - 1) / k.tile_h);
+    return (w * h + k.cols_per_item - 1) / k.cols_per_item;
+}
 bool find_step_kernel(int storage, int compute, int nz_max, int nz_min, bool all_same_nz,
                       KernelInfo *out, int threads_hint = 0);
 
@@ -141,6 +156,7 @@ struct DevBal {
     const VPDev *vps;
     const GridDev *grids;
     int32_t cols_per_item;
+    int32_t tile_w, tile_h;         // item shape (KernelInfo)
     double kc_overhead;             // fallback per-item overhead, in k_c sweeps
     double *feat1;                  // [nvps] items * nz
     double *feat2;                  // [nvps] sum over items of max k_c * nz (current array)

@@ -185,7 +185,6 @@ extern "C" lb_status lb_step_noalloc(const lb_grid_desc *grid, const lb_vp *vps,
     KernelInfo ki;
     if (!find_step_kernel(d.storage, d.compute, d.nz, d.nz, true, &ki))
         return fail(LB_EINVAL, "no kernel variant for this grid");
-    const int cpi = ki.cols_per_item;
     long long area = 0, nitems = 0;
     for (int v = 0; v < nvps; ++v) {
         const lb_vp &p = vps[v];
@@ -193,7 +192,7 @@ extern "C" lb_status lb_step_noalloc(const lb_grid_desc *grid, const lb_vp *vps,
             p.y0 + p.h > d.ny)
             return fail(LB_EINVAL, "a VP lies outside the grid (grid index must be 0)");
         area += (long long)p.w * p.h;
-        nitems += (p.w * p.h + cpi - 1) / cpi;
+        nitems += items_of_vp(ki, p.w, p.h);
     }
     if (area != (long long)d.nx * d.ny) return fail(LB_EINVAL, "VPs do not tile the grid");
     if (nitems > kMaxItems) return fail(LB_EINVAL, "too many work items for LB_NOALLOC_MAX_ITEMS");
@@ -270,8 +269,8 @@ extern "C" lb_status lb_step_noalloc(const lb_grid_desc *grid, const lb_vp *vps,
         h_bin_start[b] = ni;
         const int vend = (int)(((long long)(b + 1) * nvps) / nbins);
         for (; v < vend; ++v) {
-            const int ncols = vps[v].w * vps[v].h;
-            for (int c = 0; c * cpi < ncols; ++c) h_items[ni++] = make_int2(v, c);
+            const int n = items_of_vp(ki, vps[v].w, vps[v].h);
+            for (int c = 0; c < n; ++c) h_items[ni++] = make_int2(v, c);
         }
     }
     h_bin_start[nbins] = ni;

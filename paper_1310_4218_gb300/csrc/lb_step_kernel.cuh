@@ -338,13 +338,17 @@ __device__ __forceinline__ int process_item_split(const StepParams<TC> &p, const
     constexpr int H = NZ / 2;
     static_assert(H % 2 == 0, "levels are processed in pairs");
     constexpr int kCols = kWarp / 2;
+    static_assert(kTileW * kTileH == kCols, "a tile is one column per lane pair");
     const int top = lane >> 4;
-    const int q = chunk * kCols + (lane & (kCols - 1));
-    const bool active = q < vp.ncols;
-    const int qq = active ? q : vp.ncols - 1;
-    const int ly = qq / vp.w;
-    const int i = vp.x0 + (qq - ly * vp.w);
-    const int j = vp.y0 + ly;
+    // item = kTileW x kTileH tile of the VP, tiles in row-major order; lane
+    // pair (c, c + 16) holds column c of the tile
+    const int c = lane & (kCols - 1);
+    const int tiles_x = (vp.w + kTileW - 1) / kTileW;
+    const int ty = chunk / tiles_x, tx = chunk - ty * tiles_x;
+    const int xi = tx * kTileW + (c % kTileW), yi = ty * kTileH + c / kTileW;
+    const bool active = xi < vp.w && yi < vp.h;
+    const int i = vp.x0 + (xi < vp.w ? xi : vp.w - 1);
+    const int j = vp.y0 + (yi < vp.h ? yi : vp.h - 1);
     int im = i - g.sx, jm = j - g.sy;
     im = im < 0 ? im + g.nx : (im >= g.nx ? im - g.nx : im);
     jm = jm < 0 ? jm + g.ny : (jm >= g.ny ? jm - g.ny : jm);
@@ -689,6 +693,8 @@ inline KernelInfo kernel_entry() {
     k.exact = EXACT ? 1 : 0;
     k.split = SPLIT ? 1 : 0;
     k.cols_per_item = SPLIT ? kWarp / 2 : kWarp;
+    k.tile_w = SPLIT ? kTileW : 0;
+    k.tile_h = SPLIT ? kTileH : 0;
     return k;
 }
 

@@ -63,7 +63,8 @@ class lb_info(ctypes.Structure):
                 ("threads_per_cta", ctypes.c_int32), ("max_ctas_per_sm", ctypes.c_int32),
                 ("nz_variant", ctypes.c_int32), ("exact_nz", ctypes.c_int32),
                 ("step", ctypes.c_int64), ("work_items", ctypes.c_int64),
-                ("strategy", ctypes.c_int32), ("regs_per_thread", ctypes.c_int32)]
+                ("strategy", ctypes.c_int32), ("regs_per_thread", ctypes.c_int32),
+                ("item_w", ctypes.c_int32), ("item_h", ctypes.c_int32)]
 
 
 _P = ctypes.c_void_p

@@ -54,3 +54,20 @@ def normwise(gpu, ref):
 def random_field(g, seed, lo=0.2, hi=1.0):
     rng = np.random.default_rng(seed)
     return rng.uniform(lo, hi, size=(g.nz, g.ny, g.nx))
+
+
+def item_kc(kc, vp, item_w, item_h):
+    """k_c values of each work item of VP (grid, x0, y0, w, h), in the
+    kernel's item shape (lb_info.item_w / item_h): item_w x item_h tiles in
+    row-major order, or (item_h == 0) runs of item_w columns of the VP in
+    row-major order."""
+    _, x0, y0, w, h = vp
+    block = kc[y0:y0 + h, x0:x0 + w]
+    if item_h == 0:
+        flat = block.ravel()
+        return [flat[c:c + item_w] for c in range(0, flat.size, item_w)]
+    out = []
+    for ty in range(0, h, item_h):
+        for tx in range(0, w, item_w):
+            out.append(block[ty:ty + item_h, tx:tx + item_w].ravel())
+    return out

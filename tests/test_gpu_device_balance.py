@@ -11,7 +11,7 @@ pytestmark = pytest.mark.gpu
 
 import oracle  # noqa: E402
 from oracle import balance as B  # noqa: E402
-from gpu_common import Grid, normwise, random_field, round_to_storage  # noqa: E402
+from gpu_common import Grid, item_kc, normwise, random_field, round_to_storage  # noqa: E402
 from workloads import regular_blocks  # noqa: E402
 
 
@@ -357,21 +357,19 @@ def test_kc_redraw_rescales_costs_by_the_fitted_model():
     avg0, last0 = lb.lb_get_costs(sim.ctx, nv)
     sim.set_kc(0, kc1)
     avg1, _ = lb.lb_get_costs(sim.ctx, nv)
-    items_total = sim.info().work_items
+    info = sim.info()
     sim.step(2)
     out = sim.field(0)
     sim.close()
-    ncols = [w * h for (_, _, _, w, h) in vps]
-    cpi = 16 if sum(-(-c // 16) for c in ncols) == items_total else 32
 
     def feats(kc):
         f1, f2 = [], []
-        for (_, x0, y0, w, h) in vps:
-            flat = np.maximum(kc[y0:y0 + h, x0:x0 + w].ravel(), 0)
-            chunks = [flat[c:c + cpi] for c in range(0, flat.size, cpi)]
+        for vp in vps:
+            chunks = item_kc(np.maximum(kc, 0), vp, info.item_w, info.item_h)
             f1.append(len(chunks) * g.nz)
             f2.append(sum(int(c.max()) for c in chunks) * g.nz)
         return np.array(f1, float), np.array(f2, float)
+    assert sum(len(item_kc(kc0, vp, info.item_w, info.item_h)) for vp in vps) == info.work_items
     f1, f2o = feats(kc0)
     _, f2n = feats(kc1)
     a11, a12, a22 = (f1 * f1).sum(), (f1 * f2o).sum(), (f2o * f2o).sum()

@@ -8,7 +8,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 import oracle  # noqa: E402
-from gpu_common import Grid, normwise, random_field, round_to_storage, tolerance  # noqa: E402
+from gpu_common import Grid, item_kc, normwise, random_field, round_to_storage, tolerance  # noqa: E402
 from workloads import gaussian_blob, guillotine, regular_blocks  # noqa: E402
 
 
@@ -263,12 +263,12 @@ def test_measured_costs_follow_kc():
     sim.step(4)
     cost, busy = sim.measure()
     kc = oracle.kc_field(g.oracle(), 0)
-    # a work item is 32 consecutive columns (one per lane) of the VP's
-    # row-major order: it costs a fixed part plus its lanes' largest k_c
+    # a work item (the kernel's shape, lb_info) costs a fixed part plus its
+    # lanes' largest k_c
+    info = sim.info()
     items, sweeps = [], []
-    for (_, x0, y0, w, h) in vps:
-        flat = kc[y0:y0 + h, x0:x0 + w].ravel()
-        chunks = [flat[c:c + 32] for c in range(0, flat.size, 32)]
+    for vp in vps:
+        chunks = item_kc(kc, vp, info.item_w, info.item_h)
         items.append(len(chunks))
         sweeps.append(sum(int(c.max()) for c in chunks))
     X = np.stack([np.array(items, float), np.array(sweeps, float)], axis=1)
