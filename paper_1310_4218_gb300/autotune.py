@@ -6,9 +6,11 @@ Knobs:
                least 2*min_side columns per side into quadrants (finer
                over-decomposition, Sec. III: more, smaller VPs balance better
                but add halo traffic)
-  variant   -- lb_options.threads_hint: 0 default kernel, 2 split columns
-               without staged loads, 1 one lane per column
-  strategy  -- assignment (lb_strategy name)
+  variant   -- lb_options.threads_hint: 0 default kernel (split columns
+               where offered), 1 one lane per column
+  strategy  -- assignment (lb_strategy name), balanced on the device with
+               end-of-step stealing, the cost rescale at k_c re-draws and a
+               threshold (keep the table while predicted max/mean <= 1.15)
   period    -- time steps between balancer calls
 
 Each candidate runs `warmup` periods, then is timed over `timed` periods
@@ -57,16 +59,19 @@ def signature(grids, vps, kc_epoch_steps):
 
 
 def measure(grids, fields, vps, kc_epochs, epoch_steps, strategy, period, variant, warmup=2,
-            timed=2, device="cuda:0"):
+            timed=2, device="cuda:0", threshold=1.15):
     """Cell-sweep updates/s of one configuration (device-timed)."""
     opt = L.lb_default_options()
     opt.threads_hint = variant
+    opt.steal = 1
+    opt.predict_kc = 1
     kc0 = kc_epochs[0] if kc_epochs else None
     dev = torch.device(device)
     stream = torch.cuda.Stream(dev)
     sim = Simulation(grids, fields, vps, kc_arrays=kc0, options=opt, device=dev, stream=stream)
     try:
-        sch = Schedule(sim, period, strategy, kc_epochs, epoch_steps)
+        sch = Schedule(sim, period, strategy, kc_epochs, epoch_steps,
+                       threshold=None if strategy == "queue" else threshold, device=True)
         for _ in range(warmup):
             sch.run_period()
         torch.cuda.synchronize(dev)
@@ -85,7 +90,8 @@ def measure(grids, fields, vps, kc_epochs, epoch_steps, strategy, period, varian
 
 
 def autotune(grids, fields, vps, kc_epochs=None, epoch_steps=0, cache=None,
-             strategies=("auto_spatial", "queue"), periods=(10, 20), variants=(0, 2),
+             strategies=("greedy_blocked", "auto_spatial", "queue"), periods=(10, 20),
+             variants=(0, 1),
              splits=(1, 2), device="cuda:0", log=None):
     """Best configuration over the candidate grid; returns a dict with the
     knobs, the score and every candidate's score."""

@@ -19,8 +19,11 @@ class Schedule:
     on (they are free on the device), migrations happen only when needed.
 
     device: measure and rebalance with the device balancer
-    (lb_device_measure / lb_device_rebalance): nothing waits for the host
-    between periods; per-period records come from lb_balance_history.
+    (lb_device_measure / lb_device_rebalance_if): nothing waits for the host
+    between periods; per-period records come from lb_balance_history.  A
+    threshold then keeps the table while its predicted max/mean under the
+    current costs stays within it (on the host balancer the test is on the
+    measured SM max/mean).  The atomic queue is entered once on the host.
     With a ctx created with lb_options.predict_kc, the k_c arrays of the
     next segment are installed between the measurement and the balancer
     call, so the balancer sees costs rescaled for the coming array.
@@ -28,8 +31,6 @@ class Schedule:
 
     def __init__(self, sim, period, strategy="auto", kc_epochs=None, epoch_steps=0,
                  threshold=None, device=False):
-        if device and threshold is not None:
-            raise ValueError("threshold-triggered rebalancing runs on the host balancer")
         self.device = device
         self.sim = sim
         self.period = int(period)
@@ -82,7 +83,9 @@ class Schedule:
             if self.epoch_steps and getattr(self.sim, "options", None) is not None and \
                     self.sim.options.predict_kc:
                 self._install(self.t // self.epoch_steps)
-            L.lb_device_rebalance(self.sim.ctx, self.strategy)
+            if self.strategy == "queue" and self.sim.info().strategy != L.LB_ATOMIC_QUEUE:
+                self.sim.rebalance("queue")
+            L.lb_device_rebalance_if(self.sim.ctx, self.strategy, self.threshold or 0.0)
             rec = {"t": self.t, "device": True}
             self.history.append(rec)
             return rec

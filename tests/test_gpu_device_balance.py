@@ -436,3 +436,19 @@ def test_device_threshold_keeps_a_good_table():
     ref, _ = oracle.run(g.oracle(kc0), q, 4)
     ref, _ = oracle.run(g.oracle(kc1), ref, 3, t0=4)
     assert normwise(out, ref) <= 1e-5
+
+
+def test_autotuner_picks_the_fastest_candidate_and_caches(tmp_path):
+    from paper_1310_4218_gb300.autotune import autotune
+    g = Grid(128, 96, 32, disk=(30, 30, 1, 1, 20), k_in=24, k_out=1)
+    q = round_to_storage(random_field(g, 5), "f32")
+    vps = regular_blocks(128, 96, 16, 16)
+    cache = str(tmp_path / "tune.json")
+    res = autotune([g], [q], vps, cache=cache, strategies=("greedy_blocked", "queue"),
+                   periods=(4,), variants=(0,), splits=(1, 2))
+    vals = [c["value"] for c in res["candidates"] if c["value"]]
+    assert len(res["candidates"]) == 4 and len(vals) == 4
+    assert res["value"] == max(vals)
+    again = autotune([g], [q], vps, cache=cache, strategies=("greedy_blocked", "queue"),
+                     periods=(4,), variants=(0,), splits=(1, 2))
+    assert again == res
