@@ -20,8 +20,9 @@ time steps as the workload prescribes.
 
 Strategy names: an lb_strategy name, optionally followed by "+steal"
 (end-of-step work stealing), "+dev" (device balancer), "+pred" (cost
-rescale at k_c re-draws, with +dev) and "+thr" (keep a table within the
-1.15 threshold, with +dev).
+rescale at k_c re-draws, with +dev), "+thr" (keep a table within the
+1.15 threshold, with +dev) and "+graph" (each period one CUDA graph
+replay: steps, device measurement, device rebalance; with +dev).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--workload NAME] [--period P] [--strategy auto|static|queue|...]
@@ -269,6 +270,10 @@ class StrategyRun:
         # balancer runs and the costs are rescaled by the fitted model
         self.predict = "pred" in flags and self.dev_mode
         self.threshold = "thr" in flags and self.dev_mode
+        # "+graph": each period replays one CUDA graph (steps, device
+        # measurement, device rebalance); k_c re-draws between replays
+        self.use_graph = "graph" in flags and self.dev_mode and strategy != "queue"
+        self.gexec = None
         self.kc_epoch = None
         self.dev_tags = []
         self.kernels = 0             # our kernel launches (step, k_c switch, balancer)
@@ -296,7 +301,15 @@ class StrategyRun:
                 e = t // w.kc_epoch_steps
                 self.set_epoch(e)
                 n = min(n, (e + 1) * w.kc_epoch_steps - t)
-            self.sim.step(n)
+            if self.use_graph and n == self.P:
+                if self.gexec is None:
+                    self.gexec = self.lb.lb_graph_create_periods(
+                        self.sim.ctx, self.P, self.strategy, 1, 1.15 if self.threshold else 0.0)
+                self.lb.lb_graph_launch(self.sim.ctx, self.gexec)
+                self.kernels += 4                  # measure, prep, balance, items
+                self.dev_tags.append("graph")
+            else:
+                self.sim.step(n)
             t += n
             n_launch += 1
         self.kernels += n_launch
@@ -314,6 +327,20 @@ class StrategyRun:
     def balance(self, tag, t_next):
         """Load measurement (Sec. V) and the balancer call (Sec. VI) before
         time step t_next."""
+        if self.use_graph and self.gexec is not None:
+            # measured and rebalanced inside the graph; a k_c re-draw with
+            # +pred rescales the costs and forces one more rebalance now
+            if self.dev_tags and self.dev_tags[-1] == "graph":
+                self.dev_tags[-1] = tag
+            if self.predict and self.epochs:
+                e = t_next // self.w.kc_epoch_steps
+                if e != self.kc_epoch:
+                    self.set_epoch(e)
+                    self.lb.lb_device_rebalance_if(self.sim.ctx, self.strategy,
+                                                   1.15 if self.threshold else 0.0)
+                    self.kernels += 3
+                    self.dev_tags.append(tag)
+            return
         if self.dev_mode:
             # enqueued only: measurement, cost rounding and ranks, balancer,
             # table kernels (the queue has no table: measurement and record)
@@ -428,6 +455,9 @@ class StrategyRun:
                 "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
 
     def close(self):
+        if self.gexec is not None:
+            self.lb.lb_graph_destroy(self.sim.ctx, self.gexec)
+            self.gexec = None
         self.sim.close()
 
 
@@ -494,7 +524,8 @@ def main():
     if not args.no_compare:
         for st in [x for x in ("static", "static+steal", "auto", "auto+dev", "auto_spatial+steal",
                                "auto_spatial+steal+dev", "greedy_blocked+steal+dev",
-                               "greedy_blocked+steal+dev+pred", "queue", "queue+dev")
+                               "greedy_blocked+steal+dev+pred",
+                               "greedy_blocked+steal+dev+pred+thr+graph", "queue", "queue+dev")
                    if x != args.strategy]:
             r2 = StrategyRun(w, fields, epochs, kc_dev, args, dev, stream, st)
             r2.warmup(args.warmup)

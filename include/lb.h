@@ -348,12 +348,14 @@ lb_status lb_balance_history(lb_ctx *ctx, double *rows, int32_t max, int32_t *n)
 /*
  * One executable graph of nperiods rebalance periods (Fig. 2's loop): each
  * period is one persistent launch of nsteps steps, lb_device_measure and
- * lb_device_rebalance(strategy).  Replay with lb_graph_launch (the ctx's
- * step counters advance by nsteps*nperiods); destroy with
- * lb_graph_destroy.  Same availability rules as lb_device_rebalance.
+ * lb_device_rebalance_if(strategy, threshold) (threshold <= 0: always
+ * rebalance).  Replay with lb_graph_launch (the ctx's step counters advance
+ * by nsteps*nperiods); destroy with lb_graph_destroy.  lb_set_kc between
+ * replays switches the k_c array (and rescales costs with predict_kc).
+ * Same availability rules as lb_device_rebalance.
  */
 lb_status lb_graph_create_periods(lb_ctx *ctx, int32_t nsteps, int32_t strategy,
-                                  int32_t nperiods, void **graph_exec);
+                                  int32_t nperiods, double threshold, void **graph_exec);
 
 /* Wait for all work of the ctx; report a pending device-side error. */
 lb_status lb_sync(lb_ctx *ctx);

@@ -843,8 +843,9 @@ extern "C" lb_status lb_balance_history(lb_ctx *ctx, double *rows, int32_t max, 
 }
 
 extern "C" lb_status lb_graph_create_periods(lb_ctx *ctx, int32_t nsteps, int32_t strategy,
-                                             int32_t nperiods, void **graph_exec) {
-    if (!ctx || !graph_exec || nsteps < 1 || nperiods < 1)
+                                             int32_t nperiods, double threshold,
+                                             void **graph_exec) {
+    if (!ctx || !graph_exec || nsteps < 1 || nperiods < 1 || !(threshold == threshold))
         return fail(ctx, LB_EINVAL, "lb_graph_create_periods: bad arguments");
     *graph_exec = nullptr;
     lb_status st = devbal_check(ctx, strategy, true);
@@ -864,7 +865,7 @@ extern "C" lb_status lb_graph_create_periods(lb_ctx *ctx, int32_t nsteps, int32_
             st = ctx->compute == LB_F64 ? launch<double>(ctx, nsteps, ctx->coef_d)
                                         : launch<float>(ctx, nsteps, ctx->coef_f);
             if (st == LB_OK) e = dev_measure(db, cap);
-            if (st == LB_OK && e == cudaSuccess) e = dev_rebalance(db, strategy, 0.0, cap);
+            if (st == LB_OK && e == cudaSuccess) e = dev_rebalance(db, strategy, threshold, cap);
         }
         ctx->stream = own;
         cudaError_t e2 = cudaStreamEndCapture(cap, &graph);

@@ -99,7 +99,8 @@ _SIG = {
     "lb_device_rebalance_if": (_I32, [_P, _I32, ctypes.c_double]),
     "lb_get_costs": (_I32, [_P, _P, _P]),
     "lb_balance_history": (_I32, [_P, _P, _I32, _P]),
-    "lb_graph_create_periods": (_I32, [_P, _I32, _I32, _I32, ctypes.POINTER(_P)]),
+    "lb_graph_create_periods": (_I32, [_P, _I32, _I32, _I32, ctypes.c_double,
+                                       ctypes.POINTER(_P)]),
     "lb_step_noalloc": (_I32, [ctypes.POINTER(lb_grid_desc), ctypes.POINTER(lb_vp), _I32,
                                ctypes.c_int64, _I32, _P, _P]),
 }
@@ -292,13 +293,13 @@ def lb_balance_history(ctx, max_rows=1024):
     return buf[:n.value]
 
 
-def lb_graph_create_periods(ctx, nsteps, strategy, nperiods):
+def lb_graph_create_periods(ctx, nsteps, strategy, nperiods, threshold=0.0):
     """Executable CUDA graph of nperiods x (nsteps steps, device measurement,
-    device rebalance)."""
+    device rebalance within threshold)."""
     g = _P()
     s = STRATEGIES.get(strategy, strategy)
     _check(load_library().lb_graph_create_periods(ctx, int(nsteps), int(s), int(nperiods),
-                                                  ctypes.byref(g)), ctx)
+                                                  float(threshold), ctypes.byref(g)), ctx)
     return g.value
 
 

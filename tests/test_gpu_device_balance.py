@@ -246,7 +246,7 @@ def test_graph_of_rebalance_periods():
     ref = a.field(0)
     a.close()
     b = make_sim([g], [q], vps, steal=1)
-    graph = lb.lb_graph_create_periods(b.ctx, 2, "auto_spatial", 3)
+    graph = lb.lb_graph_create_periods(b.ctx, 2, "auto_spatial", 3, 0.0)
     lb.lb_graph_launch(b.ctx, graph)
     lb.lb_graph_launch(b.ctx, graph)
     out = b.field(0)
