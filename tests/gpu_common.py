@@ -71,3 +71,27 @@ def item_kc(kc, vp, item_w, item_h):
         for tx in range(0, w, item_w):
             out.append(block[ty:ty + item_h, tx:tx + item_w].ravel())
     return out
+
+
+def report(name, **metrics):
+    """Append measured metrics to the JSON file named by LB_REPORT (if set):
+    the error and drift figures the design notes state per workload."""
+    import json
+    import os
+    path = os.environ.get("LB_REPORT")
+    if not path:
+        return
+    data = {}
+    if os.path.exists(path):
+        with open(path) as f:
+            data = json.load(f)
+    data[name] = {k: (float(v) if v is not None else None) for k, v in metrics.items()}
+    with open(path, "w") as f:
+        json.dump(data, f, indent=1)
+
+
+def mass_drift(hist, m0):
+    """Largest per-step change and total change of the global sum, relative
+    to the initial sum."""
+    h = np.concatenate([[m0], np.asarray(hist, dtype=np.float64)])
+    return float(np.abs(np.diff(h)).max() / abs(m0)), float(abs(h[-1] - m0) / abs(m0))

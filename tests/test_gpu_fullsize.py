@@ -12,7 +12,7 @@ torch = pytest.importorskip("torch")
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 
 import oracle  # noqa: E402
-from gpu_common import normwise, round_to_storage, tolerance  # noqa: E402
+from gpu_common import mass_drift, normwise, report, round_to_storage, tolerance  # noqa: E402
 from workloads import get_config  # noqa: E402
 
 
@@ -65,6 +65,7 @@ def window_check(w, gi, q0, out, epochs, nsteps, corners, valid=8):
         refs = list(ex.map(one, jobs))
     errs = []
     scale = 0.0
+    sq_d = sq_r = 0.0
     for (i0, j0, _), ref in zip(jobs, refs):
         r = ref[:, nsteps:, nsteps:]
         assert np.isfinite(r).all()
@@ -73,6 +74,9 @@ def window_check(w, gi, q0, out, epochs, nsteps, corners, valid=8):
         gpu = out[:, jj][:, :, ii]
         errs.append(float(np.abs(gpu - r).max()))
         scale = max(scale, float(np.abs(r).max()))
+        sq_d += float(((gpu - r) ** 2).sum())
+        sq_r += float((r ** 2).sum())
+    window_check.l2 = (sq_d / sq_r) ** 0.5 if sq_r > 0 else 0.0
     return max(errs), scale
 
 
@@ -82,6 +86,11 @@ def test_plain_fp64_full_field():
     q0 = w.grids[0].initial_field()
     outs, hist, _, _ = run_gpu(w, [q0], w.steps, strategy="static")
     ref, mass = oracle.run(oracle.OracleGrid.from_spec(w.grids[0]), q0, w.steps)
+    d = np.abs(outs[0] - ref)
+    report("plain_fp64_64x64x32", max_abs=d.max(), normwise=normwise(outs[0], ref),
+           l2_rel=np.sqrt((d ** 2).sum() / (ref ** 2).sum()),
+           mass_vs_oracle=np.max(np.abs(hist[0] - mass)) / abs(mass[0]),
+           mass_step_drift=mass_drift(hist[0], oracle.compensated_sum(q0))[0])
     assert normwise(outs[0], ref) <= 1e-12
     assert np.max(np.abs(hist[0] - mass)) <= 1e-12 * abs(mass[0])
 
@@ -94,8 +103,11 @@ def test_hotspot_512_fp32_windows():
     # the disk's final centre (228, 228), its rim, a cold corner, the wrap seam
     corners = [(224, 224), (280, 230), (60, 400), (508, 3)]
     err, scale = window_check(w, 0, q0, outs[0], None, w.steps, corners)
-    assert err / scale <= 1e-5, err / scale
     m0 = oracle.compensated_sum(q0)
+    step_d, tot_d = mass_drift(hist[0], m0)
+    report("hotspot_fp32_512x512x64", max_abs=err, normwise=err / scale, l2_rel=window_check.l2,
+           mass_step_drift=step_d, mass_total_drift=tot_d)
+    assert err / scale <= 1e-5, err / scale
     assert np.max(np.abs(hist[0] - m0)) <= 1e-6 * m0
     assert sched[0]["migrations"] > 0
 
@@ -109,6 +121,9 @@ def test_lognormal_1024_fp32_windows():
     j, i = np.unravel_index(np.argmax(kc), kc.shape)       # a k_c = 64 hotspot
     corners = [(int(i) - 4, int(j) - 4), (1020, 1019)]
     err, scale = window_check(w, 0, q0, outs[0], epochs, w.steps, corners)
+    step_d, tot_d = mass_drift(hist[0], oracle.compensated_sum(q0))
+    report("lognormal_fp32_1024x1024x96", max_abs=err, normwise=err / scale,
+           l2_rel=window_check.l2, mass_step_drift=step_d, mass_total_drift=tot_d)
     assert err / scale <= 1e-5, err / scale
 
 
@@ -120,6 +135,9 @@ def test_precision_2048_windows(storage):
     outs, hist, _, _ = run_gpu(w, [q0], w.steps)
     corners = [(556, 556), (300, 800), (1500, 1500), (2045, 2046)]
     err, scale = window_check(w, 0, q0, outs[0], None, w.steps, corners)
+    step_d, tot_d = mass_drift(hist[0], oracle.compensated_sum(q0))
+    report("precision_2048x2048x64_" + storage, max_abs=err, normwise=err / scale,
+           l2_rel=window_check.l2, mass_step_drift=step_d, mass_total_drift=tot_d)
     assert err / scale <= tolerance(g, w.steps), err / scale
 
 
@@ -136,4 +154,5 @@ def test_batch64_windows():
         err, scale = window_check(w, gi, fields[gi], outs[gi], None, w.steps,
                                   [(cx, cy), (g.nx - 2, g.ny - 3)], valid=4)
         worst = max(worst, err / scale)
+    report("batch64_fp32", normwise=worst)
     assert worst <= 1e-5, worst
