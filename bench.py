@@ -555,7 +555,10 @@ def main():
                        "parallelism": "replicas" if world > 1 else "1gpu",
                        "l2": "fields larger than L2 (no flush)",
                        "cell_steps_per_s": cells_all / s,
-                       "processors": info.nprocs, "threads_per_cta": info.threads_per_cta},
+                       "processors": info.nprocs, "threads_per_cta": info.threads_per_cta,
+                       "per_grid_cell_steps_per_s": (
+                           [g.nx * g.ny * g.nz * args.steps * P * world / s for g in w.grids]
+                           if len(w.grids) > 1 else None)},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_source": peak_src,
                          "traffic": (tr["dram_bytes_per_step"] * steps_per_launch) if tr else None,

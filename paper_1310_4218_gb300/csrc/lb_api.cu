@@ -484,6 +484,7 @@ extern "C" lb_status lb_create(const lb_grid_desc *grids, int32_t ngrids, const 
         h.rlast_d = d.r * ml;
         h.mlast_f = (float)ml;
         h.rlast_f = (float)(d.r * ml);
+        if (d.nz >= 2) split_coupling(d.r, d.nz, &h.ifa_b_f, &h.ifa_t_f, &h.ifc_bt_f);
     }
 
     // VP table and work items

@@ -29,6 +29,10 @@ struct GridDev {
     double wd[4];                  // same for FP64 compute
     float mlast_f, rlast_f;        // last-row coefficients (runtime-nz kernels)
     double mlast_d, rlast_d;
+    // runtime-nz split kernels: lower half ceil(nz/2) levels, upper half
+    // floor(nz/2); middle coupling a_b = r m[Hb-1], a_t = r m[Ht-1],
+    // c = 1 / (1 - a_b a_t)
+    float ifa_b_f, ifa_t_f, ifc_bt_f, pad1;
 };
 
 // One VP (rectangle of columns of one grid).
@@ -107,7 +111,26 @@ bool kernels_f32(int nz_max, int nz_min, bool same, int threads_hint, KernelInfo
 bool kernels_f64(int nz_max, int nz_min, bool same, KernelInfo *out);
 bool kernels_f64s(int nz_max, int nz_min, bool same, KernelInfo *out);
 bool kernels_bf16(int nz_max, int nz_min, bool same, KernelInfo *out);
-bool kernels_f32_any(int nz_max, int nz_min, KernelInfo *out);
+bool kernels_f32_any(int nz_max, int nz_min, bool one_lane, KernelInfo *out);
+
+// Middle coupling of the runtime-nz split kernels for a column of nz >= 2
+// rows: lower half hb = ceil(nz/2) rows, upper ht = floor(nz/2), each
+// eliminated from its zero-flux end with the nz-independent pivots m_k
+// (m_0 = 1/(1+r), m_k = 1/(1+2r-r^2 m_{k-1})); a_b = r m_{hb-1},
+// a_t = r m_{ht-1}, c = 1/(1 - a_b a_t); FP64, rounded once.
+inline void split_coupling(double r, int nz, float *ab, float *at, float *c) {
+    const int hb = (nz + 1) / 2, ht = nz / 2;
+    double m = 0.0, mb = 0.0, mt = 0.0;
+    for (int k = 0; k < hb; ++k) {
+        m = k == 0 ? 1.0 / (1.0 + r) : 1.0 / (1.0 + 2.0 * r - r * r * m);
+        if (k == hb - 1) mb = m;
+        if (k == ht - 1) mt = m;
+    }
+    const double a_b = ht >= 1 ? r * mb : 0.0, a_t = ht >= 1 ? r * mt : 0.0;
+    *ab = (float)a_b;
+    *at = (float)a_t;
+    *c = (float)(1.0 / (1.0 - a_b * a_t));
+}
 
 // Device balancer (lb_device_balance.cu): limits, state words, history.
 constexpr int kDevBalMaxVps = 8192;

@@ -264,6 +264,7 @@ extern "C" lb_status lb_step_noalloc(const lb_grid_desc *grid, const lb_vp *vps,
     g.rlast_d = d.r * ml;
     g.mlast_f = (float)ml;
     g.rlast_f = (float)(d.r * ml);
+    if (d.nz >= 2) split_coupling(d.r, d.nz, &g.ifa_b_f, &g.ifa_t_f, &g.ifc_bt_f);
     int ni = 0;
     for (int b = 0, v = 0; b < nbins; ++b) {
         h_bin_start[b] = ni;

@@ -23,7 +23,7 @@ bool kernels_f32(int nz_max, int nz_min, bool same, int threads_hint, KernelInfo
         else *out = kernel_entry<float, float, 96, true, 1, 768, true>();
         return true;
     }
-    return kernels_f32_any(nz_max, nz_min, out);
+    return kernels_f32_any(nz_max, nz_min, one_lane, out);
 }
 
 }  // namespace lbk

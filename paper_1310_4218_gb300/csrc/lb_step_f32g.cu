@@ -4,7 +4,14 @@
 
 namespace lbk {
 
-bool kernels_f32_any(int nz_max, int nz_min, KernelInfo *out) {
+bool kernels_f32_any(int nz_max, int nz_min, bool one_lane, KernelInfo *out) {
+    // split columns with runtime nz (any nz >= 2 up to the bucket)
+    if (!one_lane && nz_min >= 2) {
+        if (nz_max <= 32) { *out = kernel_entry<float, float, 32, false, 1, 1024, true>(); return true; }
+        if (nz_max <= 64) { *out = kernel_entry<float, float, 64, false, 1, 768, true>(); return true; }
+        if (nz_max <= 96) { *out = kernel_entry<float, float, 96, false, 1, 768, true>(); return true; }
+    }
+    // one lane per column
     if (nz_max <= 32) { *out = kernel_entry<float, float, 32, false, 1, 512>(); return true; }
     if (nz_max <= 64) { *out = kernel_entry<float, float, 64, false, 1, 512>(); return true; }
     if (nz_max <= 96 && nz_min >= 32) { *out = kernel_entry<float, float, 96, false, 32, 384>(); return true; }

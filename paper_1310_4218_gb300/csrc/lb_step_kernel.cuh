@@ -447,6 +447,152 @@ __device__ __forceinline__ int process_item_split(const StepParams<TC> &p, const
     return top ? 0 : kc;
 }
 
+// Split columns for grids of any nz in [2, 2 * HMAX] (several grids of
+// different nz in one launch): the lower lane holds the ceil(nz/2) lowest
+// levels, the upper lane the floor(nz/2) highest, each counted from its own
+// end.  Both eliminate toward the middle with the same nz-independent
+// pivots of a column that starts at a zero-flux end; the middle 2x2 system
+// couples them with the grid's a_b, a_t.  The lane's half length is a
+// runtime value, so no per-level branch may depend on it (the compiler
+// could turn it into a loop bound and move the column out of registers):
+// loads read a clamped level, selects keep levels beyond the half at zero,
+// and stores are predicated in PTX.
+__device__ __forceinline__ void st_pred(float *ptr, float v, bool pred) {
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t@q st.global.f32 [%0], %1;\n\t}"
+                 :: "l"(ptr), "f"(v), "r"((unsigned)pred) : "memory");
+}
+
+template <class TS, class TC, int HMAX>
+__device__ __forceinline__ int process_item_split_rt(const StepParams<TC> &p, const GridDev &g,
+                                                     const VPDev &vp, int chunk, long long t,
+                                                     int src, int lane, bool do_mass,
+                                                     LaneSum<TC> &acc) {
+    static_assert(sizeof(TS) == 4 && sizeof(TC) == 4, "split kernels are FP32");
+    static_assert(HMAX % 2 == 0, "levels are processed in pairs");
+    constexpr int kCols = kWarp / 2;
+    static_assert(kTileW * kTileH == kCols, "a tile is one column per lane pair");
+    const int top = lane >> 4;
+    const int c = lane & (kCols - 1);
+    const int tiles_x = (vp.w + kTileW - 1) / kTileW;
+    const int ty = chunk / tiles_x, tx = chunk - ty * tiles_x;
+    const int xi = tx * kTileW + (c % kTileW), yi = ty * kTileH + c / kTileW;
+    const bool active = xi < vp.w && yi < vp.h;
+    const int i = vp.x0 + (xi < vp.w ? xi : vp.w - 1);
+    const int j = vp.y0 + (yi < vp.h ? yi : vp.h - 1);
+    int im = i - g.sx, jm = j - g.sy;
+    im = im < 0 ? im + g.nx : (im >= g.nx ? im - g.nx : im);
+    jm = jm < 0 ? jm + g.ny : (jm >= g.ny ? jm - g.ny : jm);
+    const int plane = g.plane, nz = g.nz;
+    const int hlen = top ? nz / 2 : (nz + 1) / 2;     // levels this lane holds
+    const int oc = j * g.nx + i, oi = j * g.nx + im, oj = jm * g.nx + i;
+    const int lbase = top ? (nz - 1) * plane : 0;
+    const int lstep = top ? -plane : plane;
+    const TS *in = static_cast<const TS *>(g.q[src]);
+    TS *out = static_cast<TS *>(g.q[src ^ 1]);
+
+    int kc = g.kc_disk ? kc_disk(g, i, j, t) : g.kc[oc];
+    if (!active || !g.sweeps_on) kc = 0;
+
+    float2 y2[HMAX / 2];
+    float *y = reinterpret_cast<float *>(y2);
+    const float wx = wgt<float>(g, 1), wy = wgt<float>(g, 2);
+    if (g.xy_only) {
+        const float2 wx2 = f2(wx, wx), wy2 = f2(wy, wy);
+#pragma unroll
+        for (int m = 0; m < HMAX / 2; ++m) {
+            const int s0 = min(2 * m, hlen - 1), s1 = min(2 * m + 1, hlen - 1);
+            const int off0 = lbase + s0 * lstep, off1 = lbase + s1 * lstep;
+            const float2 a = f2(IO<TS, TC>::ld(in + (off0 + oi)), IO<TS, TC>::ld(in + (off1 + oi)));
+            const float2 b = f2(IO<TS, TC>::ld(in + (off0 + oj)), IO<TS, TC>::ld(in + (off1 + oj)));
+            const float2 v = fma2(wy2, b, mul2(wx2, a));
+            y2[m] = f2(2 * m < hlen ? v.x : 0.f, 2 * m + 1 < hlen ? v.y : 0.f);
+        }
+    } else {
+        const float w0 = wgt<float>(g, 0), wz = wgt<float>(g, 3);
+        const int sz = g.sz;
+        const int kdown = sz >= 0 ? nz - 1 : 0;
+#pragma unroll
+        for (int s = 0; s < HMAX; ++s) {
+            const int sc = min(s, hlen - 1);
+            const int k = top ? nz - 1 - sc : sc;
+            const int off = lbase + sc * lstep;
+            const float cc = IO<TS, TC>::ld(in + (off + oc));
+            const float a = IO<TS, TC>::ld(in + (off + oi));
+            const float b = IO<TS, TC>::ld(in + (off + oj));
+            float v = fmaT(wy, b, wx * a);
+            v = fmaT(k == kdown ? w0 + wz : w0, cc, v);
+            const int ku = k - sz;
+            const int kuc = ku < 0 ? 0 : (ku >= nz ? nz - 1 : ku);
+            const float u = IO<TS, TC>::ld(in + (kuc * plane + oc));
+            v = (ku >= 0 && ku < nz) ? fmaT(wz, u, v) : v;
+            y[s] = s < hlen ? v : 0.f;
+        }
+    }
+
+    // shift by the column's level ceil(nz/2)-1 value (the lower lane's last)
+    float last = 0.f;
+#pragma unroll
+    for (int s = 0; s < HMAX; ++s) last = s == hlen - 1 ? y[s] : last;
+    const float mid = __shfl_xor_sync(0xffffffffu, last, kCols);
+    const float cref = kc > 0 ? (top ? mid : last) : 0.f;
+    if (kc > 0) {
+        const float2 nc = f2(-cref, -cref);
+#pragma unroll
+        for (int m = 0; m < HMAX / 2; ++m) y2[m] = add2(y2[m], nc);
+    }
+    const Coef<TC> &cf = p.coef;
+    const float ifa = top ? g.ifa_t_f : g.ifa_b_f, ifc = g.ifc_bt_f;
+    const int kmax = __reduce_max_sync(0xffffffffu, (unsigned)kc);
+    for (int r = 0; r < kmax; ++r) {
+        const bool act = r < kc;
+        float pp = 0.f;
+        if (act) {
+            pp = y[0] * cf.m[0];
+            y[0] = pp;
+#pragma unroll
+            for (int s = 1; s < HMAX; ++s) {
+                const float np = fmaT(pp, cf.rm[s], y[s] * cf.m[s]);
+                const bool in_half = s < hlen;
+                y[s] = in_half ? np : y[s];
+                pp = in_half ? np : pp;
+            }
+        }
+        const float other = __shfl_xor_sync(0xffffffffu, pp, kCols);
+        if (act) {
+            const float xl = fmaT(ifa, other, pp) * ifc;
+            y[HMAX - 1] = hlen == HMAX ? xl : y[HMAX - 1];
+#pragma unroll
+            for (int s = HMAX - 2; s >= 0; --s) {
+                const float bk = fmaT(cf.rm[s], y[s + 1], y[s]);
+                y[s] = s == hlen - 1 ? xl : (s < hlen - 1 ? bk : y[s]);
+            }
+        }
+    }
+
+    const float2 c2 = f2(cref, cref);
+    PairSum ps;
+    if (do_mass) ps.begin();
+#pragma unroll
+    for (int m = 0; m < HMAX / 2; ++m) {
+        float2 x = add2(y2[m], c2);
+        const bool v0 = active && 2 * m < hlen, v1 = active && 2 * m + 1 < hlen;
+        st_pred(out + (lbase + (v0 ? 2 * m : 0) * lstep + oc), x.x, v0);
+        st_pred(out + (lbase + (v1 ? 2 * m + 1 : 0) * lstep + oc), x.y, v1);
+        x.x = v0 ? x.x : 0.f;
+        x.y = v1 ? x.y : 0.f;
+        if (do_mass) ps.add(x);
+    }
+    if (do_mass && active) {
+        acc.col_begin();
+        acc.s = ps.s.x;
+        acc.e = ps.e.x;
+        acc.add(ps.s.y);
+        acc.e = __fadd_rn(acc.e, ps.e.y);
+        acc.col_end();
+    }
+    return top ? 0 : kc;
+}
+
 // ------------------------------------------------------------ grid barrier
 // Sense-reversing barrier over all CTAs with a time limit.  On timeout the
 // CTA records LB_ETIMEOUT in the status word and returns false; so does
@@ -635,8 +781,22 @@ lb_step_kernel(const __grid_constant__ StepParams<TC> p) {
             }
             long long c0 = clock64();
             int kc;
-            if constexpr (SPLIT)
+            if constexpr (SPLIT && EXACT)
                 kc = process_item_split<TS, TC, NZ>(p, g, vp, it.y, t, src, lane, do_mass, acc);
+            else if constexpr (SPLIT) {
+                // per item (one grid, warp-uniform): the smallest half-length
+                // bucket that holds the grid's ceil(nz/2) levels
+                const int hb = (g.nz + 1) / 2;
+                if (NZ / 2 > 16 && hb <= 16)
+                    kc = process_item_split_rt<TS, TC, 16>(p, g, vp, it.y, t, src, lane, do_mass,
+                                                          acc);
+                else if (NZ / 2 > 32 && hb <= 32)
+                    kc = process_item_split_rt<TS, TC, 32>(p, g, vp, it.y, t, src, lane, do_mass,
+                                                          acc);
+                else
+                    kc = process_item_split_rt<TS, TC, NZ / 2>(p, g, vp, it.y, t, src, lane,
+                                                              do_mass, acc);
+            }
             else
                 kc = process_item<TS, TC, NZ, EXACT, NZLO>(p, g, vp, it.y, t, src, lane, do_mass,
                                                            acc);
@@ -685,7 +845,7 @@ lb_step_kernel(const __grid_constant__ StepParams<TC> p) {
 
 template <class TS, class TC, int NZ, bool EXACT, int NZLO, int THREADS, bool SPLIT = false>
 inline KernelInfo kernel_entry() {
-    static_assert(!SPLIT || (EXACT && NZ % 2 == 0), "split kernels need an exact, even nz");
+    static_assert(!SPLIT || NZ % 4 == 0, "split kernels hold nz/2 levels in register pairs");
     KernelInfo k;
     k.fn = (const void *)&lb_step_kernel<TS, TC, NZ, EXACT, NZLO, THREADS, SPLIT>;
     k.threads = THREADS;

@@ -37,7 +37,8 @@ def oracle_run(g, q, nsteps, t0=0, kc=None):
 VARIANTS = [
     # storage, compute, nz  (exact-nz kernels and runtime-nz kernels)
     ("f32", "f32", 32), ("f32", "f32", 64), ("f32", "f32", 96),
-    ("f32", "f32", 1), ("f32", "f32", 5), ("f32", "f32", 17), ("f32", "f32", 47),
+    ("f32", "f32", 1), ("f32", "f32", 2), ("f32", "f32", 3), ("f32", "f32", 5),
+    ("f32", "f32", 17), ("f32", "f32", 33), ("f32", "f32", 47), ("f32", "f32", 95),
     ("f32", "f32", 100), ("f32", "f32", 128),
     ("f64", "f64", 32), ("f64", "f64", 7), ("f64", "f64", 50),
     ("f64", "f32", 64), ("f64", "f32", 20), ("f64", "f32", 90),
