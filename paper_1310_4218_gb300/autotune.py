@@ -10,7 +10,8 @@ Knobs:
                where offered), 1 one lane per column
   strategy  -- assignment (lb_strategy name), balanced on the device with
                end-of-step stealing, the cost rescale at k_c re-draws and a
-               threshold (keep the table while predicted max/mean <= 1.15)
+               threshold (keep the table while predicted max/mean <= 1.15);
+               layouts of more than 8192 VPs use the host balancer
   period    -- time steps between balancer calls
 
 Each candidate runs `warmup` periods, then is timed over `timed` periods
@@ -70,8 +71,11 @@ def measure(grids, fields, vps, kc_epochs, epoch_steps, strategy, period, varian
     stream = torch.cuda.Stream(dev)
     sim = Simulation(grids, fields, vps, kc_arrays=kc0, options=opt, device=dev, stream=stream)
     try:
+        # the device balancer takes up to 8192 VPs; beyond, the host balancer
+        dev_ok = len(vps) <= 8192
         sch = Schedule(sim, period, strategy, kc_epochs, epoch_steps,
-                       threshold=None if strategy == "queue" else threshold, device=True)
+                       threshold=None if (strategy == "queue" or not dev_ok) else threshold,
+                       device=dev_ok)
         for _ in range(warmup):
             sch.run_period()
         torch.cuda.synchronize(dev)
