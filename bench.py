@@ -321,7 +321,7 @@ class StrategyRun:
             return
         for gi in range(len(self.w.grids)):
             self.lb.lb_set_kc(self.sim.ctx, gi, self.kc_dev[e][gi].data_ptr())
-            self.kernels += 3 if self.predict else 1
+            self.kernels += 4 if self.predict else 1   # switch, features, fit, rescale
         self.kc_epoch = e
 
     def balance(self, tag, t_next):

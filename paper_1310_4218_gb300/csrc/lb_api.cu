@@ -62,6 +62,7 @@ struct lb_ctx {
     double *d_bhist = nullptr;
     unsigned *d_ticket = nullptr;
     double *d_feat1 = nullptr, *d_feat2 = nullptr, *d_featn = nullptr;   // predictive cost model
+    double *d_fit = nullptr;
     bool predict = false;              // predict_kc active
     bool dev_newer = false;            // device balancer state newer than the host copy
     std::string devbal_off;            // why the device balancer is unavailable ("" = available)
@@ -278,7 +279,7 @@ static void free_ctx(lb_ctx *ctx) {
                     ctx->d_last,      ctx->d_assign,   ctx->d_order,     ctx->d_spatial,
                     ctx->d_nchunks,   ctx->d_bstate,   ctx->d_pend,      ctx->d_bhist,
                     ctx->d_ticket,    ctx->d_q,        ctx->d_feat1,     ctx->d_feat2,
-                    ctx->d_featn};
+                    ctx->d_featn,     ctx->d_fit};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete ctx;
@@ -529,6 +530,7 @@ extern "C" lb_status lb_create(const lb_grid_desc *grids, int32_t ngrids, const 
     if (e == cudaSuccess) e = dalloc(&ctx->d_feat1, nvps);
     if (e == cudaSuccess) e = dalloc(&ctx->d_feat2, nvps);
     if (e == cudaSuccess) e = dalloc(&ctx->d_featn, nvps);
+    if (e == cudaSuccess) e = dalloc(&ctx->d_fit, (size_t)kFitBlocks * 5);
     if (e == cudaSuccess) e = dalloc(&ctx->d_spatial, nvps);
     if (e == cudaSuccess) e = dalloc(&ctx->d_nchunks, nvps);
     if (e == cudaSuccess) e = dalloc(&ctx->d_bstate, kStWords);
@@ -761,6 +763,7 @@ static DevBal make_devbal(lb_ctx *ctx) {
     p.feat1 = ctx->d_feat1;
     p.feat2 = ctx->d_feat2;
     p.feat_new = ctx->d_featn;
+    p.fit = ctx->d_fit;
     return p;
 }
 

@@ -26,6 +26,9 @@
 //              migrations and predicted max/mean
 //   k_items    one CTA per processor: its work-item range and its items in
 //              spatial order (the tables the step kernel reads)
+//   k_features, k_fit, k_rescale  cost rescale for a new k_c array
+//              (lb_set_kc with predict_kc): item features, least-squares
+//              fit of the per-item overhead, rescaled cost averages
 #include <cuda_runtime.h>
 
 #include "lb_internal.h"
@@ -769,32 +772,42 @@ __device__ double block_sum_f64(double x, double *s_d) {
     return t;
 }
 
-// Rescale the cost averages of grid `grid`'s VPs for a new k_c array: work
-// modelled as kappa f1 + f2; kappa = a / b from the least-squares fit of the
-// last measured costs to a f1 + b f2 (old array), p.kc_overhead when the
-// fit is ill-posed; cost *= (kappa f1 + f2_new) / (kappa f1 + f2_old).
-// Then the new features become the current ones.
-__global__ void __launch_bounds__(kBalThreads) k_rescale(const DevBal p, int grid) {
-    __shared__ double s_d[kBalWarps];
-    __shared__ double s_kappa;
-    const int tid = threadIdx.x;
-    const bool have = p.state[kStHave] != 0;
-    double a11 = 0.0, a12 = 0.0, a22 = 0.0, b1 = 0.0, b2 = 0.0;
-    for (int v = tid; v < p.nvps; v += kBalThreads) {
-        if (p.vps[v].grid != grid) continue;
+// Cost rescale for a new k_c array of grid `grid`, part 1: per block of
+// kFitThreads VPs the sums of the least-squares fit of the last measured
+// costs y to a f1 + b f2 (old array): sum x1^2, x1 x2, x2^2, x1 y, x2 y.
+__global__ void __launch_bounds__(kFitThreads) k_fit(const DevBal p, int grid) {
+    __shared__ double s_d[kFitThreads / kWarp];
+    const int v = blockIdx.x * kFitThreads + threadIdx.x;
+    double t[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    if (v < p.nvps && p.vps[v].grid == grid) {
         const double x1 = p.feat1[v], x2 = p.feat2[v], y = p.last[v];
-        a11 += x1 * x1;
-        a12 += x1 * x2;
-        a22 += x2 * x2;
-        b1 += x1 * y;
-        b2 += x2 * y;
+        t[0] = x1 * x1;
+        t[1] = x1 * x2;
+        t[2] = x2 * x2;
+        t[3] = x1 * y;
+        t[4] = x2 * y;
     }
-    a11 = block_sum_f64(a11, s_d);
-    a12 = block_sum_f64(a12, s_d);
-    a22 = block_sum_f64(a22, s_d);
-    b1 = block_sum_f64(b1, s_d);
-    b2 = block_sum_f64(b2, s_d);
-    if (tid == 0) {
+    for (int k = 0; k < 5; ++k) {
+        const double sum = block_sum_f64(t[k], s_d);
+        if (threadIdx.x == 0) p.fit[blockIdx.x * 5 + k] = sum;
+    }
+}
+
+// Part 2: every block adds the partial sums in block order (the same kappa
+// everywhere) -- kappa = a / b, p.kc_overhead when the fit is ill-posed --
+// and rescales its VPs: cost *= (kappa f1 + f2_new) / (kappa f1 + f2_old);
+// the new features become the current ones.
+__global__ void __launch_bounds__(kFitThreads) k_rescale(const DevBal p, int grid, int nblocks) {
+    __shared__ double s_kappa;
+    if (threadIdx.x == 0) {
+        double a11 = 0.0, a12 = 0.0, a22 = 0.0, b1 = 0.0, b2 = 0.0;
+        for (int k = 0; k < nblocks; ++k) {
+            a11 += p.fit[k * 5 + 0];
+            a12 += p.fit[k * 5 + 1];
+            a22 += p.fit[k * 5 + 2];
+            b1 += p.fit[k * 5 + 3];
+            b2 += p.fit[k * 5 + 4];
+        }
         double kappa = p.kc_overhead;
         const double det = a11 * a22 - a12 * a12;
         if (det > 1e-9 * a11 * a22 && a22 > 0.0) {
@@ -802,18 +815,19 @@ __global__ void __launch_bounds__(kBalThreads) k_rescale(const DevBal p, int gri
             if (b > 0.0 && a >= 0.0) kappa = a / b;
         }
         s_kappa = kappa;
-        p.pend[1] = kappa;
+        if (blockIdx.x == 0) p.pend[1] = kappa;
     }
     __syncthreads();
+    const bool have = p.state[kStHave] != 0;
     const double kappa = s_kappa;
-    for (int v = tid; v < p.nvps; v += kBalThreads) {
-        if (p.vps[v].grid != grid) continue;
+    const int v = blockIdx.x * kFitThreads + threadIdx.x;
+    if (v < p.nvps && p.vps[v].grid == grid) {
         const double f1 = p.feat1[v], fo = p.feat2[v], fn = p.feat_new[v];
         const double den = kappa * f1 + fo;
         if (have && den > 0.0) p.cost[v] = p.cost[v] * ((kappa * f1 + fn) / den);
         p.feat2[v] = fn;
     }
-    if (tid == 0 && have) p.state[kStForce] = 1;
+    if (blockIdx.x == 0 && threadIdx.x == 0 && have) p.state[kStForce] = 1;
 }
 
 }  // namespace
@@ -827,7 +841,11 @@ cudaError_t dev_kc_features(const DevBal &p, int grid, const int32_t *kc, bool i
                             cudaStream_t s) {
     const int blocks = (p.nvps * kWarp + 255) / 256;
     k_features<<<blocks, 256, 0, s>>>(p, grid, kc, initial ? p.feat2 : p.feat_new);
-    if (!initial) k_rescale<<<1, kBalThreads, 0, s>>>(p, grid);
+    if (!initial) {
+        const int nb = (p.nvps + kFitThreads - 1) / kFitThreads;
+        k_fit<<<nb, kFitThreads, 0, s>>>(p, grid);
+        k_rescale<<<nb, kFitThreads, 0, s>>>(p, grid, nb);
+    }
     return cudaGetLastError();
 }
 

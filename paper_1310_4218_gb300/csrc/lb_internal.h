@@ -184,7 +184,10 @@ struct DevBal {
     double *feat1;                  // [nvps] items * nz
     double *feat2;                  // [nvps] sum over items of max k_c * nz (current array)
     double *feat_new;               // [nvps] the same for a new array
+    double *fit;                    // [kFitBlocks][5] partial sums of the cost fit
 };
+constexpr int kFitThreads = 256;
+constexpr int kFitBlocks = (kDevBalMaxVps + kFitThreads - 1) / kFitThreads;
 size_t dev_balance_smem(int nvps, int nbins);
 cudaError_t dev_balance_init();
 cudaError_t dev_measure(const DevBal &p, cudaStream_t s);

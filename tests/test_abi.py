@@ -116,3 +116,31 @@ def test_plan_greedy_blocked_matches_oracle(lbmod, seed):
     ref = B.greedy_blocked(costs, nb, list(range(nv)))
     assert list(g) == ref
     assert pred == B.max_over_mean(costs, ref, nb)
+
+
+@pytest.mark.parametrize("scale_exp", [-300, -20, 0, 20, 300])
+@pytest.mark.parametrize("strategy", ["greedy", "greedy_blocked", "refine_swap"])
+def test_plan_fixed_point_grid_at_any_cost_scale(lbmod, scale_exp, strategy):
+    """The balancers' fixed-point grid (C++ llrint(ldexp)) equals the
+    oracle's (Python round(ldexp)) for costs of any magnitude, zeros and
+    exact ties included."""
+    rng = random.Random(900 + scale_exp)
+    nb = rng.randint(2, 40)
+    nv = rng.randint(nb, 600)
+    scale = 10.0 ** scale_exp
+    costs = [rng.lognormvariate(0, 2) * scale for _ in range(nv)]
+    for v in rng.sample(range(nv), nv // 10):
+        costs[v] = 0.0
+    for v in rng.sample(range(nv), nv // 10):
+        costs[v] = costs[0]
+    cur = [rng.randrange(nb) for _ in range(nv)]
+    a, mig, pred = lbmod.lb_plan(strategy, costs, nb, current=cur)
+    if strategy == "greedy":
+        ref = B.greedy(costs, nb)
+    elif strategy == "greedy_blocked":
+        ref = B.greedy_blocked(costs, nb, list(range(nv)))
+    else:
+        ref = B.refine_swap(costs, cur, nb)
+    assert list(a) == ref
+    assert pred == B.max_over_mean(costs, ref, nb)
+    assert mig == B.migrations(cur, ref)
