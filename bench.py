@@ -266,6 +266,11 @@ class StrategyRun:
         strategy, flags = parts[0], set(parts[1:])
         steal = "steal" in flags
         self.dev_mode = "dev" in flags
+        # "+tma": the TMA-staged kernel; "+half" / "+pair": split columns on
+        # half-warps / paired warps (default: paired where VP widths allow)
+        staged = "tma" in flags
+        half = "half" in flags
+        pair = "pair" in flags
         # "+pred": at a k_c re-draw the new array is installed before the
         # balancer runs and the costs are rescaled by the fitted model
         self.predict = "pred" in flags and self.dev_mode
@@ -283,6 +288,11 @@ class StrategyRun:
         opt.queue_order = 0
         opt.steal = 1 if steal else 0
         opt.predict_kc = 1 if self.predict else 0
+        opt.staged_loads = 1 if staged else 0
+        if half:
+            opt.threads_hint = 2
+        if pair:
+            opt.threads_hint = 3
         kc0 = [epochs[0][gi] for gi in range(len(w.grids))] if epochs else None
         self.sim = Simulation(w.grids, fields, w.vps, kc_arrays=kc0, options=opt, device=dev,
                               stream=stream)
@@ -525,7 +535,9 @@ def main():
         for st in [x for x in ("static", "static+steal", "auto", "auto+dev", "auto_spatial+steal",
                                "auto_spatial+steal+dev", "greedy_blocked+steal+dev",
                                "greedy_blocked+steal+dev+pred",
-                               "greedy_blocked+steal+dev+pred+thr+graph", "queue", "queue+dev")
+                               "greedy_blocked+steal+dev+pred+thr+graph",
+                               "greedy_blocked+steal+dev+pred+thr+pair",
+                               "greedy_blocked+steal+dev+pred+thr+tma", "queue", "queue+dev")
                    if x != args.strategy]:
             r2 = StrategyRun(w, fields, epochs, kc_dev, args, dev, stream, st)
             r2.warmup(args.warmup)

@@ -141,8 +141,14 @@ typedef struct {
                                      per-VP cost average (default 0.5) */
     double refine_tol;            /* RefineSwapLB tolerance (default 0.05) */
     int64_t barrier_timeout_ns;   /* grid-barrier wait limit (default 2 s) */
-    int32_t threads_hint;         /* threads per processor for kernels that
-                                     have several variants (0: default) */
+    int32_t threads_hint;         /* kernel variant for FP32 grids: 0 default
+                                     (split columns; for nz 32, 64, 96 on
+                                     paired warps with 16 x 2 tiles when
+                                     every VP width is a multiple of 16,
+                                     else on half-warps with 8 x 2 tiles),
+                                     1 one lane per column, 2 split columns
+                                     on half-warps, 3 split columns on
+                                     paired warps (nz 32, 64, 96) */
     int32_t steal;                /* 1: with processor tables, a processor
                                      that finishes its VPs takes the next
                                      work items of the processor with the
@@ -150,7 +156,11 @@ typedef struct {
     int32_t predict_kc;           /* 1: lb_set_kc also rescales each VP's cost
                                      average for the new k_c array (see
                                      lb_set_kc); default 0 */
-    int32_t reserved[5];          /* must be 0 */
+    int32_t staged_loads;         /* 1: the TMA-staged kernel where it applies
+                                     (FP32 split columns of nz 32, 64 or 96,
+                                     nx % 4 == 0, 16-byte aligned fields);
+                                     default 0 */
+    int32_t reserved[4];          /* must be 0 */
 } lb_options;
 
 /* Fill *opt with the defaults listed above. */
@@ -384,6 +394,10 @@ typedef struct {
     int32_t item_w, item_h;   /* work item shape: an item_w x item_h tile of a
                                  VP (tiles row-major), or item_h == 0: runs of
                                  item_w columns of the VP in row-major order */
+    int32_t staged_slots;     /* TMA-staged kernel: input boxes in flight per
+                                 processor (shared-memory ring); 0: each warp
+                                 loads its own items */
+    int32_t pad0;
 } lb_info;
 
 lb_status lb_get_info(lb_ctx *ctx, lb_info *info);

@@ -1,7 +1,9 @@
 // C ABI of liblb.so: ctx life cycle, validation, work tables, launches,
 // load measurement and rebalancing.  Declarations and contracts: lb.h.
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 
 #include <algorithm>
 #include <cmath>
@@ -63,6 +65,7 @@ struct lb_ctx {
     unsigned *d_ticket = nullptr;
     double *d_feat1 = nullptr, *d_feat2 = nullptr, *d_featn = nullptr;   // predictive cost model
     double *d_fit = nullptr;
+    CUtensorMap *d_tmaps = nullptr;    // TMA-staged kernel: [ngrids][2] field maps
     bool predict = false;              // predict_kc active
     bool dev_newer = false;            // device balancer state newer than the host copy
     std::string devbal_off;            // why the device balancer is unavailable ("" = available)
@@ -279,7 +282,7 @@ static void free_ctx(lb_ctx *ctx) {
                     ctx->d_last,      ctx->d_assign,   ctx->d_order,     ctx->d_spatial,
                     ctx->d_nchunks,   ctx->d_bstate,   ctx->d_pend,      ctx->d_bhist,
                     ctx->d_ticket,    ctx->d_q,        ctx->d_feat1,     ctx->d_feat2,
-                    ctx->d_featn,     ctx->d_fit};
+                    ctx->d_featn,     ctx->d_fit,      ctx->d_tmaps};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete ctx;
@@ -288,6 +291,53 @@ static void free_ctx(lb_ctx *ctx) {
 template <class T>
 static cudaError_t dalloc(T **p, size_t n) {
     return cudaMalloc((void **)p, sizeof(T) * std::max<size_t>(n, 1));
+}
+
+// ------------------------------------------------------------------ TMA maps
+// Tensor maps of every grid's two field buffers for the TMA-staged kernel:
+// FP32, dims (nx, ny, nz) x-fastest, box kBoxW x kBoxH x nz (the 12 x 3
+// column neighbourhood of an 8 x 2 tile, all levels), zero fill outside.
+// The kernel applies when every buffer is 16-byte aligned and rows are a
+// multiple of 16 bytes (nx % 4 == 0), TMA's addressing rules.
+static bool staged_eligible(const std::vector<lb_grid_desc> &grids) {
+    for (const auto &d : grids) {
+        if (d.storage != LB_F32 || d.compute != LB_F32 || d.nx % 4 != 0) return false;
+        if ((reinterpret_cast<uintptr_t>(d.q0) | reinterpret_cast<uintptr_t>(d.q1)) & 15u) return false;
+    }
+    return true;
+}
+
+static bool encode_tmaps(const std::vector<lb_grid_desc> &grids, int nz_box,
+                         std::vector<CUtensorMap> &maps, std::string &why) {
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn) {
+        why = "cuTensorMapEncodeTiled unavailable";
+        return false;
+    }
+    auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    maps.assign(2 * grids.size(), CUtensorMap{});
+    for (size_t g = 0; g < grids.size(); ++g) {
+        const lb_grid_desc &d = grids[g];
+        const cuuint64_t dims[3] = {(cuuint64_t)d.nx, (cuuint64_t)d.ny, (cuuint64_t)d.nz};
+        const cuuint64_t strides[2] = {(cuuint64_t)d.nx * 4, (cuuint64_t)d.nx * d.ny * 4};
+        const cuuint32_t box[3] = {(cuuint32_t)kBoxW, (cuuint32_t)kBoxH, (cuuint32_t)nz_box};
+        const cuuint32_t estr[3] = {1, 1, 1};
+        for (int b = 0; b < 2; ++b) {
+            CUresult r = encode(&maps[2 * g + b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
+                                b ? d.q1 : d.q0, dims, strides, box, estr,
+                                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            if (r != CUDA_SUCCESS) {
+                why = "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")";
+                return false;
+            }
+        }
+    }
+    return true;
 }
 
 // ------------------------------------------------------------------ create
@@ -394,16 +444,47 @@ extern "C" lb_status lb_create(const lb_grid_desc *grids, int32_t ngrids, const 
         nzmax = std::max(nzmax, d.nz);
         nzmin = std::min(nzmin, d.nz);
     }
+    const bool staged = ctx->opt.staged_loads && staged_eligible(ctx->grids);
+    bool wide = true;
+    for (int v = 0; v < nvps; ++v) wide = wide && vps[v].w % 16 == 0;
     if (!find_step_kernel(ctx->storage, ctx->compute, nzmax, nzmin, nzmax == nzmin, &ctx->kinfo,
-                          ctx->opt.threads_hint)) {
+                          ctx->opt.threads_hint, staged, wide)) {
         ctx->err = "no kernel variant for these grids";
         return bail(LB_EINVAL);
     }
+    std::vector<CUtensorMap> maps;
+    if (ctx->kinfo.tma_slots > 0) {
+        // the ring and the per-warp sums must fit the shared memory of a CTA
+        int optin = 0;
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
+        const size_t need = 128 + (size_t)ctx->kinfo.tma_slots * ctx->kinfo.tma_slot_bytes +
+                            sizeof(double) * (size_t)(ctx->kinfo.threads / kWarp) * ngrids + 4096;
+        std::string why;
+        if (need > (size_t)optin || !encode_tmaps(ctx->grids, ctx->kinfo.nz_variant, maps, why)) {
+            // register-load kernel instead
+            maps.clear();
+            find_step_kernel(ctx->storage, ctx->compute, nzmax, nzmin, nzmax == nzmin, &ctx->kinfo,
+                             ctx->opt.threads_hint, false, wide);
+        }
+    }
     ctx->threads = ctx->kinfo.threads;
     ctx->dyn_smem = sizeof(double) * (size_t)(ctx->threads / kWarp) * ngrids;
+    if (ctx->kinfo.tma_slots > 0)
+        ctx->dyn_smem += 128 + (size_t)ctx->kinfo.tma_slots * ctx->kinfo.tma_slot_bytes;
     if (ctx->dyn_smem > 48 * 1024) {
-        e = cudaFuncSetAttribute(ctx->kinfo.fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)ctx->dyn_smem);
+        // the limit is per kernel, not per ctx: raise it to the device
+        // maximum so that no ctx lowers it under another one's needs
+        int optin = 0;
+        cudaFuncAttributes fa0;
+        e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
+        if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa0, ctx->kinfo.fn);
+        if (e == cudaSuccess && ctx->dyn_smem + fa0.sharedSizeBytes > (size_t)optin) {
+            ctx->err = "work tables need more shared memory than the device has";
+            return bail(LB_EINVAL);
+        }
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(ctx->kinfo.fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     optin - (int)fa0.sharedSizeBytes);
         if (e != cudaSuccess) {
             ctx->err = std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e);
             return bail(LB_ECUDA);
@@ -537,6 +618,10 @@ extern "C" lb_status lb_create(const lb_grid_desc *grids, int32_t ngrids, const 
     if (e == cudaSuccess) e = dalloc(&ctx->d_pend, 2);
     if (e == cudaSuccess) e = dalloc(&ctx->d_bhist, (size_t)kBalHist * kBalHistCols);
     if (e == cudaSuccess) e = dalloc(&ctx->d_ticket, 1);
+    if (e == cudaSuccess && !maps.empty()) e = dalloc(&ctx->d_tmaps, maps.size());
+    if (e == cudaSuccess && !maps.empty())
+        e = cudaMemcpyAsync(ctx->d_tmaps, maps.data(), sizeof(CUtensorMap) * maps.size(),
+                            cudaMemcpyHostToDevice, ctx->stream);
     const std::vector<int> sp = spatial_order(ctx);
     std::vector<int32_t> sp32(sp.begin(), sp.end()), nch(ctx->vp_nchunks.begin(), ctx->vp_nchunks.end());
     cudaStream_t sm = ctx->stream;
@@ -633,6 +718,7 @@ static lb_status launch(lb_ctx *ctx, int nsteps, const Coef<TC> &coef) {
     p.dclock = ctx->d_clock;
     p.bin_ctr = ctx->d_bin_ctr;
     p.steal = ctx->opt.steal ? 1 : 0;
+    p.tmaps = ctx->d_tmaps;
     p.coef = coef;
 
     CK(cudaMemsetAsync(ctx->d_bar, 0, 2 * sizeof(unsigned), ctx->stream));
@@ -1283,6 +1369,7 @@ extern "C" lb_status lb_get_info(lb_ctx *ctx, lb_info *info) {
     info->regs_per_thread = ctx->regs;
     info->item_w = ctx->kinfo.tile_w ? ctx->kinfo.tile_w : ctx->kinfo.cols_per_item;
     info->item_h = ctx->kinfo.tile_w ? ctx->kinfo.tile_h : 0;
+    info->staged_slots = ctx->kinfo.tma_slots;
     return LB_OK;
 }
 
@@ -1299,9 +1386,9 @@ extern "C" void lb_destroy(lb_ctx *ctx) {
 
 namespace lbk {
 bool find_step_kernel(int storage, int compute, int nz_max, int nz_min, bool same, KernelInfo *out,
-                      int threads_hint) {
+                      int threads_hint, bool staged, bool wide) {
     if (storage == LB_F32 && compute == LB_F32)
-        return kernels_f32(nz_max, nz_min, same, threads_hint, out);
+        return kernels_f32(nz_max, nz_min, same, threads_hint, staged, wide, out);
     if (storage == LB_F64 && compute == LB_F64) return kernels_f64(nz_max, nz_min, same, out);
     if (storage == LB_F64 && compute == LB_F32) return kernels_f64s(nz_max, nz_min, same, out);
     if (storage == LB_BF16 && compute == LB_F32) return kernels_bf16(nz_max, nz_min, same, out);

@@ -13,6 +13,7 @@ constexpr int kNzMax = 128;        // longest register-resident column
 constexpr int kMassHist = 1024;    // global sums kept per grid
 constexpr int kMaxGrids = 512;
 constexpr int kWarp = 32;
+constexpr int kBoxW = 12, kBoxH = 3;   // TMA-staged kernel: box of an 8 x 2 tile
 
 // One grid as the kernel sees it.
 struct GridDev {
@@ -75,6 +76,8 @@ struct StepParams {
     int32_t steal;                 // 1: processors that run out take others' items
     long long *dclock;             // [0] step index, [1] buffer parity: read at start
                                    // instead of t0/parity0, advanced at the end (may be null)
+    const void *tmaps;             // TMA-staged kernels: [ngrids][2] tensor maps of the
+                                   // fields (128 bytes each), else null
     Coef<TC> coef;
 };
 
@@ -90,6 +93,8 @@ struct KernelInfo {
     int tile_w, tile_h; // split kernels: an item is a tile_w x tile_h tile of
                         // the VP (row-major over tiles); 0: runs of
                         // cols_per_item columns in the VP's row-major order
+    int tma_slots;      // TMA-staged kernel: boxes in the shared-memory ring, else 0
+    int tma_slot_bytes; // bytes of one box
 };
 
 // Split kernels' work items: 8 x 2 column tiles.  A compact tile spans less
@@ -103,11 +108,15 @@ inline int items_of_vp(const KernelInfo &k, int w, int h) {
     if (k.tile_w > 0) return ((w + k.tile_w - 1) / k.tile_w) * ((h + k.tile_h - 1) / k.tile_h);
     return (w * h + k.cols_per_item - 1) / k.cols_per_item;
 }
+// staged: allow the TMA-staged kernel (the caller then provides tensor maps);
+// wide: every VP width is a multiple of 16 (paired-warp tiles 16 x 2, else 8 x 4).
 bool find_step_kernel(int storage, int compute, int nz_max, int nz_min, bool all_same_nz,
-                      KernelInfo *out, int threads_hint = 0);
+                      KernelInfo *out, int threads_hint = 0, bool staged = false,
+                      bool wide = false);
 
 // Per-type kernel tables (one translation unit each, compiled in parallel).
-bool kernels_f32(int nz_max, int nz_min, bool same, int threads_hint, KernelInfo *out);
+bool kernels_f32(int nz_max, int nz_min, bool same, int threads_hint, bool staged, bool wide,
+                 KernelInfo *out);
 bool kernels_f64(int nz_max, int nz_min, bool same, KernelInfo *out);
 bool kernels_f64s(int nz_max, int nz_min, bool same, KernelInfo *out);
 bool kernels_bf16(int nz_max, int nz_min, bool same, KernelInfo *out);

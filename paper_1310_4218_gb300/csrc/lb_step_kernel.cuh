@@ -329,6 +329,118 @@ struct PairSum {
     }
 };
 
+// Lane geometry within an 8x2 tile: item = kTileW x kTileH tile of the VP,
+// tiles in row-major order; lane pair (c, c + 16) holds column c of the tile.
+struct SplitGeom {
+    int top;              // 1: upper half of the column
+    int i, j;             // column (clamped to the VP for inactive lanes)
+    int tx0, ty0;         // tile origin in grid coordinates
+    int oc, oi, oj;       // plane offsets of the column and its upwind neighbours
+    int lbase, lstep;     // element offset of local level s: lbase + s * lstep
+    bool active;
+};
+
+template <int NZ>
+__device__ __forceinline__ SplitGeom split_geom(const GridDev &g, const VPDev &vp, int chunk,
+                                                int lane) {
+    constexpr int kCols = kWarp / 2;
+    static_assert(kTileW * kTileH == kCols, "a tile is one column per lane pair");
+    SplitGeom sg;
+    sg.top = lane >> 4;
+    const int c = lane & (kCols - 1);
+    const int tiles_x = (vp.w + kTileW - 1) / kTileW;
+    const int ty = chunk / tiles_x, tx = chunk - ty * tiles_x;
+    const int xi = tx * kTileW + (c % kTileW), yi = ty * kTileH + c / kTileW;
+    sg.active = xi < vp.w && yi < vp.h;
+    sg.tx0 = vp.x0 + tx * kTileW;
+    sg.ty0 = vp.y0 + ty * kTileH;
+    sg.i = vp.x0 + (xi < vp.w ? xi : vp.w - 1);
+    sg.j = vp.y0 + (yi < vp.h ? yi : vp.h - 1);
+    int im = sg.i - g.sx, jm = sg.j - g.sy;
+    im = im < 0 ? im + g.nx : (im >= g.nx ? im - g.nx : im);
+    jm = jm < 0 ? jm + g.ny : (jm >= g.ny ? jm - g.ny : jm);
+    sg.oc = sg.j * g.nx + sg.i;
+    sg.oi = sg.j * g.nx + im;
+    sg.oj = jm * g.nx + sg.i;
+    sg.lbase = sg.top ? (NZ - 1) * g.plane : 0;
+    sg.lstep = sg.top ? -g.plane : g.plane;
+    return sg;
+}
+
+template <int NZ>
+__device__ __forceinline__ int split_kc(const GridDev &g, const SplitGeom &sg, long long t) {
+    int kc = g.kc_disk ? kc_disk(g, sg.i, sg.j, t) : g.kc[sg.oc];
+    if (!sg.active || !g.sweeps_on) kc = 0;
+    return kc;
+}
+
+// Shift, k_c twisted solves, shift back, store and compensated sum: the part
+// of a split item after its advected column is in y2 (levels 2m, 2m+1 of the
+// lane's half in y2[m]).  Returns the column's k_c on the lower lane, 0 on
+// the upper one.
+template <class TS, class TC, int NZ>
+__device__ __forceinline__ int split_finish(const StepParams<TC> &p, const GridDev &g,
+                                            const SplitGeom &sg, float2 (&y2)[NZ / 4], int kc,
+                                            int src, bool do_mass, LaneSum<TC> &acc) {
+    constexpr int H = NZ / 2;
+    constexpr int kCols = kWarp / 2;
+    const int top = sg.top;
+    float *y = reinterpret_cast<float *>(y2);
+    TS *out = static_cast<TS *>(g.q[src ^ 1]);
+
+    // shift by the column's level H-1 value (held by the bottom lane)
+    const float mid = __shfl_xor_sync(0xffffffffu, y[H - 1], kCols);
+    const float cref = kc > 0 ? (top ? mid : y[H - 1]) : 0.f;
+    if (kc > 0) {
+        const float2 nc = f2(-cref, -cref);
+#pragma unroll
+        for (int m = 0; m < H / 2; ++m) y2[m] = add2(y2[m], nc);
+    }
+    const Coef<TC> &cf = p.coef;
+    const int kmax = __reduce_max_sync(0xffffffffu, (unsigned)kc);
+    for (int r = 0; r < kmax; ++r) {
+        const bool act = r < kc;
+        if (act) {
+            float pp = y[0] * cf.m[0];
+            y[0] = pp;
+#pragma unroll
+            for (int s = 1; s < H; ++s) {
+                pp = fmaT(pp, cf.rm[s], y[s] * cf.m[s]);
+                y[s] = pp;
+            }
+        }
+        const float other = __shfl_xor_sync(0xffffffffu, y[H - 1], kCols);
+        if (act) {
+            y[H - 1] = fmaT(cf.ifa, other, y[H - 1]) * cf.ifc;
+#pragma unroll
+            for (int s = H - 2; s >= 0; --s) y[s] = fmaT(cf.rm[s], y[s + 1], y[s]);
+        }
+    }
+
+    if (sg.active) {
+        const float2 c2 = f2(cref, cref);
+        PairSum ps;
+        if (do_mass) ps.begin();
+#pragma unroll
+        for (int m = 0; m < H / 2; ++m) {
+            const float2 x = add2(y2[m], c2);
+            out[sg.lbase + (2 * m) * sg.lstep + sg.oc] = x.x;
+            out[sg.lbase + (2 * m + 1) * sg.lstep + sg.oc] = x.y;
+            if (do_mass) ps.add(x);
+        }
+        if (do_mass) {
+            // fold the two chains into the lane's column sum
+            acc.col_begin();
+            acc.s = ps.s.x;
+            acc.e = ps.e.x;
+            acc.add(ps.s.y);
+            acc.e = __fadd_rn(acc.e, ps.e.y);
+            acc.col_end();
+        }
+    }
+    return top ? 0 : kc;
+}
+
 template <class TS, class TC, int NZ>
 __device__ __forceinline__ int process_item_split(const StepParams<TC> &p, const GridDev &g,
                                                   const VPDev &vp, int chunk, long long t,
@@ -337,31 +449,12 @@ __device__ __forceinline__ int process_item_split(const StepParams<TC> &p, const
     static_assert(sizeof(TS) == 4 && sizeof(TC) == 4, "split kernels are FP32");
     constexpr int H = NZ / 2;
     static_assert(H % 2 == 0, "levels are processed in pairs");
-    constexpr int kCols = kWarp / 2;
-    static_assert(kTileW * kTileH == kCols, "a tile is one column per lane pair");
-    const int top = lane >> 4;
-    // item = kTileW x kTileH tile of the VP, tiles in row-major order; lane
-    // pair (c, c + 16) holds column c of the tile
-    const int c = lane & (kCols - 1);
-    const int tiles_x = (vp.w + kTileW - 1) / kTileW;
-    const int ty = chunk / tiles_x, tx = chunk - ty * tiles_x;
-    const int xi = tx * kTileW + (c % kTileW), yi = ty * kTileH + c / kTileW;
-    const bool active = xi < vp.w && yi < vp.h;
-    const int i = vp.x0 + (xi < vp.w ? xi : vp.w - 1);
-    const int j = vp.y0 + (yi < vp.h ? yi : vp.h - 1);
-    int im = i - g.sx, jm = j - g.sy;
-    im = im < 0 ? im + g.nx : (im >= g.nx ? im - g.nx : im);
-    jm = jm < 0 ? jm + g.ny : (jm >= g.ny ? jm - g.ny : jm);
+    const SplitGeom sg = split_geom<NZ>(g, vp, chunk, lane);
+    const int top = sg.top, lbase = sg.lbase, lstep = sg.lstep;
+    const int oc = sg.oc, oi = sg.oi, oj = sg.oj;
     const int plane = g.plane;
-    const int oc = j * g.nx + i, oi = j * g.nx + im, oj = jm * g.nx + i;
-    // element offset of local level s: (top ? NZ-1-s : s) * plane
-    const int lbase = top ? (NZ - 1) * plane : 0;
-    const int lstep = top ? -plane : plane;
     const TS *in = static_cast<const TS *>(g.q[src]);
-    TS *out = static_cast<TS *>(g.q[src ^ 1]);
-
-    int kc = g.kc_disk ? kc_disk(g, i, j, t) : g.kc[oc];
-    if (!active || !g.sweeps_on) kc = 0;
+    const int kc = split_kc<NZ>(g, sg, t);
 
     float2 y2[H / 2];                  // levels 2m, 2m+1 in one register pair
     float *y = reinterpret_cast<float *>(y2);
@@ -393,58 +486,7 @@ __device__ __forceinline__ int process_item_split(const StepParams<TC> &p, const
             y[s] = v;
         }
     }
-
-    // shift by the column's level H-1 value (held by the bottom lane)
-    const float mid = __shfl_xor_sync(0xffffffffu, y[H - 1], kCols);
-    const float cref = kc > 0 ? (top ? mid : y[H - 1]) : 0.f;
-    if (kc > 0) {
-        const float2 nc = f2(-cref, -cref);
-#pragma unroll
-        for (int m = 0; m < H / 2; ++m) y2[m] = add2(y2[m], nc);
-    }
-    const Coef<TC> &cf = p.coef;
-    const int kmax = __reduce_max_sync(0xffffffffu, (unsigned)kc);
-    for (int r = 0; r < kmax; ++r) {
-        const bool act = r < kc;
-        if (act) {
-            float pp = y[0] * cf.m[0];
-            y[0] = pp;
-#pragma unroll
-            for (int s = 1; s < H; ++s) {
-                pp = fmaT(pp, cf.rm[s], y[s] * cf.m[s]);
-                y[s] = pp;
-            }
-        }
-        const float other = __shfl_xor_sync(0xffffffffu, y[H - 1], kCols);
-        if (act) {
-            y[H - 1] = fmaT(cf.ifa, other, y[H - 1]) * cf.ifc;
-#pragma unroll
-            for (int s = H - 2; s >= 0; --s) y[s] = fmaT(cf.rm[s], y[s + 1], y[s]);
-        }
-    }
-
-    if (active) {
-        const float2 c2 = f2(cref, cref);
-        PairSum ps;
-        if (do_mass) ps.begin();
-#pragma unroll
-        for (int m = 0; m < H / 2; ++m) {
-            const float2 x = add2(y2[m], c2);
-            out[lbase + (2 * m) * lstep + oc] = x.x;
-            out[lbase + (2 * m + 1) * lstep + oc] = x.y;
-            if (do_mass) ps.add(x);
-        }
-        if (do_mass) {
-            // fold the two chains into the lane's column sum
-            acc.col_begin();
-            acc.s = ps.s.x;
-            acc.e = ps.e.x;
-            acc.add(ps.s.y);
-            acc.e = __fadd_rn(acc.e, ps.e.y);
-            acc.col_end();
-        }
-    }
-    return top ? 0 : kc;
+    return split_finish<TS, TC, NZ>(p, g, sg, y2, kc, src, do_mass, acc);
 }
 
 // Split columns for grids of any nz in [2, 2 * HMAX] (several grids of
@@ -709,11 +751,169 @@ __device__ __forceinline__ int pop_with_stealing(const StepParams<TC> &p, int pa
     return -1;
 }
 
+// ------------------------------------------------------------ paired warps
+// Split columns on two warps: a work item is a PW x (32 / PW) tile of 32
+// columns (PW = 16); lane l of the lower warp holds levels 0..H-1 of
+// column l, lane l
+// of the upper warp levels NZ-1..H of the same column (the twisted
+// factorisation of the split kernels, with the halves on two warps instead
+// of two half-warps).  Every load and store instruction of a warp then
+// covers 32 columns of one level where the half-warp split touches two
+// levels, 16 columns each; on the 1024 x 1024 x 96 field the memory-only
+// rate of the load-compute-store pattern is 5.2 TB/s for 16 x 2 tiles
+// against 3.3 TB/s for the half-warp split.  The wider tile idles more
+// lanes at the edges of VPs whose widths are not multiples of 16, so the
+// kernel tables choose it only where VP widths allow.  The middle exchange of each
+// solve and the column's reference value go through shared memory, with a
+// named barrier of the pair's 64 threads.  Both warps hold the same 32
+// columns, so they see the same k_c values and the same sweep count and
+// reach every barrier together.
+struct PairXch {
+    float mid[2][2][kWarp];   // [solve parity][half][lane]: last eliminated value
+    float ref[kWarp];         // the column's level H-1 value (lower warp)
+    int item;                 // work item popped by the lower warp, -1: none
+};
+
+__device__ __forceinline__ void pair_sync(int id) {
+    asm volatile("bar.sync %0, 64;" ::"r"(id) : "memory");
+}
+
+// Returns the column's k_c on the lower warp, 0 on the upper one.
+template <class TS, class TC, int NZ, int PW>
+__device__ __forceinline__ int process_item_pair(const StepParams<TC> &p, const GridDev &g,
+                                                 const VPDev &vp, int chunk, long long t, int src,
+                                                 int lane, int top, int bar_id, PairXch &x,
+                                                 bool do_mass, LaneSum<TC> &acc) {
+    static_assert(sizeof(TS) == 4 && sizeof(TC) == 4, "paired split kernels are FP32");
+    constexpr int H = NZ / 2;
+    static_assert(H % 2 == 0, "levels are processed in pairs");
+    constexpr int PH = kWarp / PW;
+    static_assert(PW * PH == kWarp, "a tile is one column per lane");
+    const int tiles_x = (vp.w + PW - 1) / PW;
+    const int ty = chunk / tiles_x, tx = chunk - ty * tiles_x;
+    const int xi = tx * PW + (lane % PW), yi = ty * PH + lane / PW;
+    const bool active = xi < vp.w && yi < vp.h;
+    const int i = vp.x0 + (xi < vp.w ? xi : vp.w - 1);
+    const int j = vp.y0 + (yi < vp.h ? yi : vp.h - 1);
+    int im = i - g.sx, jm = j - g.sy;
+    im = im < 0 ? im + g.nx : (im >= g.nx ? im - g.nx : im);
+    jm = jm < 0 ? jm + g.ny : (jm >= g.ny ? jm - g.ny : jm);
+    const int plane = g.plane;
+    const int oc = j * g.nx + i, oi = j * g.nx + im, oj = jm * g.nx + i;
+    const int lbase = top ? (NZ - 1) * plane : 0;
+    const int lstep = top ? -plane : plane;
+    const TS *in = static_cast<const TS *>(g.q[src]);
+    TS *out = static_cast<TS *>(g.q[src ^ 1]);
+    int kc = g.kc_disk ? kc_disk(g, i, j, t) : g.kc[oc];
+    if (!active || !g.sweeps_on) kc = 0;
+
+    float2 y2[H / 2];
+    float *y = reinterpret_cast<float *>(y2);
+    const float wx = wgt<float>(g, 1), wy = wgt<float>(g, 2);
+    if (g.xy_only) {
+        const float2 wx2 = f2(wx, wx), wy2 = f2(wy, wy);
+#pragma unroll
+        for (int m = 0; m < H / 2; ++m) {
+            const int off0 = lbase + (2 * m) * lstep, off1 = off0 + lstep;
+            const float2 a = f2(IO<TS, TC>::ld(in + (off0 + oi)), IO<TS, TC>::ld(in + (off1 + oi)));
+            const float2 b = f2(IO<TS, TC>::ld(in + (off0 + oj)), IO<TS, TC>::ld(in + (off1 + oj)));
+            y2[m] = fma2(wy2, b, mul2(wx2, a));
+        }
+    } else {
+        const float w0 = wgt<float>(g, 0), wz = wgt<float>(g, 3);
+        const int sz = g.sz;
+        const int kdown = sz >= 0 ? NZ - 1 : 0;
+#pragma unroll
+        for (int s = 0; s < H; ++s) {
+            const int k = top ? NZ - 1 - s : s;
+            const int off = lbase + s * lstep;
+            float c = IO<TS, TC>::ld(in + (off + oc));
+            float a = IO<TS, TC>::ld(in + (off + oi));
+            float b = IO<TS, TC>::ld(in + (off + oj));
+            float v = fmaT(wy, b, wx * a);
+            v = fmaT(k == kdown ? w0 + wz : w0, c, v);
+            const int ku = k - sz;
+            if (ku >= 0 && ku < NZ) v = fmaT(wz, IO<TS, TC>::ld(in + (ku * plane + oc)), v);
+            y[s] = v;
+        }
+    }
+
+    // shift by the column's level H-1 value (held by the lower warp)
+    if (!top) x.ref[lane] = y[H - 1];
+    pair_sync(bar_id);
+    const float cref = kc > 0 ? x.ref[lane] : 0.f;
+    if (kc > 0) {
+        const float2 nc = f2(-cref, -cref);
+#pragma unroll
+        for (int m = 0; m < H / 2; ++m) y2[m] = add2(y2[m], nc);
+    }
+    const Coef<TC> &cf = p.coef;
+    const int kmax = __reduce_max_sync(0xffffffffu, (unsigned)kc);
+    for (int r = 0; r < kmax; ++r) {
+        const bool act = r < kc;
+        if (act) {
+            float pp = y[0] * cf.m[0];
+            y[0] = pp;
+#pragma unroll
+            for (int s = 1; s < H; ++s) {
+                pp = fmaT(pp, cf.rm[s], y[s] * cf.m[s]);
+                y[s] = pp;
+            }
+        }
+        x.mid[r & 1][top][lane] = y[H - 1];
+        pair_sync(bar_id);
+        const float other = x.mid[r & 1][top ^ 1][lane];
+        if (act) {
+            y[H - 1] = fmaT(cf.ifa, other, y[H - 1]) * cf.ifc;
+#pragma unroll
+            for (int s = H - 2; s >= 0; --s) y[s] = fmaT(cf.rm[s], y[s + 1], y[s]);
+        }
+    }
+
+    if (active) {
+        const float2 c2 = f2(cref, cref);
+        PairSum ps;
+        if (do_mass) ps.begin();
+#pragma unroll
+        for (int m = 0; m < H / 2; ++m) {
+            const float2 v = add2(y2[m], c2);
+            out[lbase + (2 * m) * lstep + oc] = v.x;
+            out[lbase + (2 * m + 1) * lstep + oc] = v.y;
+            if (do_mass) ps.add(v);
+        }
+        if (do_mass) {
+            acc.col_begin();
+            acc.s = ps.s.x;
+            acc.e = ps.e.x;
+            acc.add(ps.s.y);
+            acc.e = __fadd_rn(acc.e, ps.e.y);
+            acc.col_end();
+        }
+    }
+    return top ? 0 : kc;
+}
+
+// Next work item of a warp (processor tables, stealing or atomic queue),
+// -1 when none is left this step.
+template <class TC>
+__device__ __forceinline__ int pop_item(const StepParams<TC> &p, int s, int bin, int lane, int *s_ctr,
+                                        int ibeg, int iend) {
+    if (p.steal && !p.queue_mode) return pop_with_stealing(p, s & 1, bin, lane);
+    int c = 0;
+    if (lane == 0) c = p.queue_mode ? (int)atomicAdd(&p.qhead[s & 1], 1u) : atomicAdd(s_ctr, 1);
+    c = __shfl_sync(0xffffffffu, c, 0) + ibeg;
+    return c < iend ? c : -1;
+}
+
 // ------------------------------------------------------------ the kernel
-template <class TS, class TC, int NZ, bool EXACT, int NZLO, int THREADS, bool SPLIT>
+template <class TS, class TC, int NZ, bool EXACT, int NZLO, int THREADS, bool SPLIT, int PAIRW>
 __global__ void __launch_bounds__(THREADS, 1)
 lb_step_kernel(const __grid_constant__ StepParams<TC> p) {
+    constexpr bool PAIR = PAIRW > 0;
+    static_assert(!PAIR || (SPLIT && EXACT && THREADS % 64 == 0 && THREADS / 64 <= 15),
+                  "paired warps: exact split columns, at most 15 pairs (named barriers 1..15)");
     extern __shared__ double s_mass[];          // [warps][ngrids]
+    __shared__ PairXch s_pair[PAIR ? THREADS / 64 : 1];
     __shared__ int s_ctr;
     __shared__ int s_flag;
     __shared__ unsigned long long s_t0, s_tend;
@@ -756,7 +956,42 @@ lb_step_kernel(const __grid_constant__ StepParams<TC> p) {
 
         LaneSum<TC> acc;
         int cur_grid = -1;
-        for (;;) {
+        if constexpr (PAIR) {
+            // the lower warp of each pair pops; both process the item
+            const int top = warp & 1, bar_id = 1 + (warp >> 1);
+            PairXch &x = s_pair[warp >> 1];
+            for (;;) {
+                if (!top) {
+                    const int c = pop_item(p, s, bin, lane, &s_ctr, ibeg, iend);
+                    if (lane == 0) x.item = c;
+                }
+                pair_sync(bar_id);
+                const int c = x.item;
+                if (c < 0) break;
+                const int2 it = p.items[c];
+                const VPDev vp = p.vps[it.x];
+                const GridDev &g = p.grids[vp.grid];
+                if (do_mass && vp.grid != cur_grid) {
+                    if (cur_grid >= 0) {
+                        double v = acc.take();
+#pragma unroll
+                        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                        if (lane == 0) s_mass[warp * p.ngrids + cur_grid] += v;
+                    }
+                    cur_grid = vp.grid;
+                }
+                const long long c0 = clock64();
+                const int kc = process_item_pair<TS, TC, NZ, (PAIR ? PAIRW : 16)>(
+                    p, g, vp, it.y, t, src, lane, top, bar_id, x, do_mass, acc);
+                __syncwarp();
+                const long long c1 = clock64();
+                const unsigned ksum = __reduce_add_sync(0xffffffffu, (unsigned)kc);
+                if (lane == 0 && !top) {
+                    atomicAdd(&p.vp_cycles[it.x], (unsigned long long)(c1 - c0));
+                    if (p.sweeps) atomicAdd(p.sweeps, (unsigned long long)ksum * (unsigned)g.nz);
+                }
+            }
+        } else for (;;) {
             int c = 0;
             if (p.steal && !p.queue_mode) {
                 c = pop_with_stealing(p, s & 1, bin, lane);
@@ -843,18 +1078,22 @@ lb_step_kernel(const __grid_constant__ StepParams<TC> p) {
     }
 }
 
-template <class TS, class TC, int NZ, bool EXACT, int NZLO, int THREADS, bool SPLIT = false>
+template <class TS, class TC, int NZ, bool EXACT, int NZLO, int THREADS, bool SPLIT = false,
+          int PAIRW = 0>
 inline KernelInfo kernel_entry() {
     static_assert(!SPLIT || NZ % 4 == 0, "split kernels hold nz/2 levels in register pairs");
+    constexpr bool PAIR = PAIRW > 0;
     KernelInfo k;
-    k.fn = (const void *)&lb_step_kernel<TS, TC, NZ, EXACT, NZLO, THREADS, SPLIT>;
+    k.fn = (const void *)&lb_step_kernel<TS, TC, NZ, EXACT, NZLO, THREADS, SPLIT, PAIRW>;
     k.threads = THREADS;
     k.nz_variant = NZ;
     k.exact = EXACT ? 1 : 0;
     k.split = SPLIT ? 1 : 0;
-    k.cols_per_item = SPLIT ? kWarp / 2 : kWarp;
-    k.tile_w = SPLIT ? kTileW : 0;
-    k.tile_h = SPLIT ? kTileH : 0;
+    k.cols_per_item = (SPLIT && !PAIR) ? kWarp / 2 : kWarp;
+    k.tile_w = PAIR ? PAIRW : (SPLIT ? kTileW : 0);
+    k.tile_h = PAIR ? kWarp / PAIRW : (SPLIT ? kTileH : 0);
+    k.tma_slots = 0;
+    k.tma_slot_bytes = 0;
     return k;
 }
 

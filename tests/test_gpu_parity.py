@@ -62,6 +62,73 @@ def test_variant_parity(storage, compute, nz):
     assert err <= tolerance(g, n), err
 
 
+# Kernels of FP32 grids with nz 32, 64 or 96 (lb_options.threads_hint,
+# staged_loads): by default split columns on paired warps (16 x 2 tiles)
+# when every VP width is a multiple of 16 ("wide"), else on half-warps
+# (8 x 2 tiles, "narrow"); forced paired warps on narrow VPs; forced
+# half-warps; TMA-staged; one lane per column.
+EXACT_KERNELS = {"narrow": {}, "wide": {}, "pair": {"threads_hint": 3},
+                 "half": {"threads_hint": 2}, "staged": {"staged_loads": 1},
+                 "one_lane": {"threads_hint": 1}}
+
+
+def _check_kernel_shape(info, kernel):
+    if kernel in ("wide", "pair"):
+        assert (info.item_w, info.item_h, info.staged_slots) == (16, 2, 0)
+    elif kernel in ("narrow", "half"):
+        assert (info.item_w, info.item_h, info.staged_slots) == (8, 2, 0)
+    elif kernel == "staged":
+        assert (info.item_w, info.item_h) == (8, 2) and info.staged_slots > 0
+    else:
+        assert info.item_h == 0 and info.staged_slots == 0
+
+
+@pytest.mark.parametrize("nz", [32, 64, 96])
+@pytest.mark.parametrize("kernel", list(EXACT_KERNELS))
+def test_exact_nz_kernels(nz, kernel):
+    """Every kernel of the exact-nz grids matches the oracle: VPs leave
+    ragged tiles in x and y, tiles wrap at both periodic boundaries, and
+    the steps run from processor tables, with stealing after a measured
+    rebalance, and from the queue."""
+    nx = 64 if kernel == "wide" else 52
+    g = Grid(nx, 38, nz, 0.5, 0.5, 0.0, 0.1, "f32", "f32", True, (40, 30, 1, 1, 9), 7, 1)
+    q = round_to_storage(gaussian_blob(nx, 38, nz, (26, 19, nz / 2), 9.0, 1e-3, 3), "f32")
+    # widths 20, 20, 12 (ragged 8 x 4 and 8 x 2 tiles) or 16 (wide tiles);
+    # heights 12, 12, 12, 2 (ragged rows)
+    vps = regular_blocks(nx, 38, 16 if kernel == "wide" else 20, 12)
+    ref, _ = oracle_run(g, q, 6)
+    for extra, strategy in (({}, None), ({"steal": 1}, "greedy_blocked"), ({}, "queue")):
+        sim = make_sim([g], [q], vps, **EXACT_KERNELS[kernel], **extra)
+        _check_kernel_shape(sim.info(), kernel)
+        sim.step(2)
+        if strategy:
+            sim.measure()
+            sim.rebalance(strategy)
+        sim.step(4)
+        out = sim.field(0)
+        sim.close()
+        assert normwise(out, ref) <= tolerance(g, 6), (extra, strategy)
+
+
+@pytest.mark.parametrize("kernel", ["narrow", "wide", "pair", "staged"])
+@pytest.mark.parametrize("cx,cy,cz", [(-0.4, 0.25, -0.3), (0.2, -0.5, 0.0), (-0.3, -0.3, 0.2)])
+def test_exact_nz_kernels_general_advection(kernel, cx, cy, cz):
+    """Either upwind side on every axis, and vertical advection, on the
+    exact-nz kernels (for the TMA-staged kernel the box origin follows the
+    upwind side)."""
+    nx = 48 if kernel == "wide" else 44
+    g = Grid(nx, 36, 32, cx, cy, cz, 0.25, "f32", "f32", True, (5, 30, -1, 2, 7), 5, 2)
+    q = round_to_storage(random_field(g, 4), "f32")
+    vps = regular_blocks(nx, 36, 16 if kernel == "wide" else 12, 10)
+    sim = make_sim([g], [q], vps, **EXACT_KERNELS[kernel])
+    _check_kernel_shape(sim.info(), kernel)
+    sim.step(6)
+    out = sim.field(0)
+    sim.close()
+    ref, _ = oracle_run(g, q, 6)
+    assert normwise(out, ref) <= 1e-5
+
+
 @pytest.mark.parametrize("cx,cy,cz", [(0.3, 0.2, 0.1), (-0.4, 0.25, -0.3), (0.2, -0.5, 0.0),
                                       (-0.1, -0.1, 0.6)])
 def test_general_advection(cx, cy, cz):
