@@ -22,7 +22,11 @@ Strategy names: an lb_strategy name, optionally followed by "+steal"
 (end-of-step work stealing), "+dev" (device balancer), "+pred" (cost
 rescale at k_c re-draws, with +dev), "+thr" (keep a table within the
 1.15 threshold, with +dev) and "+graph" (each period one CUDA graph
-replay: steps, device measurement, device rebalance; with +dev).
+replay: steps, device measurement, device rebalance; with +dev); kernel
+choices "+pair" (split columns on paired warps), "+half" (on half-warps),
+"+tma" (TMA-staged) and "+one" (one lane per column) override the
+default, which takes paired warps where every VP width is a multiple of
+16 and half-warps otherwise.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--workload NAME] [--period P] [--strategy auto|static|queue|...]
@@ -271,6 +275,7 @@ class StrategyRun:
         staged = "tma" in flags
         half = "half" in flags
         pair = "pair" in flags
+        one = "one" in flags          # "+one": one lane per column
         # "+pred": at a k_c re-draw the new array is installed before the
         # balancer runs and the costs are rescaled by the fitted model
         self.predict = "pred" in flags and self.dev_mode
@@ -293,6 +298,8 @@ class StrategyRun:
             opt.threads_hint = 2
         if pair:
             opt.threads_hint = 3
+        if one:
+            opt.threads_hint = 1
         kc0 = [epochs[0][gi] for gi in range(len(w.grids))] if epochs else None
         self.sim = Simulation(w.grids, fields, w.vps, kc_arrays=kc0, options=opt, device=dev,
                               stream=stream)
