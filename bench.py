@@ -24,9 +24,10 @@ rescale at k_c re-draws, with +dev), "+thr" (keep a table within the
 1.15 threshold, with +dev) and "+graph" (each period one CUDA graph
 replay: steps, device measurement, device rebalance; with +dev); kernel
 choices "+pair" (split columns on paired warps), "+half" (on half-warps),
-"+tma" (TMA-staged) and "+one" (one lane per column) override the
-default, which takes paired warps where every VP width is a multiple of
-16 and half-warps otherwise.
+"+twin" (one lane per column, packed twisted halves), "+tma" (TMA-staged)
+and "+one" (one lane per column, plain Thomas) override the default, which
+takes twin halves where every VP width is a multiple of 16 and half-warps
+otherwise.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--workload NAME] [--period P] [--strategy auto|static|queue|...]
@@ -270,12 +271,14 @@ class StrategyRun:
         strategy, flags = parts[0], set(parts[1:])
         steal = "steal" in flags
         self.dev_mode = "dev" in flags
-        # "+tma": the TMA-staged kernel; "+half" / "+pair": split columns on
-        # half-warps / paired warps (default: paired where VP widths allow)
+        # kernel choice (default: twin halves where VP widths allow, else
+        # half-warps): "+tma" TMA-staged, "+half" / "+pair" split columns on
+        # half-warps / paired warps
         staged = "tma" in flags
         half = "half" in flags
         pair = "pair" in flags
         one = "one" in flags          # "+one": one lane per column
+        twin = "twin" in flags        # "+twin": one lane per column, packed halves
         # "+pred": at a k_c re-draw the new array is installed before the
         # balancer runs and the costs are rescaled by the fitted model
         self.predict = "pred" in flags and self.dev_mode
@@ -300,6 +303,8 @@ class StrategyRun:
             opt.threads_hint = 3
         if one:
             opt.threads_hint = 1
+        if twin:
+            opt.threads_hint = 4
         kc0 = [epochs[0][gi] for gi in range(len(w.grids))] if epochs else None
         self.sim = Simulation(w.grids, fields, w.vps, kc_arrays=kc0, options=opt, device=dev,
                               stream=stream)
@@ -544,6 +549,7 @@ def main():
                                "greedy_blocked+steal+dev+pred",
                                "greedy_blocked+steal+dev+pred+thr+graph",
                                "greedy_blocked+steal+dev+pred+thr+pair",
+                               "greedy_blocked+steal+dev+pred+thr+twin",
                                "greedy_blocked+steal+dev+pred+thr+tma", "queue", "queue+dev")
                    if x != args.strategy]:
             r2 = StrategyRun(w, fields, epochs, kc_dev, args, dev, stream, st)

@@ -142,13 +142,15 @@ typedef struct {
     double refine_tol;            /* RefineSwapLB tolerance (default 0.05) */
     int64_t barrier_timeout_ns;   /* grid-barrier wait limit (default 2 s) */
     int32_t threads_hint;         /* kernel variant for FP32 grids: 0 default
-                                     (split columns; for nz 32, 64, 96 on
-                                     paired warps with 16 x 2 tiles when
-                                     every VP width is a multiple of 16,
-                                     else on half-warps with 8 x 2 tiles),
-                                     1 one lane per column, 2 split columns
-                                     on half-warps, 3 split columns on
-                                     paired warps (nz 32, 64, 96) */
+                                     (nz 32, 64, 96: one lane per column with
+                                     packed twisted halves when every VP
+                                     width is a multiple of 16 and r lets
+                                     the FP32 pivots converge, else split
+                                     columns on half-warps; other nz: split
+                                     columns), 1 one lane per column, 2 split
+                                     columns on half-warps, 3 split columns
+                                     on paired warps, 4 packed twisted
+                                     halves (nz 32, 64, 96) */
     int32_t steal;                /* 1: with processor tables, a processor
                                      that finishes its VPs takes the next
                                      work items of the processor with the

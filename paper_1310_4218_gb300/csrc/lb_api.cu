@@ -447,8 +447,20 @@ extern "C" lb_status lb_create(const lb_grid_desc *grids, int32_t ngrids, const 
     const bool staged = ctx->opt.staged_loads && staged_eligible(ctx->grids);
     bool wide = true;
     for (int v = 0; v < nvps; ++v) wide = wide && vps[v].w % 16 == 0;
+    // twin kernels: the FP32 pivots of a zero-flux end must be one constant
+    // pair from level kTwinS0 up to the middle
+    bool twin_ok = false;
+    {
+        double mt[kNzMax];
+        pivots(grids[0].r, 0, mt);
+        const int h = nzmax / 2;
+        twin_ok = nzmax == nzmin && h > kTwinS0;
+        for (int k = kTwinS0; twin_ok && k < h; ++k)
+            twin_ok = (float)mt[k] == (float)mt[kTwinS0] &&
+                      (float)(grids[0].r * mt[k]) == (float)(grids[0].r * mt[kTwinS0]);
+    }
     if (!find_step_kernel(ctx->storage, ctx->compute, nzmax, nzmin, nzmax == nzmin, &ctx->kinfo,
-                          ctx->opt.threads_hint, staged, wide)) {
+                          ctx->opt.threads_hint, staged, wide, twin_ok)) {
         ctx->err = "no kernel variant for these grids";
         return bail(LB_EINVAL);
     }
@@ -464,7 +476,7 @@ extern "C" lb_status lb_create(const lb_grid_desc *grids, int32_t ngrids, const 
             // register-load kernel instead
             maps.clear();
             find_step_kernel(ctx->storage, ctx->compute, nzmax, nzmin, nzmax == nzmin, &ctx->kinfo,
-                             ctx->opt.threads_hint, false, wide);
+                             ctx->opt.threads_hint, false, wide, twin_ok);
         }
     }
     ctx->threads = ctx->kinfo.threads;
@@ -1386,9 +1398,9 @@ extern "C" void lb_destroy(lb_ctx *ctx) {
 
 namespace lbk {
 bool find_step_kernel(int storage, int compute, int nz_max, int nz_min, bool same, KernelInfo *out,
-                      int threads_hint, bool staged, bool wide) {
+                      int threads_hint, bool staged, bool wide, bool twin_ok) {
     if (storage == LB_F32 && compute == LB_F32)
-        return kernels_f32(nz_max, nz_min, same, threads_hint, staged, wide, out);
+        return kernels_f32(nz_max, nz_min, same, threads_hint, staged, wide, twin_ok, out);
     if (storage == LB_F64 && compute == LB_F64) return kernels_f64(nz_max, nz_min, same, out);
     if (storage == LB_F64 && compute == LB_F32) return kernels_f64s(nz_max, nz_min, same, out);
     if (storage == LB_BF16 && compute == LB_F32) return kernels_bf16(nz_max, nz_min, same, out);

@@ -14,6 +14,10 @@ constexpr int kMassHist = 1024;    // global sums kept per grid
 constexpr int kMaxGrids = 512;
 constexpr int kWarp = 32;
 constexpr int kBoxW = 12, kBoxH = 3;   // TMA-staged kernel: box of an 8 x 2 tile
+// Twin kernels: level from which the FP32 pivots m_s and r m_s of a zero-flux
+// end must be one constant pair (checked by the host for every ctx that
+// selects them).
+constexpr int kTwinS0 = 8;
 
 // One grid as the kernel sees it.
 struct GridDev {
@@ -93,6 +97,8 @@ struct KernelInfo {
     int tile_w, tile_h; // split kernels: an item is a tile_w x tile_h tile of
                         // the VP (row-major over tiles); 0: runs of
                         // cols_per_item columns in the VP's row-major order
+    int twin_s0;        // twin kernels: level from which the FP32 pivots must be one
+                        // constant pair, else 0
     int tma_slots;      // TMA-staged kernel: boxes in the shared-memory ring, else 0
     int tma_slot_bytes; // bytes of one box
 };
@@ -109,14 +115,16 @@ inline int items_of_vp(const KernelInfo &k, int w, int h) {
     return (w * h + k.cols_per_item - 1) / k.cols_per_item;
 }
 // staged: allow the TMA-staged kernel (the caller then provides tensor maps);
-// wide: every VP width is a multiple of 16 (paired-warp tiles 16 x 2, else 8 x 4).
+// wide: every VP width is a multiple of 16 (paired-warp kernels apply);
+// twin_ok: the FP32 pivots are one constant pair from level kTwinS0 on (twin
+// kernels apply).
 bool find_step_kernel(int storage, int compute, int nz_max, int nz_min, bool all_same_nz,
                       KernelInfo *out, int threads_hint = 0, bool staged = false,
-                      bool wide = false);
+                      bool wide = false, bool twin_ok = false);
 
 // Per-type kernel tables (one translation unit each, compiled in parallel).
 bool kernels_f32(int nz_max, int nz_min, bool same, int threads_hint, bool staged, bool wide,
-                 KernelInfo *out);
+                 bool twin_ok, KernelInfo *out);
 bool kernels_f64(int nz_max, int nz_min, bool same, KernelInfo *out);
 bool kernels_f64s(int nz_max, int nz_min, bool same, KernelInfo *out);
 bool kernels_bf16(int nz_max, int nz_min, bool same, KernelInfo *out);

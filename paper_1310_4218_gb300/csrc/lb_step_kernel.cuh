@@ -751,6 +751,118 @@ __device__ __forceinline__ int pop_with_stealing(const StepParams<TC> &p, int pa
     return -1;
 }
 
+// ------------------------------------------------------------ twin halves
+// One lane per column with the twisted factorisation of the split kernels
+// inside the lane: y2[s] holds (level s, level NZ-1-s), so both halves'
+// eliminations, the middle 2x2 system and both back substitutions run as
+// one chain of packed FP32x2 operations -- the same operations, in the same
+// order, as the split kernels, on half the instructions, without a shuffle.
+// A warp's load and store instructions cover 32 columns of one level (runs
+// of 32 columns in the VP's row-major order).  A packed operation needs its
+// coefficient pair in registers; the pivots m_s, r m_s of a zero-flux end
+// converge, and from level S0 on their FP32 values are one constant pair
+// (the host selects this kernel only when that holds), so levels below S0
+// use scalar operations on the per-level constants and the rest four
+// registers.
+template <class TS, class TC, int NZ, int S0>
+__device__ __forceinline__ int process_item_twin(const StepParams<TC> &p, const GridDev &g,
+                                                 const VPDev &vp, int chunk, long long t, int src,
+                                                 int lane, bool do_mass, LaneSum<TC> &acc) {
+    static_assert(sizeof(TS) == 4 && sizeof(TC) == 4, "twin kernels are FP32");
+    constexpr int H = NZ / 2;
+    static_assert(S0 >= 1 && S0 < H, "converged pivots from level S0");
+    const ColGeom cg = col_geom(g, vp, chunk, lane);
+    const int plane = g.plane;
+    const TS *in = static_cast<const TS *>(g.q[src]);
+    TS *out = static_cast<TS *>(g.q[src ^ 1]);
+    int kc = g.kc_disk ? kc_disk(g, cg.i, cg.j, t) : g.kc[cg.oc];
+    if (!cg.active || !g.sweeps_on) kc = 0;
+
+    float2 y2[H];                      // (level s, level NZ-1-s)
+    const float wx = wgt<float>(g, 1), wy = wgt<float>(g, 2);
+    if (g.xy_only) {
+        const float2 wx2 = f2(wx, wx), wy2 = f2(wy, wy);
+#pragma unroll
+        for (int s = 0; s < H; ++s) {
+            const int lo = s * plane, hi = (NZ - 1 - s) * plane;
+            const float2 a = f2(IO<TS, TC>::ld(in + (lo + cg.oi)), IO<TS, TC>::ld(in + (hi + cg.oi)));
+            const float2 b = f2(IO<TS, TC>::ld(in + (lo + cg.oj)), IO<TS, TC>::ld(in + (hi + cg.oj)));
+            y2[s] = fma2(wy2, b, mul2(wx2, a));
+        }
+    } else {
+        const float w0 = wgt<float>(g, 0), wz = wgt<float>(g, 3);
+        const int sz = g.sz;
+        const int kdown = sz >= 0 ? NZ - 1 : 0;
+        auto level = [&](int k) {
+            float v = fmaT(wy, IO<TS, TC>::ld(in + (k * plane + cg.oj)),
+                           wx * IO<TS, TC>::ld(in + (k * plane + cg.oi)));
+            v = fmaT(k == kdown ? w0 + wz : w0, IO<TS, TC>::ld(in + (k * plane + cg.oc)), v);
+            const int ku = k - sz;
+            if (ku >= 0 && ku < NZ) v = fmaT(wz, IO<TS, TC>::ld(in + (ku * plane + cg.oc)), v);
+            return v;
+        };
+#pragma unroll
+        for (int s = 0; s < H; ++s) y2[s] = f2(level(s), level(NZ - 1 - s));
+    }
+
+    // shift by the column's level H-1 value
+    const float cref = kc > 0 ? y2[H - 1].x : 0.f;
+    if (kc > 0) {
+        const float2 nc = f2(-cref, -cref);
+#pragma unroll
+        for (int s = 0; s < H; ++s) y2[s] = add2(y2[s], nc);
+    }
+    const Coef<TC> &cf = p.coef;
+    const float2 minf = f2(cf.m[S0], cf.m[S0]), rminf = f2(cf.rm[S0], cf.rm[S0]);
+    for (int r = 0; r < kc; ++r) {
+        // both halves eliminate toward the middle
+        float2 pp = f2(y2[0].x * cf.m[0], y2[0].y * cf.m[0]);
+        y2[0] = pp;
+#pragma unroll
+        for (int s = 1; s < H; ++s) {
+            if (s < S0) {
+                pp = f2(fmaT(pp.x, cf.rm[s], y2[s].x * cf.m[s]),
+                        fmaT(pp.y, cf.rm[s], y2[s].y * cf.m[s]));
+            } else {
+                pp = fma2(pp, rminf, mul2(y2[s], minf));
+            }
+            y2[s] = pp;
+        }
+        // middle: x_own = (p + a p_other) / (1 - a^2)
+        y2[H - 1] = f2(fmaT(cf.ifa, pp.y, pp.x) * cf.ifc, fmaT(cf.ifa, pp.x, pp.y) * cf.ifc);
+        // both back substitutions outward
+#pragma unroll
+        for (int s = H - 2; s >= 0; --s) {
+            if (s < S0)
+                y2[s] = f2(fmaT(cf.rm[s], y2[s + 1].x, y2[s].x), fmaT(cf.rm[s], y2[s + 1].y, y2[s].y));
+            else
+                y2[s] = fma2(rminf, y2[s + 1], y2[s]);
+        }
+    }
+
+    if (cg.active) {
+        const float2 c2 = f2(cref, cref);
+        PairSum ps;
+        if (do_mass) ps.begin();
+#pragma unroll
+        for (int s = 0; s < H; ++s) {
+            const float2 v = add2(y2[s], c2);
+            out[s * plane + cg.oc] = v.x;
+            out[(NZ - 1 - s) * plane + cg.oc] = v.y;
+            if (do_mass) ps.add(v);
+        }
+        if (do_mass) {
+            acc.col_begin();
+            acc.s = ps.s.x;
+            acc.e = ps.e.x;
+            acc.add(ps.s.y);
+            acc.e = __fadd_rn(acc.e, ps.e.y);
+            acc.col_end();
+        }
+    }
+    return kc;
+}
+
 // ------------------------------------------------------------ paired warps
 // Split columns on two warps: a work item is a PW x (32 / PW) tile of 32
 // columns (PW = 16); lane l of the lower warp holds levels 0..H-1 of
@@ -906,10 +1018,12 @@ __device__ __forceinline__ int pop_item(const StepParams<TC> &p, int s, int bin,
 }
 
 // ------------------------------------------------------------ the kernel
-template <class TS, class TC, int NZ, bool EXACT, int NZLO, int THREADS, bool SPLIT, int PAIRW>
+template <class TS, class TC, int NZ, bool EXACT, int NZLO, int THREADS, bool SPLIT, int PAIRW,
+          bool TWIN>
 __global__ void __launch_bounds__(THREADS, 1)
 lb_step_kernel(const __grid_constant__ StepParams<TC> p) {
     constexpr bool PAIR = PAIRW > 0;
+    static_assert(!TWIN || (EXACT && !SPLIT && !PAIR), "twin kernels: exact nz, one lane per column");
     static_assert(!PAIR || (SPLIT && EXACT && THREADS % 64 == 0 && THREADS / 64 <= 15),
                   "paired warps: exact split columns, at most 15 pairs (named barriers 1..15)");
     extern __shared__ double s_mass[];          // [warps][ngrids]
@@ -1016,7 +1130,10 @@ lb_step_kernel(const __grid_constant__ StepParams<TC> p) {
             }
             long long c0 = clock64();
             int kc;
-            if constexpr (SPLIT && EXACT)
+            if constexpr (TWIN)
+                kc = process_item_twin<TS, TC, NZ, kTwinS0>(p, g, vp, it.y, t, src, lane, do_mass,
+                                                            acc);
+            else if constexpr (SPLIT && EXACT)
                 kc = process_item_split<TS, TC, NZ>(p, g, vp, it.y, t, src, lane, do_mass, acc);
             else if constexpr (SPLIT) {
                 // per item (one grid, warp-uniform): the smallest half-length
@@ -1079,16 +1196,18 @@ lb_step_kernel(const __grid_constant__ StepParams<TC> p) {
 }
 
 template <class TS, class TC, int NZ, bool EXACT, int NZLO, int THREADS, bool SPLIT = false,
-          int PAIRW = 0>
+          int PAIRW = 0, bool TWIN = false>
 inline KernelInfo kernel_entry() {
     static_assert(!SPLIT || NZ % 4 == 0, "split kernels hold nz/2 levels in register pairs");
     constexpr bool PAIR = PAIRW > 0;
     KernelInfo k;
-    k.fn = (const void *)&lb_step_kernel<TS, TC, NZ, EXACT, NZLO, THREADS, SPLIT, PAIRW>;
+    k.fn = (const void *)&lb_step_kernel<TS, TC, NZ, EXACT, NZLO, THREADS, SPLIT, PAIRW, TWIN>;
     k.threads = THREADS;
     k.nz_variant = NZ;
     k.exact = EXACT ? 1 : 0;
-    k.split = SPLIT ? 1 : 0;
+    // twin kernels use the split kernels' coefficient tables
+    k.split = (SPLIT || TWIN) ? 1 : 0;
+    k.twin_s0 = TWIN ? kTwinS0 : 0;
     k.cols_per_item = (SPLIT && !PAIR) ? kWarp / 2 : kWarp;
     k.tile_w = PAIR ? PAIRW : (SPLIT ? kTileW : 0);
     k.tile_h = PAIR ? kWarp / PAIRW : (SPLIT ? kTileH : 0);

@@ -63,24 +63,25 @@ def test_variant_parity(storage, compute, nz):
 
 
 # Kernels of FP32 grids with nz 32, 64 or 96 (lb_options.threads_hint,
-# staged_loads): by default split columns on paired warps (16 x 2 tiles)
-# when every VP width is a multiple of 16 ("wide"), else on half-warps
-# (8 x 2 tiles, "narrow"); forced paired warps on narrow VPs; forced
-# half-warps; TMA-staged; one lane per column.
+# staged_loads): by default one lane per column with packed twisted halves
+# when every VP width is a multiple of 16 ("wide"), else split columns on
+# half-warps (8 x 2 tiles, "narrow"); forced paired warps; forced
+# half-warps; TMA-staged; one lane per column (plain Thomas); forced twin
+# halves on narrow VPs.
 EXACT_KERNELS = {"narrow": {}, "wide": {}, "pair": {"threads_hint": 3},
                  "half": {"threads_hint": 2}, "staged": {"staged_loads": 1},
-                 "one_lane": {"threads_hint": 1}}
+                 "one_lane": {"threads_hint": 1}, "twin": {"threads_hint": 4}}
 
 
 def _check_kernel_shape(info, kernel):
-    if kernel in ("wide", "pair"):
+    if kernel == "pair":
         assert (info.item_w, info.item_h, info.staged_slots) == (16, 2, 0)
     elif kernel in ("narrow", "half"):
         assert (info.item_w, info.item_h, info.staged_slots) == (8, 2, 0)
     elif kernel == "staged":
         assert (info.item_w, info.item_h) == (8, 2) and info.staged_slots > 0
-    else:
-        assert info.item_h == 0 and info.staged_slots == 0
+    else:                                        # runs of 32 columns
+        assert (info.item_w, info.item_h, info.staged_slots) == (32, 0, 0)
 
 
 @pytest.mark.parametrize("nz", [32, 64, 96])
@@ -110,7 +111,24 @@ def test_exact_nz_kernels(nz, kernel):
         assert normwise(out, ref) <= tolerance(g, 6), (extra, strategy)
 
 
-@pytest.mark.parametrize("kernel", ["narrow", "wide", "pair", "staged"])
+def test_twin_kernel_needs_converged_pivots():
+    """Wide VPs take the twin kernel only when the FP32 pivots are one
+    constant pair from a fixed level on; with r = 5 they are not, and the
+    half-warp kernel runs instead (same results)."""
+    for r, shape in ((0.1, (32, 0)), (5.0, (8, 2))):
+        g = Grid(64, 32, 32, 0.5, 0.5, 0.0, r, "f32", "f32", True, (20, 10, 1, 1, 9), 6, 1)
+        q = round_to_storage(gaussian_blob(64, 32, 32, (30, 15, 16), 8.0, 1e-3, 3), "f32")
+        sim = make_sim([g], [q], regular_blocks(64, 32, 16, 16))
+        info = sim.info()
+        assert (info.item_w, info.item_h) == shape, r
+        sim.step(4)
+        out = sim.field(0)
+        sim.close()
+        ref, _ = oracle_run(g, q, 4)
+        assert normwise(out, ref) <= 1e-5, r
+
+
+@pytest.mark.parametrize("kernel", ["narrow", "wide", "pair", "staged", "twin"])
 @pytest.mark.parametrize("cx,cy,cz", [(-0.4, 0.25, -0.3), (0.2, -0.5, 0.0), (-0.3, -0.3, 0.2)])
 def test_exact_nz_kernels_general_advection(kernel, cx, cy, cz):
     """Either upwind side on every axis, and vertical advection, on the
