@@ -6,8 +6,10 @@ Knobs:
                least 2*min_side columns per side into quadrants (finer
                over-decomposition, Sec. III: more, smaller VPs balance better
                but add halo traffic)
-  variant   -- lb_options.threads_hint: 0 default kernel (split columns
-               where offered), 1 one lane per column
+  variant   -- lb_options.threads_hint: 0 default kernel, 1 one lane per
+               column, 2 split columns on half-warps, 3 on paired warps,
+               4 twin halves (one lane per column, packed twisted halves;
+               where the pivots do not allow it, half-warps run instead)
   strategy  -- assignment (lb_strategy name), balanced on the device with
                end-of-step stealing, the cost rescale at k_c re-draws and a
                threshold (keep the table while predicted max/mean <= 1.15);
@@ -95,7 +97,7 @@ def measure(grids, fields, vps, kc_epochs, epoch_steps, strategy, period, varian
 
 def autotune(grids, fields, vps, kc_epochs=None, epoch_steps=0, cache=None,
              strategies=("greedy_blocked", "auto_spatial", "queue"), periods=(10, 20),
-             variants=(0, 1),
+             variants=(2, 4),
              splits=(1, 2), device="cuda:0", log=None):
     """Best configuration over the candidate grid; returns a dict with the
     knobs, the score and every candidate's score."""
