@@ -751,6 +751,21 @@ __device__ __forceinline__ int pop_with_stealing(const StepParams<TC> &p, int pa
     return -1;
 }
 
+// Runtime-nz split item in the smallest bucket of HB, HB - 8, ... levels per
+// lane that holds the grid's ceil(nz/2) levels (padding levels cost loads,
+// selects and predicated stores, so buckets every 8 levels keep the waste
+// near 10 % over nz 32..96).
+template <class TS, class TC, int HB>
+__device__ __forceinline__ int split_rt_bucket(const StepParams<TC> &p, const GridDev &g,
+                                               const VPDev &vp, int chunk, long long t, int src,
+                                               int lane, bool do_mass, LaneSum<TC> &acc) {
+    if constexpr (HB > 8) {
+        if ((g.nz + 1) / 2 <= HB - 8)
+            return split_rt_bucket<TS, TC, HB - 8>(p, g, vp, chunk, t, src, lane, do_mass, acc);
+    }
+    return process_item_split_rt<TS, TC, HB>(p, g, vp, chunk, t, src, lane, do_mass, acc);
+}
+
 // ------------------------------------------------------------ twin halves
 // One lane per column with the twisted factorisation of the split kernels
 // inside the lane: y2[s] holds (level s, level NZ-1-s), so both halves'
@@ -1137,17 +1152,9 @@ lb_step_kernel(const __grid_constant__ StepParams<TC> p) {
                 kc = process_item_split<TS, TC, NZ>(p, g, vp, it.y, t, src, lane, do_mass, acc);
             else if constexpr (SPLIT) {
                 // per item (one grid, warp-uniform): the smallest half-length
-                // bucket that holds the grid's ceil(nz/2) levels
-                const int hb = (g.nz + 1) / 2;
-                if (NZ / 2 > 16 && hb <= 16)
-                    kc = process_item_split_rt<TS, TC, 16>(p, g, vp, it.y, t, src, lane, do_mass,
-                                                          acc);
-                else if (NZ / 2 > 32 && hb <= 32)
-                    kc = process_item_split_rt<TS, TC, 32>(p, g, vp, it.y, t, src, lane, do_mass,
-                                                          acc);
-                else
-                    kc = process_item_split_rt<TS, TC, NZ / 2>(p, g, vp, it.y, t, src, lane,
-                                                              do_mass, acc);
+                // bucket (multiples of 8 levels) that holds the grid's
+                // ceil(nz/2) levels
+                kc = split_rt_bucket<TS, TC, NZ / 2>(p, g, vp, it.y, t, src, lane, do_mass, acc);
             }
             else
                 kc = process_item<TS, TC, NZ, EXACT, NZLO>(p, g, vp, it.y, t, src, lane, do_mass,
