@@ -10,7 +10,11 @@
 // With plain loads the next item's reads only start after the solves, and
 // the loads in flight are bounded by the registers of the warps that happen
 // to be in their load phase.  A tensor copy needs no registers and overlaps
-// the whole solve phase.
+// the whole solve phase.  Measured on GB300 this kernel is slower than the
+// register-load kernels on every workload tried: the memory phase itself
+// (not its overlap with the solves) bounds the step, and the slots leave
+// room for only 16 warps at nz = 96.  It is an option
+// (lb_options.staged_loads), not a default.
 //
 // Box.  An item's input is the 9x3 column neighbourhood of its 8x2 tile
 // (upwind side on each axis, Sec. VI-B stencil).  TMA wants the innermost
