@@ -445,17 +445,22 @@ extern "C" lb_status lb_create(const lb_grid_desc *grids, int32_t ngrids, const 
         nzmin = std::min(nzmin, d.nz);
     }
     const bool staged = ctx->opt.staged_loads && staged_eligible(ctx->grids);
-    bool wide = true;
-    for (int v = 0; v < nvps; ++v) wide = wide && vps[v].w % 16 == 0;
+    // wide: at least 3/4 of the columns lie in VPs whose width is a multiple
+    // of 16 (32-column work items then idle few lanes)
+    long long cols_all = 0, cols_wide = 0;
+    for (int v = 0; v < nvps; ++v) {
+        const long long c = (long long)vps[v].w * vps[v].h;
+        cols_all += c;
+        if (vps[v].w % 16 == 0) cols_wide += c;
+    }
+    const bool wide = 4 * cols_wide >= 3 * cols_all;
     // twin kernels: the FP32 pivots of a zero-flux end must be one constant
-    // pair from level kTwinS0 up to the middle
-    bool twin_ok = false;
+    // pair from level kTwinS0 on, through the longest half column
+    bool twin_ok = true;
     {
         double mt[kNzMax];
         pivots(grids[0].r, 0, mt);
-        const int h = nzmax / 2;
-        twin_ok = nzmax == nzmin && h > kTwinS0;
-        for (int k = kTwinS0; twin_ok && k < h; ++k)
+        for (int k = kTwinS0; twin_ok && k < kNzMax / 2; ++k)
             twin_ok = (float)mt[k] == (float)mt[kTwinS0] &&
                       (float)(grids[0].r * mt[k]) == (float)(grids[0].r * mt[kTwinS0]);
     }

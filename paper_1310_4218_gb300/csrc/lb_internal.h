@@ -115,9 +115,9 @@ inline int items_of_vp(const KernelInfo &k, int w, int h) {
     return (w * h + k.cols_per_item - 1) / k.cols_per_item;
 }
 // staged: allow the TMA-staged kernel (the caller then provides tensor maps);
-// wide: every VP width is a multiple of 16 (paired-warp kernels apply);
-// twin_ok: the FP32 pivots are one constant pair from level kTwinS0 on (twin
-// kernels apply).
+// wide: at least 3/4 of the columns lie in VPs whose width is a multiple of
+// 16 (the twin kernels are the default there); twin_ok: the FP32 pivots are
+// one constant pair from level kTwinS0 on (twin kernels may run).
 bool find_step_kernel(int storage, int compute, int nz_max, int nz_min, bool all_same_nz,
                       KernelInfo *out, int threads_hint = 0, bool staged = false,
                       bool wide = false, bool twin_ok = false);
@@ -128,7 +128,8 @@ bool kernels_f32(int nz_max, int nz_min, bool same, int threads_hint, bool stage
 bool kernels_f64(int nz_max, int nz_min, bool same, KernelInfo *out);
 bool kernels_f64s(int nz_max, int nz_min, bool same, KernelInfo *out);
 bool kernels_bf16(int nz_max, int nz_min, bool same, KernelInfo *out);
-bool kernels_f32_any(int nz_max, int nz_min, bool one_lane, KernelInfo *out);
+bool kernels_f32_any(int nz_max, int nz_min, int threads_hint, bool wide, bool twin_ok,
+                     KernelInfo *out);
 
 // Middle coupling of the runtime-nz split kernels for a column of nz >= 2
 // rows: lower half hb = ceil(nz/2) rows, upper ht = floor(nz/2), each

@@ -4,11 +4,11 @@
 
 namespace lbk {
 
-// Exact nz 32 / 64 / 96.  Default: when every VP width is a multiple of 16
-// (wide) and the FP32 pivots converge (twin_ok), one lane per column with
-// both twisted halves in packed pairs, items of 32 columns; otherwise split
-// columns on half-warps with 8 x 2 tiles (narrower items idle fewer lanes at
-// the edges of narrow VPs).  threads_hint: 1 one lane per column (plain
+// Exact nz 32 / 64 / 96.  Default: when most columns lie in VPs whose width
+// is a multiple of 16 (wide) and the FP32 pivots converge (twin_ok), one
+// lane per column with both twisted halves in packed pairs, items of 32
+// columns; otherwise split columns on half-warps with 8 x 2 tiles (narrower
+// items idle fewer lanes at the edges of narrow VPs).  threads_hint: 1 one lane per column (plain
 // Thomas), 2 half-warps, 3 paired warps (16 x 2 tiles), 4 twin halves;
 // `staged` the TMA-staged kernels (one box slot per warp, 147-221 KB of
 // shared memory per SM).
@@ -16,7 +16,8 @@ bool kernels_f32(int nz_max, int nz_min, bool same, int threads_hint, bool stage
                  bool twin_ok, KernelInfo *out) {
     const bool one_lane = threads_hint == 1;
     const bool pair = threads_hint == 3;
-    const bool twin = twin_ok && (threads_hint == 4 || (threads_hint == 0 && wide));
+    const bool twin = twin_ok && nz_max / 2 > kTwinS0 &&
+                      (threads_hint == 4 || (threads_hint == 0 && wide));
     if (same && nz_max == 32) {
         if (one_lane) *out = kernel_entry<float, float, 32, true, 1, 512>();
         else if (staged) *out = kernel_entry_tma<32, 1024>();
@@ -41,7 +42,7 @@ bool kernels_f32(int nz_max, int nz_min, bool same, int threads_hint, bool stage
         else *out = kernel_entry<float, float, 96, true, 1, 768, true>();
         return true;
     }
-    return kernels_f32_any(nz_max, nz_min, one_lane, out);
+    return kernels_f32_any(nz_max, nz_min, threads_hint, wide, twin_ok, out);
 }
 
 }  // namespace lbk

@@ -878,6 +878,143 @@ __device__ __forceinline__ int process_item_twin(const StepParams<TC> &p, const 
     return kc;
 }
 
+// Twin halves for grids of any nz >= 2 (several grids of different nz in
+// one launch): pair s holds (level s, level nz-1-s) for s < HMAX; the lower
+// half has hb = ceil(nz/2) levels, the upper ht = floor(nz/2), so each
+// component of a pair is masked at its own half length (for odd nz the
+// middle level belongs to the lower half only).  Same operations per value,
+// in the same order, as the runtime-nz split kernels: clamped loads, selects
+// instead of length-dependent branches, predicated stores.
+template <class TS, class TC, int HMAX, int S0>
+__device__ __forceinline__ int process_item_twin_rt(const StepParams<TC> &p, const GridDev &g,
+                                                    const VPDev &vp, int chunk, long long t,
+                                                    int src, int lane, bool do_mass,
+                                                    LaneSum<TC> &acc) {
+    static_assert(sizeof(TS) == 4 && sizeof(TC) == 4, "twin kernels are FP32");
+    static_assert(HMAX >= 1 && S0 >= 1, "bucket");
+    const ColGeom cg = col_geom(g, vp, chunk, lane);
+    const int plane = g.plane, nz = g.nz;
+    const int hb = (nz + 1) / 2, ht = nz / 2;
+    const TS *in = static_cast<const TS *>(g.q[src]);
+    TS *out = static_cast<TS *>(g.q[src ^ 1]);
+    int kc = g.kc_disk ? kc_disk(g, cg.i, cg.j, t) : g.kc[cg.oc];
+    if (!cg.active || !g.sweeps_on) kc = 0;
+
+    float2 y2[HMAX];
+    const float wx = wgt<float>(g, 1), wy = wgt<float>(g, 2);
+    if (g.xy_only) {
+        const float2 wx2 = f2(wx, wx), wy2 = f2(wy, wy);
+#pragma unroll
+        for (int s = 0; s < HMAX; ++s) {
+            const int lo = min(s, hb - 1) * plane, hi = (nz - 1 - min(s, ht - 1)) * plane;
+            const float2 a = f2(IO<TS, TC>::ld(in + (lo + cg.oi)), IO<TS, TC>::ld(in + (hi + cg.oi)));
+            const float2 b = f2(IO<TS, TC>::ld(in + (lo + cg.oj)), IO<TS, TC>::ld(in + (hi + cg.oj)));
+            const float2 v = fma2(wy2, b, mul2(wx2, a));
+            y2[s] = f2(s < hb ? v.x : 0.f, s < ht ? v.y : 0.f);
+        }
+    } else {
+        const float w0 = wgt<float>(g, 0), wz = wgt<float>(g, 3);
+        const int sz = g.sz;
+        const int kdown = sz >= 0 ? nz - 1 : 0;
+        auto level = [&](int k) {
+            const float cc = IO<TS, TC>::ld(in + (k * plane + cg.oc));
+            const float a = IO<TS, TC>::ld(in + (k * plane + cg.oi));
+            const float b = IO<TS, TC>::ld(in + (k * plane + cg.oj));
+            float v = fmaT(wy, b, wx * a);
+            v = fmaT(k == kdown ? w0 + wz : w0, cc, v);
+            const int ku = k - sz;
+            const int kuc = ku < 0 ? 0 : (ku >= nz ? nz - 1 : ku);
+            const float u = IO<TS, TC>::ld(in + (kuc * plane + cg.oc));
+            return (ku >= 0 && ku < nz) ? fmaT(wz, u, v) : v;
+        };
+#pragma unroll
+        for (int s = 0; s < HMAX; ++s) {
+            const float vl = level(min(s, hb - 1)), vh = level(nz - 1 - min(s, ht - 1));
+            y2[s] = f2(s < hb ? vl : 0.f, s < ht ? vh : 0.f);
+        }
+    }
+
+    // shift by the column's level hb-1 value (the lower half's last)
+    float last = 0.f;
+#pragma unroll
+    for (int s = 0; s < HMAX; ++s) last = s == hb - 1 ? y2[s].x : last;
+    const float cref = kc > 0 ? last : 0.f;
+    if (kc > 0) {
+        const float2 nc = f2(-cref, -cref);
+#pragma unroll
+        for (int s = 0; s < HMAX; ++s) y2[s] = add2(y2[s], nc);
+    }
+    const Coef<TC> &cf = p.coef;
+    const float2 minf = f2(cf.m[S0], cf.m[S0]), rminf = f2(cf.rm[S0], cf.rm[S0]);
+    for (int r = 0; r < kc; ++r) {
+        float2 pp = f2(y2[0].x * cf.m[0], y2[0].y * cf.m[0]);
+        y2[0] = pp;
+#pragma unroll
+        for (int s = 1; s < HMAX; ++s) {
+            float2 np;
+            if (s < S0)
+                np = f2(fmaT(pp.x, cf.rm[s], y2[s].x * cf.m[s]),
+                        fmaT(pp.y, cf.rm[s], y2[s].y * cf.m[s]));
+            else
+                np = fma2(pp, rminf, mul2(y2[s], minf));
+            const bool inl = s < hb, inh = s < ht;
+            y2[s] = f2(inl ? np.x : y2[s].x, inh ? np.y : y2[s].y);
+            pp = f2(inl ? np.x : pp.x, inh ? np.y : pp.y);
+        }
+        // middle: pp holds the last eliminated value of each half
+        const float xl = fmaT(g.ifa_b_f, pp.y, pp.x) * g.ifc_bt_f;
+        const float xh = fmaT(g.ifa_t_f, pp.x, pp.y) * g.ifc_bt_f;
+        y2[HMAX - 1] = f2(hb == HMAX ? xl : y2[HMAX - 1].x, ht == HMAX ? xh : y2[HMAX - 1].y);
+#pragma unroll
+        for (int s = HMAX - 2; s >= 0; --s) {
+            float2 bk;
+            if (s < S0)
+                bk = f2(fmaT(cf.rm[s], y2[s + 1].x, y2[s].x), fmaT(cf.rm[s], y2[s + 1].y, y2[s].y));
+            else
+                bk = fma2(rminf, y2[s + 1], y2[s]);
+            y2[s] = f2(s == hb - 1 ? xl : (s < hb - 1 ? bk.x : y2[s].x),
+                       s == ht - 1 ? xh : (s < ht - 1 ? bk.y : y2[s].y));
+        }
+    }
+
+    const float2 c2 = f2(cref, cref);
+    PairSum ps;
+    if (do_mass) ps.begin();
+#pragma unroll
+    for (int s = 0; s < HMAX; ++s) {
+        float2 x = add2(y2[s], c2);
+        const bool vl = cg.active && s < hb, vh = cg.active && s < ht;
+        st_pred(out + ((vl ? s : 0) * plane + cg.oc), x.x, vl);
+        st_pred(out + ((nz - 1 - (vh ? s : 0)) * plane + cg.oc), x.y, vh);
+        x.x = vl ? x.x : 0.f;
+        x.y = vh ? x.y : 0.f;
+        if (do_mass) ps.add(x);
+    }
+    if (do_mass && cg.active) {
+        acc.col_begin();
+        acc.s = ps.s.x;
+        acc.e = ps.e.x;
+        acc.add(ps.s.y);
+        acc.e = __fadd_rn(acc.e, ps.e.y);
+        acc.col_end();
+    }
+    return kc;
+}
+
+// Runtime-nz twin item in the smallest bucket of HB, HB - 8, ... pairs that
+// holds the grid's ceil(nz/2) levels.
+template <class TS, class TC, int HB>
+__device__ __forceinline__ int twin_rt_bucket(const StepParams<TC> &p, const GridDev &g,
+                                              const VPDev &vp, int chunk, long long t, int src,
+                                              int lane, bool do_mass, LaneSum<TC> &acc) {
+    if constexpr (HB > 8) {
+        if ((g.nz + 1) / 2 <= HB - 8)
+            return twin_rt_bucket<TS, TC, HB - 8>(p, g, vp, chunk, t, src, lane, do_mass, acc);
+    }
+    return process_item_twin_rt<TS, TC, HB, (kTwinS0 < HB ? kTwinS0 : HB)>(p, g, vp, chunk, t, src,
+                                                                             lane, do_mass, acc);
+}
+
 // ------------------------------------------------------------ paired warps
 // Split columns on two warps: a work item is a PW x (32 / PW) tile of 32
 // columns (PW = 16); lane l of the lower warp holds levels 0..H-1 of
@@ -1038,7 +1175,7 @@ template <class TS, class TC, int NZ, bool EXACT, int NZLO, int THREADS, bool SP
 __global__ void __launch_bounds__(THREADS, 1)
 lb_step_kernel(const __grid_constant__ StepParams<TC> p) {
     constexpr bool PAIR = PAIRW > 0;
-    static_assert(!TWIN || (EXACT && !SPLIT && !PAIR), "twin kernels: exact nz, one lane per column");
+    static_assert(!TWIN || (!SPLIT && !PAIR), "twin kernels: one lane per column");
     static_assert(!PAIR || (SPLIT && EXACT && THREADS % 64 == 0 && THREADS / 64 <= 15),
                   "paired warps: exact split columns, at most 15 pairs (named barriers 1..15)");
     extern __shared__ double s_mass[];          // [warps][ngrids]
@@ -1145,9 +1282,11 @@ lb_step_kernel(const __grid_constant__ StepParams<TC> p) {
             }
             long long c0 = clock64();
             int kc;
-            if constexpr (TWIN)
+            if constexpr (TWIN && EXACT)
                 kc = process_item_twin<TS, TC, NZ, kTwinS0>(p, g, vp, it.y, t, src, lane, do_mass,
                                                             acc);
+            else if constexpr (TWIN)
+                kc = twin_rt_bucket<TS, TC, NZ / 2>(p, g, vp, it.y, t, src, lane, do_mass, acc);
             else if constexpr (SPLIT && EXACT)
                 kc = process_item_split<TS, TC, NZ>(p, g, vp, it.y, t, src, lane, do_mass, acc);
             else if constexpr (SPLIT) {

@@ -111,6 +111,66 @@ def test_exact_nz_kernels(nz, kernel):
         assert normwise(out, ref) <= tolerance(g, 6), (extra, strategy)
 
 
+@pytest.mark.parametrize("nz", [32, 64, 96])
+def test_split_family_kernels_agree_bitwise(nz):
+    """The half-warp, paired-warp, twin-halves and TMA-staged kernels run the
+    same floating-point operations on every value in the same order (the
+    twisted factorisation of the split columns; only the lane mapping and
+    the way inputs arrive differ), so their fields agree bit for bit, with
+    tables, stealing and the queue, and match the oracle."""
+    g = Grid(64, 40, nz, 0.5, 0.5, 0.0, 0.1, "f32", "f32", True, (20, 30, 1, 1, 11), 9, 1)
+    q = round_to_storage(gaussian_blob(64, 40, nz, (30, 20, nz / 2), 9.0, 1e-3, 3), "f32")
+    vps = regular_blocks(64, 40, 16, 10)
+    outs = {}
+    for kernel in ("half", "pair", "twin", "staged"):
+        for extra in ({}, {"steal": 1}, {"queue_order": 0}):
+            sim = make_sim([g], [q], vps, **EXACT_KERNELS[kernel], **extra)
+            _check_kernel_shape(sim.info(), kernel)
+            sim.step(3)
+            if extra.get("steal"):
+                sim.measure()
+                sim.rebalance("greedy_blocked")
+            elif "queue_order" in extra:
+                sim.measure()
+                sim.rebalance("queue")
+            sim.step(3)
+            outs[(kernel, tuple(extra))] = sim.field(0)
+            sim.close()
+    base = outs[("half", ())]
+    for k, v in outs.items():
+        assert np.array_equal(v, base), k
+    ref, _ = oracle_run(g, q, 6)
+    assert normwise(base, ref) <= 1e-5
+
+
+@pytest.mark.parametrize("nz", [2, 3, 16, 17, 33, 47, 64, 95])
+def test_runtime_nz_twin_and_split_agree_bitwise(nz):
+    """Runtime-nz kernels (a grid of nz 96 in the same launch selects them):
+    twin halves and half-warp split columns run the same operations per value
+    in the same order, odd nz included (the middle level belongs to the lower
+    half), so the fields agree bit for bit and match the oracle."""
+    grids, fields = [], []
+    for gi, (n, side) in enumerate(((nz, 48), (96, 32))):
+        g = Grid(side, 40, n, 0.5, 0.5, 0.0, 0.1, "f32", "f32", True, (10 + gi, 20, 1, 1, 9), 9, 1)
+        grids.append(g)
+        fields.append(round_to_storage(gaussian_blob(side, 40, n, (side / 2, 20, n / 2), 8.0,
+                                                     1e-3, 3 + gi), "f32"))
+    vps = regular_blocks(48, 40, 16, 10, grid=0) + regular_blocks(32, 40, 16, 10, grid=1)
+    outs = {}
+    for kernel in ("half", "twin"):
+        sim = make_sim(grids, fields, vps, **EXACT_KERNELS[kernel])
+        info = sim.info()
+        assert info.exact_nz == 0
+        assert (info.item_w, info.item_h) == ((8, 2) if kernel == "half" else (32, 0))
+        sim.step(5)
+        outs[kernel] = [sim.field(0), sim.field(1)]
+        sim.close()
+    for gi in range(2):
+        assert np.array_equal(outs["twin"][gi], outs["half"][gi]), gi
+        ref, _ = oracle_run(grids[gi], fields[gi], 5)
+        assert normwise(outs["twin"][gi], ref) <= 1e-5, gi
+
+
 def test_twin_kernel_needs_converged_pivots():
     """Wide VPs take the twin kernel only when the FP32 pivots are one
     constant pair from a fixed level on; with r = 5 they are not, and the
