@@ -35,6 +35,16 @@
  *
  *  4. Diagnostic: the global sum of q after the step (Neumaier-compensated).
  *
+ *  Dynamics, second form (dynamics == 1): the Sec. IV "3D Jacobi solver",
+ *  read as one sweep per step of the weighted Jacobi iteration for Laplace's
+ *  equation on the 7-point stencil,
+ *        q*[k][j][i] = (1 - 6 nu) q + nu (q[i-1] + q[i+1] + q[j-1] + q[j+1]
+ *                                         + q[k-1] + q[k+1]),
+ *  periodic in x and y; vertically the end faces carry no flux (mirror
+ *  ghosts: the missing neighbour of an end cell is the cell itself).  The
+ *  paper gives neither weight nor sweep count; nu = 1/7 (the 7-point mean)
+ *  is the default reading, 0 < nu <= 1/6 keeps every weight non-negative.
+ *
  * Layout: x fastest, idx = (k*ny + j)*nx + i.  All arithmetic is FP64.
  */
 #include <math.h>
@@ -48,6 +58,8 @@ typedef struct {
     int32_t kc_mode;        /* 0: kc array (ny*nx, row j, column i); 1: moving disk */
     const int32_t *kc;      /* used when kc_mode == 0 */
     int32_t disk_x0, disk_y0, disk_vx, disk_vy, disk_r, k_in, k_out;
+    int32_t dynamics;       /* 0: upwind advection; 1: weighted Jacobi sweep */
+    double nu;              /* Jacobi weight (dynamics == 1) */
 } orc_grid;
 
 static long wrap(long a, long n) {
@@ -138,6 +150,44 @@ void orc_advect(const orc_grid *g, int periodic, const double *q, double *qs) {
     }
 }
 
+/*
+ * Weighted Jacobi sweep of the 7-point stencil (dynamics == 1).
+ * periodic != 0: x/y wrap; periodic == 0 (window mode): a neighbour outside
+ * the array is NaN.  Vertical ends: mirror ghosts (zero flux).
+ */
+void orc_jacobi(const orc_grid *g, int periodic, const double *q, double *qs) {
+    const long nx = g->nx, ny = g->ny, nz = g->nz;
+    const double nu = g->nu, w0 = 1.0 - 6.0 * g->nu;
+    for (long k = 0; k < nz; ++k) {
+        const long kd = k > 0 ? k - 1 : 0, ku = k < nz - 1 ? k + 1 : nz - 1;
+        for (long j = 0; j < ny; ++j) {
+            long jm = j - 1, jp = j + 1;
+            const int jmin = periodic || jm >= 0, jpin = periodic || jp < ny;
+            if (periodic) {
+                jm = wrap(jm, ny);
+                jp = wrap(jp, ny);
+            }
+            for (long i = 0; i < nx; ++i) {
+                long im = i - 1, ip = i + 1;
+                const int imin = periodic || im >= 0, ipin = periodic || ip < nx;
+                if (periodic) {
+                    im = wrap(im, nx);
+                    ip = wrap(ip, nx);
+                }
+                const double c = q[(k * ny + j) * nx + i];
+                double sum = 0.0;
+                sum += imin ? q[(k * ny + j) * nx + im] : NAN;
+                sum += ipin ? q[(k * ny + j) * nx + ip] : NAN;
+                sum += jmin ? q[(k * ny + jm) * nx + i] : NAN;
+                sum += jpin ? q[(k * ny + jp) * nx + i] : NAN;
+                sum += q[(kd * ny + j) * nx + i];
+                sum += q[(ku * ny + j) * nx + i];
+                qs[(k * ny + j) * nx + i] = w0 * c + nu * sum;
+            }
+        }
+    }
+}
+
 /* Neumaier-compensated sum; returns sum, writes the compensation term. */
 double orc_sum(const double *x, long n, double *comp) {
     double s = 0.0, c = 0.0;
@@ -160,7 +210,8 @@ double orc_sum(const double *x, long n, double *comp) {
 void orc_step(const orc_grid *g, int periodic, const int32_t *kc,
               const double *q_in, double *q_out) {
     const long nx = g->nx, ny = g->ny, nz = g->nz;
-    orc_advect(g, periodic, q_in, q_out);
+    if (g->dynamics == 1) orc_jacobi(g, periodic, q_in, q_out);
+    else orc_advect(g, periodic, q_in, q_out);
     double *col = (double *)malloc(sizeof(double) * 3 * (size_t)nz);
     double *cp = col + nz, *dp = col + 2 * nz;
     for (long j = 0; j < ny; ++j)
@@ -203,7 +254,8 @@ void orc_run(const orc_grid *g, long t0, int32_t nsteps, double *q,
  * [i0, i0+wx) x [j0, j0+wy) of a periodic grid (full size g->nx x g->ny).
  * q holds nz*wy*wx values on entry (x fastest) and is updated in place;
  * outside the window every neighbour is NaN, so after s steps only the
- * columns whose whole upwind dependence lies in the window stay finite.
+ * columns whose whole dependence (upwind side, or both sides for the Jacobi
+ * sweep) lies in the window stay finite.
  * k_c of a window column is the full grid's value at its global position:
  * the disk rule is evaluated at (i0+i, j0+j) wrapped; for kc_mode 0,
  * kc_fields holds nsteps windows of wy*wx values (or one, if kc_per_step==0).

@@ -39,7 +39,8 @@ class _CGrid(ctypes.Structure):
                 ("disk_x0", ctypes.c_int32), ("disk_y0", ctypes.c_int32),
                 ("disk_vx", ctypes.c_int32), ("disk_vy", ctypes.c_int32),
                 ("disk_r", ctypes.c_int32), ("k_in", ctypes.c_int32),
-                ("k_out", ctypes.c_int32)]
+                ("k_out", ctypes.c_int32), ("dynamics", ctypes.c_int32),
+                ("nu", ctypes.c_double)]
 
 
 _lib = None
@@ -54,6 +55,7 @@ def _L():
         _lib.orc_kc_field.argtypes = [ctypes.POINTER(_CGrid), i64, P]
         _lib.orc_thomas.argtypes = [i32, d, P, P, P]
         _lib.orc_advect.argtypes = [ctypes.POINTER(_CGrid), ctypes.c_int, P, P]
+        _lib.orc_jacobi.argtypes = [ctypes.POINTER(_CGrid), ctypes.c_int, P, P]
         _lib.orc_sum.argtypes = [P, i64, P]
         _lib.orc_sum.restype = d
         _lib.orc_step.argtypes = [ctypes.POINTER(_CGrid), ctypes.c_int, P, P, P]
@@ -79,11 +81,13 @@ class OracleGrid:
     k_in: int = 1
     k_out: int = 1
     kc: np.ndarray = None              # (ny, nx) int32 when kc_disk is False
+    dynamics: int = 0                  # 0: upwind advection; 1: weighted Jacobi sweep
+    nu: float = 1.0 / 7.0              # Jacobi weight
 
     @classmethod
     def from_spec(cls, g, kc=None):
         return cls(g.nx, g.ny, g.nz, g.cx, g.cy, g.cz, g.r, g.kc_disk, tuple(g.disk),
-                   g.k_in, g.k_out, kc)
+                   g.k_in, g.k_out, kc, getattr(g, "dynamics", 0), getattr(g, "nu", 1.0 / 7.0))
 
     def _c(self):
         kc = None
@@ -93,7 +97,7 @@ class OracleGrid:
         x0, y0, vx, vy, R = self.disk
         return _CGrid(self.nx, self.ny, self.nz, self.cx, self.cy, self.cz, self.r,
                       1 if self.kc_disk else 0, kc, x0, y0, vx, vy, R,
-                      self.k_in, self.k_out)
+                      self.k_in, self.k_out, self.dynamics, self.nu)
 
 
 def _f64(q):
@@ -126,8 +130,19 @@ def advect(g, q, periodic=True):
     return out
 
 
+def jacobi(g, q, periodic=True):
+    """One weighted Jacobi sweep of the 7-point stencil (the Sec. IV dynamics
+    phase, dynamics == 1), periodic in x/y, mirror ghosts in z."""
+    q = _f64(q)
+    out = np.empty_like(q)
+    cg = g._c()
+    _L().orc_jacobi(ctypes.byref(cg), 1 if periodic else 0, q.ctypes.data, out.ctypes.data)
+    return out
+
+
 def step(g, q, kc, periodic=True):
-    """One step (advection then k_c sweeps per column) with a given k_c array."""
+    """One step (dynamics -- advection or the Jacobi sweep -- then k_c sweeps
+    per column) with a given k_c array."""
     q = _f64(q)
     kc = np.ascontiguousarray(kc, dtype=np.int32)
     out = np.empty_like(q)

@@ -231,3 +231,93 @@ def test_compensated_sum_matches_exact_rounding():
     x = np.concatenate([rng.normal(size=10000) * 1e8, rng.normal(size=10000)])
     rng.shuffle(x)
     assert oracle.compensated_sum(x) == math.fsum(x)
+
+
+# ---------------------------------------------------------------- Jacobi dynamics
+# The Sec. IV "3D Jacobi solver" phase read as one weighted Jacobi sweep of
+# the 7-point stencil per step (periodic x/y, zero-flux z by mirror ghosts).
+
+def jac_grid(nx, ny, nz, nu, r=0.1, kc=(0, 0)):
+    return OracleGrid(nx, ny, nz, 0.0, 0.0, 0.0, r, True, (0, 0, 0, 0, 10 ** 6), kc[0], kc[1],
+                      dynamics=1, nu=nu)
+
+
+@pytest.mark.parametrize("a,b,c,nu", [(1, 0, 0, 1 / 7), (2, 3, 1, 1 / 7), (0, 0, 2, 1 / 6),
+                                      (5, 1, 4, 0.05), (6, 7, 9, 1 / 7)])
+def test_jacobi_fourier_mode_is_an_eigenvector(a, b, c, nu):
+    """cos(2 pi a i/nx) cos(2 pi b j/ny) cos(pi c (k + 1/2)/nz) is an eigenvector
+    of the sweep (periodic x/y; the mirror ghosts make the half-integer
+    cosine the zero-flux eigenvector in z) with eigenvalue
+    1 - nu (6 - 2 cos(2 pi a/nx) - 2 cos(2 pi b/ny) - 2 cos(pi c/nz))."""
+    nx, ny, nz = 12, 14, 10
+    g = jac_grid(nx, ny, nz, nu)
+    k, j, i = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    q = (np.cos(2 * np.pi * a * i / nx) * np.cos(2 * np.pi * b * j / ny)
+         * np.cos(np.pi * c * (k + 0.5) / nz))
+    lam = 1 - nu * (6 - 2 * np.cos(2 * np.pi * a / nx) - 2 * np.cos(2 * np.pi * b / ny)
+                    - 2 * np.cos(np.pi * c / nz))
+    assert np.max(np.abs(oracle.jacobi(g, q) - lam * q)) <= 1e-13
+
+
+@pytest.mark.parametrize("nu", [1 / 7, 1 / 6, 0.05])
+def test_jacobi_conserves_mass_and_keeps_bounds(nu):
+    """Every cell hands nu of its value to each of its six neighbour slots
+    (a mirror slot hands it back to itself): the total is conserved, and with
+    non-negative weights every new value lies between the old extremes."""
+    g = jac_grid(9, 8, 7, nu)
+    q = rand_field(7, 8, 9, 11, -1.0, 2.0)
+    out = oracle.jacobi(g, q)
+    assert abs(out.sum() - q.sum()) <= 1e-12 * np.abs(q).sum()
+    assert out.min() >= q.min() - 1e-15 and out.max() <= q.max() + 1e-15
+
+
+def test_jacobi_unit_impulse_spreads_to_the_six_neighbours():
+    """A unit value at an interior cell becomes 1 - 6 nu there and nu at each
+    face neighbour; at the top face and x = 0 the mirror keeps one more nu at
+    the cell and the periodic wrap sends one to x = nx - 1."""
+    nu = 0.1
+    nx, ny, nz = 6, 5, 4
+    g = jac_grid(nx, ny, nz, nu)
+    q = np.zeros((nz, ny, nx))
+    q[1, 2, 3] = 1.0
+    out = oracle.jacobi(g, q)
+    want = np.zeros_like(q)
+    want[1, 2, 3] = 1 - 6 * nu
+    for (k, j, i) in ((0, 2, 3), (2, 2, 3), (1, 1, 3), (1, 3, 3), (1, 2, 2), (1, 2, 4)):
+        want[k, j, i] = nu
+    assert np.allclose(out, want, atol=1e-16, rtol=0)
+    q = np.zeros((nz, ny, nx))
+    q[nz - 1, 0, 0] = 1.0
+    out = oracle.jacobi(g, q)
+    want = np.zeros_like(q)
+    want[nz - 1, 0, 0] = 1 - 6 * nu + nu
+    for (k, j, i) in ((nz - 2, 0, 0), (nz - 1, 1, 0), (nz - 1, ny - 1, 0), (nz - 1, 0, 1),
+                      (nz - 1, 0, nx - 1)):
+        want[k, j, i] = nu
+    assert np.allclose(out, want, atol=1e-16, rtol=0)
+
+
+def test_jacobi_step_with_sweeps_conserves_mass():
+    """Jacobi sweep then k_c implicit solves (unit column sums of M^-1): the
+    global sum is invariant over many steps, to FP64 roundoff."""
+    g = OracleGrid(20, 16, 12, 0.0, 0.0, 0.0, 0.3, True, (5, 5, 1, 2, 5), 7, 1, dynamics=1,
+                   nu=1 / 7)
+    q = rand_field(12, 16, 20, 5)
+    _, mass = oracle.run(g, q, 12)
+    assert np.max(np.abs(mass - q.sum())) <= 1e-12 * q.sum()
+
+
+def test_jacobi_window_run_matches_full_run_inside():
+    """Window runs (used to check full-size fields column by column): after s
+    steps the columns at least s cells from every window edge equal the full
+    run, and the rest are NaN (the sweep reads both sides in x and y)."""
+    g = OracleGrid(16, 14, 6, 0.0, 0.0, 0.0, 0.2, True, (4, 4, 1, 0, 4), 5, 1, dynamics=1,
+                   nu=1 / 7)
+    q = rand_field(6, 14, 16, 9)
+    s = 2
+    full, _ = oracle.run(g, q, s)
+    w = oracle.run_window(g, q, 3, 2, 9, 8, s)
+    inner = w[:, s:8 - s, s:9 - s]
+    assert np.array_equal(inner, full[:, 2 + s:2 + 8 - s, 3 + s:3 + 9 - s])
+    assert np.isnan(w[:, :, 0]).all() and np.isnan(w[:, :, 8]).all()
+    assert np.isnan(w[:, 0, :]).all() and np.isnan(w[:, 7, :]).all()
