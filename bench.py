@@ -218,7 +218,7 @@ def cpu_oracle_rate(w, budget_s=12.0):
     x0, y0 = patch
     kcp = np.ascontiguousarray(kc[y0:y0 + side, x0:x0 + side], dtype=np.int32)
     og = oracle.OracleGrid(side, side, g.nz, g.cx, g.cy, g.cz, g.r, False, (0, 0, 0, 0, 0),
-                           1, 1, kcp)
+                           1, 1, kcp, getattr(g, "dynamics", 0), getattr(g, "nu", 1.0 / 7.0))
     q = np.ascontiguousarray(g.initial_field()[:, y0:y0 + side, x0:x0 + side])
     per_step = int(kcp.sum(dtype=np.int64)) * g.nz
     t0 = time.perf_counter()

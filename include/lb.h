@@ -122,6 +122,14 @@ typedef struct {
     int32_t kc_disk;          /* 1: moving-disk rule below; 0: kc array */
     int32_t disk_x0, disk_y0, disk_vx, disk_vy, disk_r;
     int32_t k_in, k_out;      /* k_c inside / outside the disk, >= 0 */
+    int32_t dynamics;         /* the step's first phase (Sec. IV dynamics):
+                                 0 upwind advection with cx, cy, cz; 1 one
+                                 weighted Jacobi sweep of the 7-point stencil,
+                                 q* = (1 - 6 nu) q + nu * (sum of the six face
+                                 neighbours), periodic in x/y, mirror ghosts
+                                 (zero flux) in z; cx, cy, cz are then unused */
+    int32_t pad0;             /* must be 0 */
+    double nu;                /* Jacobi weight, 0 < nu <= 1/6 (dynamics 1) */
 } lb_grid_desc;
 
 /* One VP: columns x0 <= i < x0+w, y0 <= j < y0+h of grid `grid`.  The VPs

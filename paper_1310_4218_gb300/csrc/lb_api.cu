@@ -301,6 +301,8 @@ static cudaError_t dalloc(T **p, size_t n) {
 // multiple of 16 bytes (nx % 4 == 0), TMA's addressing rules.
 static bool staged_eligible(const std::vector<lb_grid_desc> &grids) {
     for (const auto &d : grids) {
+        // the box holds the upwind neighbours only: advection grids
+        if (d.dynamics != 0) return false;
         if (d.storage != LB_F32 || d.compute != LB_F32 || d.nx % 4 != 0) return false;
         if ((reinterpret_cast<uintptr_t>(d.q0) | reinterpret_cast<uintptr_t>(d.q1)) & 15u) return false;
     }
@@ -355,9 +357,15 @@ static lb_status validate(const lb_grid_desc *grids, int32_t ngrids, const lb_vp
             return fail(nullptr, LB_EINVAL, pre + "need nx, ny >= 1 and 1 <= nz <= 128");
         if ((long long)d.nx * d.ny * d.nz >= (1LL << 31))
             return fail(nullptr, LB_EINVAL, pre + "nx*ny*nz must be below 2^31");
-        if (!std::isfinite(d.cx) || !std::isfinite(d.cy) || !std::isfinite(d.cz) ||
-            std::fabs(d.cx) + std::fabs(d.cy) + std::fabs(d.cz) > 1.0 + 1e-12)
+        if (d.dynamics != 0 && d.dynamics != 1)
+            return fail(nullptr, LB_EINVAL, pre + "dynamics is 0 (advection) or 1 (Jacobi)");
+        if (d.pad0 != 0) return fail(nullptr, LB_EINVAL, pre + "pad0 must be 0");
+        if (d.dynamics == 0 &&
+            (!std::isfinite(d.cx) || !std::isfinite(d.cy) || !std::isfinite(d.cz) ||
+             std::fabs(d.cx) + std::fabs(d.cy) + std::fabs(d.cz) > 1.0 + 1e-12))
             return fail(nullptr, LB_EINVAL, pre + "need |cx|+|cy|+|cz| <= 1");
+        if (d.dynamics == 1 && !(d.nu > 0.0 && d.nu <= 1.0 / 6.0 + 1e-15))
+            return fail(nullptr, LB_EINVAL, pre + "Jacobi weight needs 0 < nu <= 1/6");
         if (!std::isfinite(d.r) || d.r < 0.0) return fail(nullptr, LB_EINVAL, pre + "need r >= 0");
         const bool ok_types = (d.storage == LB_F64 && d.compute == LB_F64) ||
                               (d.storage == LB_F64 && d.compute == LB_F32) ||
@@ -453,7 +461,12 @@ extern "C" lb_status lb_create(const lb_grid_desc *grids, int32_t ngrids, const 
         cols_all += c;
         if (vps[v].w % 16 == 0) cols_wide += c;
     }
-    const bool wide = 4 * cols_wide >= 3 * cols_all;
+    bool any_jacobi = false;
+    for (const auto &d : ctx->grids) any_jacobi = any_jacobi || d.dynamics == 1;
+    // the twin kernels are the default on wide layouts, and for the Jacobi
+    // sweep (seven loads per value favour 32 columns of one level per
+    // instruction over narrow tiles)
+    const bool wide = 4 * cols_wide >= 3 * cols_all || any_jacobi;
     // twin kernels: the FP32 pivots of a zero-flux end must be one constant
     // pair from level kTwinS0 on, through the longest half column
     bool twin_ok = true;
@@ -576,7 +589,12 @@ extern "C" lb_status lb_create(const lb_grid_desc *grids, int32_t ngrids, const 
             h.wd[n] = w[n];
             h.wf[n] = (float)w[n];
         }
-        h.xy_only = (w[0] == 0.0 && d.cz == 0.0) ? 1 : 0;
+        h.xy_only = (d.dynamics == 0 && w[0] == 0.0 && d.cz == 0.0) ? 1 : 0;
+        h.jacobi = d.dynamics == 1 ? 1 : 0;
+        h.nu_d = d.nu;
+        h.w0j_d = 1.0 - 6.0 * d.nu;
+        h.nu_f = (float)d.nu;
+        h.w0j_f = (float)(1.0 - 6.0 * d.nu);
         h.sweeps_on = d.r > 0.0 ? 1 : 0;
         const double ml = last_pivot(d.r, d.nz);
         h.mlast_d = ml;

@@ -29,7 +29,9 @@ struct GridDev {
     int32_t disk_x0, disk_y0, disk_vx, disk_vy, disk_r, k_in, k_out;
     int32_t xy_only;               // w0 == 0 and wz == 0: two-neighbour stencil
     int32_t sweeps_on;             // r > 0
-    int32_t pad0;
+    int32_t jacobi;                // 1: weighted Jacobi sweep instead of advection
+    float nu_f, w0j_f;             // Jacobi weights nu, 1 - 6 nu (FP32 compute)
+    double nu_d, w0j_d;            // same for FP64 compute
     float wf[4];                   // w0, |cx|, |cy|, |cz| for FP32 compute
     double wd[4];                  // same for FP64 compute
     float mlast_f, rlast_f;        // last-row coefficients (runtime-nz kernels)

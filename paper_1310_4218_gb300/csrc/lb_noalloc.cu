@@ -169,9 +169,14 @@ extern "C" lb_status lb_step_noalloc(const lb_grid_desc *grid, const lb_vp *vps,
     if (d.nx < 1 || d.ny < 1 || d.nz < 1 || d.nz > kNzMax)
         return fail(LB_EINVAL, "need nx, ny >= 1 and 1 <= nz <= 128");
     if ((long long)d.nx * d.ny * d.nz >= (1LL << 31)) return fail(LB_EINVAL, "nx*ny*nz must be below 2^31");
-    if (!std::isfinite(d.cx) || !std::isfinite(d.cy) || !std::isfinite(d.cz) ||
-        std::fabs(d.cx) + std::fabs(d.cy) + std::fabs(d.cz) > 1.0 + 1e-12)
+    if (d.dynamics != 0 && d.dynamics != 1) return fail(LB_EINVAL, "dynamics is 0 or 1");
+    if (d.pad0 != 0) return fail(LB_EINVAL, "pad0 must be 0");
+    if (d.dynamics == 0 &&
+        (!std::isfinite(d.cx) || !std::isfinite(d.cy) || !std::isfinite(d.cz) ||
+         std::fabs(d.cx) + std::fabs(d.cy) + std::fabs(d.cz) > 1.0 + 1e-12))
         return fail(LB_EINVAL, "need |cx|+|cy|+|cz| <= 1");
+    if (d.dynamics == 1 && !(d.nu > 0.0 && d.nu <= 1.0 / 6.0 + 1e-15))
+        return fail(LB_EINVAL, "Jacobi weight needs 0 < nu <= 1/6");
     if (!std::isfinite(d.r) || d.r < 0.0) return fail(LB_EINVAL, "need r >= 0");
     const bool ok_types = (d.storage == LB_F64 && (d.compute == LB_F64 || d.compute == LB_F32)) ||
                           (d.storage == LB_F32 && d.compute == LB_F32) ||
@@ -257,7 +262,12 @@ extern "C" lb_status lb_step_noalloc(const lb_grid_desc *grid, const lb_vp *vps,
         g.wd[n] = w[n];
         g.wf[n] = (float)w[n];
     }
-    g.xy_only = (w[0] == 0.0 && d.cz == 0.0) ? 1 : 0;
+    g.xy_only = (d.dynamics == 0 && w[0] == 0.0 && d.cz == 0.0) ? 1 : 0;
+    g.jacobi = d.dynamics == 1 ? 1 : 0;
+    g.nu_d = d.nu;
+    g.w0j_d = 1.0 - 6.0 * d.nu;
+    g.nu_f = (float)d.nu;
+    g.w0j_f = (float)(1.0 - 6.0 * d.nu);
     g.sweeps_on = d.r > 0.0 ? 1 : 0;
     const double ml = last_row_pivot(d.r, d.nz);
     g.mlast_d = ml;

@@ -141,6 +141,42 @@ template <> __device__ __forceinline__ double rlast<double>(const GridDev &g) { 
 __device__ __forceinline__ float fmaT(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 __device__ __forceinline__ double fmaT(double a, double b, double c) { return __fma_rn(a, b, c); }
 
+// ------------------------------------------------------------ Jacobi sweep
+// The Sec. IV dynamics phase in its Jacobi form (GridDev.jacobi): one
+// weighted Jacobi sweep of the 7-point stencil per step,
+//     q*_k = (1 - 6 nu) q_k + nu (x-1, x+1, y-1, y+1 neighbours + q_{k-1} + q_{k+1}),
+// periodic in x/y; at the vertical ends the missing neighbour is the cell
+// itself (zero flux).  Plane offsets of a column's four lateral neighbours:
+struct JacNbr {
+    int oc, oxm, oxp, oym, oyp;
+};
+__device__ __forceinline__ JacNbr jac_nbr(const GridDev &g, int i, int j) {
+    const int im = i > 0 ? i - 1 : g.nx - 1, ip = i + 1 < g.nx ? i + 1 : 0;
+    const int jm = j > 0 ? j - 1 : g.ny - 1, jp = j + 1 < g.ny ? j + 1 : 0;
+    return JacNbr{j * g.nx + i, j * g.nx + im, j * g.nx + ip, jm * g.nx + i, jp * g.nx + i};
+}
+template <class TC> __device__ __forceinline__ TC jac_nu(const GridDev &g);
+template <> __device__ __forceinline__ float jac_nu<float>(const GridDev &g) { return g.nu_f; }
+template <> __device__ __forceinline__ double jac_nu<double>(const GridDev &g) { return g.nu_d; }
+template <class TC> __device__ __forceinline__ TC jac_w0(const GridDev &g);
+template <> __device__ __forceinline__ float jac_w0<float>(const GridDev &g) { return g.w0j_f; }
+template <> __device__ __forceinline__ double jac_w0<double>(const GridDev &g) { return g.w0j_d; }
+
+// New value of level k (0 <= k < nz) of the column.
+template <class TS, class TC>
+__device__ __forceinline__ TC jacobi_level(const GridDev &g, const TS *in, int k, int nz,
+                                           const JacNbr &n) {
+    const int plane = g.plane, o = k * plane;
+    const int kd = k > 0 ? k - 1 : 0, ku = k < nz - 1 ? k + 1 : nz - 1;
+    TC s = IO<TS, TC>::ld(in + (o + n.oxm));
+    s += IO<TS, TC>::ld(in + (o + n.oxp));
+    s += IO<TS, TC>::ld(in + (o + n.oym));
+    s += IO<TS, TC>::ld(in + (o + n.oyp));
+    s += IO<TS, TC>::ld(in + (kd * plane + n.oc));
+    s += IO<TS, TC>::ld(in + (ku * plane + n.oc));
+    return fmaT(jac_nu<TC>(g), s, jac_w0<TC>(g) * IO<TS, TC>::ld(in + (o + n.oc)));
+}
+
 // ------------------------------------------------------------ one Thomas solve
 // In place on y[0..nz-1]: forward p_k = (y_k + r p_{k-1}) m_k, back
 // x_k = p_k + r m_k x_{k+1}.  EXACT: nz == NZ, every coefficient is a
@@ -196,7 +232,7 @@ __device__ __forceinline__ ColGeom col_geom(const GridDev &g, const VPDev &vp, i
 }
 
 // Advection and the k_c solves: leaves the new column in y, minus cref.
-template <class TS, class TC, int NZ, bool EXACT, int NZLO>
+template <class TS, class TC, int NZ, bool EXACT, int NZLO, bool JAC = false>
 __device__ __forceinline__ int column_physics(const StepParams<TC> &p, const GridDev &g,
                                               const ColGeom &cg, long long t, int src,
                                               TC (&y)[NZ], TC &cref) {
@@ -206,9 +242,16 @@ __device__ __forceinline__ int column_physics(const StepParams<TC> &p, const Gri
     int kc = g.kc_disk ? kc_disk(g, cg.i, cg.j, t) : g.kc[cg.oc];
     if (!cg.active || !g.sweeps_on) kc = 0;
 
-    // 1. advection into registers (rows >= nz: exact zeros)
+    // 1. advection (or the Jacobi sweep) into registers (rows >= nz: exact zeros)
     const TC wx = wgt<TC>(g, 1), wy = wgt<TC>(g, 2);
-    if (g.xy_only) {
+    if constexpr (JAC) {
+        const JacNbr jn = jac_nbr(g, cg.i, cg.j);
+#pragma unroll
+        for (int k = 0; k < NZ; ++k) {
+            if (EXACT || k < NZLO || k < nz) y[k] = jacobi_level<TS, TC>(g, in, k, nz, jn);
+            else y[k] = TC(0);
+        }
+    } else if (g.xy_only) {
 #pragma unroll
         for (int k = 0; k < NZ; ++k) {
             if (EXACT || k < NZLO || k < nz) {
@@ -277,14 +320,14 @@ __device__ __forceinline__ void store_column(const GridDev &g, const ColGeom &cg
 }
 
 // Returns the lane's k_c (0 for lanes past the VP's last column).
-template <class TS, class TC, int NZ, bool EXACT, int NZLO>
+template <class TS, class TC, int NZ, bool EXACT, int NZLO, bool JAC = false>
 __device__ __forceinline__ int process_item(const StepParams<TC> &p, const GridDev &g,
                                             const VPDev &vp, int chunk, long long t, int src,
                                             int lane, bool do_mass, LaneSum<TC> &acc) {
     const ColGeom cg = col_geom(g, vp, chunk, lane);
     TC y[NZ];
     TC cref;
-    const int kc = column_physics<TS, TC, NZ, EXACT, NZLO>(p, g, cg, t, src, y, cref);
+    const int kc = column_physics<TS, TC, NZ, EXACT, NZLO, JAC>(p, g, cg, t, src, y, cref);
     if (do_mass) store_column<TS, TC, NZ, EXACT, NZLO, true>(g, cg, src, y, cref, acc);
     else store_column<TS, TC, NZ, EXACT, NZLO, false>(g, cg, src, y, cref, acc);
     return kc;
@@ -441,7 +484,7 @@ __device__ __forceinline__ int split_finish(const StepParams<TC> &p, const GridD
     return top ? 0 : kc;
 }
 
-template <class TS, class TC, int NZ>
+template <class TS, class TC, int NZ, bool JAC = false>
 __device__ __forceinline__ int process_item_split(const StepParams<TC> &p, const GridDev &g,
                                                   const VPDev &vp, int chunk, long long t,
                                                   int src, int lane, bool do_mass,
@@ -459,7 +502,11 @@ __device__ __forceinline__ int process_item_split(const StepParams<TC> &p, const
     float2 y2[H / 2];                  // levels 2m, 2m+1 in one register pair
     float *y = reinterpret_cast<float *>(y2);
     const float wx = wgt<float>(g, 1), wy = wgt<float>(g, 2);
-    if (g.xy_only) {
+    if constexpr (JAC) {
+        const JacNbr jn = jac_nbr(g, sg.i, sg.j);
+#pragma unroll
+        for (int s = 0; s < H; ++s) y[s] = jacobi_level<TS, TC>(g, in, top ? NZ - 1 - s : s, NZ, jn);
+    } else if (g.xy_only) {
         const float2 wx2 = f2(wx, wx), wy2 = f2(wy, wy);
 #pragma unroll
         for (int m = 0; m < H / 2; ++m) {
@@ -504,7 +551,7 @@ __device__ __forceinline__ void st_pred(float *ptr, float v, bool pred) {
                  :: "l"(ptr), "f"(v), "r"((unsigned)pred) : "memory");
 }
 
-template <class TS, class TC, int HMAX>
+template <class TS, class TC, int HMAX, bool JAC = false>
 __device__ __forceinline__ int process_item_split_rt(const StepParams<TC> &p, const GridDev &g,
                                                      const VPDev &vp, int chunk, long long t,
                                                      int src, int lane, bool do_mass,
@@ -538,7 +585,15 @@ __device__ __forceinline__ int process_item_split_rt(const StepParams<TC> &p, co
     float2 y2[HMAX / 2];
     float *y = reinterpret_cast<float *>(y2);
     const float wx = wgt<float>(g, 1), wy = wgt<float>(g, 2);
-    if (g.xy_only) {
+    if constexpr (JAC) {
+        const JacNbr jn = jac_nbr(g, i, j);
+#pragma unroll
+        for (int s = 0; s < HMAX; ++s) {
+            const int sc = min(s, hlen - 1);
+            const float v = jacobi_level<TS, TC>(g, in, top ? nz - 1 - sc : sc, nz, jn);
+            y[s] = s < hlen ? v : 0.f;
+        }
+    } else if (g.xy_only) {
         const float2 wx2 = f2(wx, wx), wy2 = f2(wy, wy);
 #pragma unroll
         for (int m = 0; m < HMAX / 2; ++m) {
@@ -755,15 +810,16 @@ __device__ __forceinline__ int pop_with_stealing(const StepParams<TC> &p, int pa
 // lane that holds the grid's ceil(nz/2) levels (padding levels cost loads,
 // selects and predicated stores, so buckets every 8 levels keep the waste
 // near 10 % over nz 32..96).
-template <class TS, class TC, int HB>
+template <class TS, class TC, int HB, bool JAC = false>
 __device__ __forceinline__ int split_rt_bucket(const StepParams<TC> &p, const GridDev &g,
                                                const VPDev &vp, int chunk, long long t, int src,
                                                int lane, bool do_mass, LaneSum<TC> &acc) {
     if constexpr (HB > 8) {
         if ((g.nz + 1) / 2 <= HB - 8)
-            return split_rt_bucket<TS, TC, HB - 8>(p, g, vp, chunk, t, src, lane, do_mass, acc);
+            return split_rt_bucket<TS, TC, HB - 8, JAC>(p, g, vp, chunk, t, src, lane, do_mass,
+                                                        acc);
     }
-    return process_item_split_rt<TS, TC, HB>(p, g, vp, chunk, t, src, lane, do_mass, acc);
+    return process_item_split_rt<TS, TC, HB, JAC>(p, g, vp, chunk, t, src, lane, do_mass, acc);
 }
 
 // ------------------------------------------------------------ twin halves
@@ -779,7 +835,7 @@ __device__ __forceinline__ int split_rt_bucket(const StepParams<TC> &p, const Gr
 // (the host selects this kernel only when that holds), so levels below S0
 // use scalar operations on the per-level constants and the rest four
 // registers.
-template <class TS, class TC, int NZ, int S0>
+template <class TS, class TC, int NZ, int S0, bool JAC = false>
 __device__ __forceinline__ int process_item_twin(const StepParams<TC> &p, const GridDev &g,
                                                  const VPDev &vp, int chunk, long long t, int src,
                                                  int lane, bool do_mass, LaneSum<TC> &acc) {
@@ -795,7 +851,13 @@ __device__ __forceinline__ int process_item_twin(const StepParams<TC> &p, const 
 
     float2 y2[H];                      // (level s, level NZ-1-s)
     const float wx = wgt<float>(g, 1), wy = wgt<float>(g, 2);
-    if (g.xy_only) {
+    if constexpr (JAC) {
+        const JacNbr jn = jac_nbr(g, cg.i, cg.j);
+#pragma unroll
+        for (int s = 0; s < H; ++s)
+            y2[s] = f2(jacobi_level<TS, TC>(g, in, s, NZ, jn),
+                       jacobi_level<TS, TC>(g, in, NZ - 1 - s, NZ, jn));
+    } else if (g.xy_only) {
         const float2 wx2 = f2(wx, wx), wy2 = f2(wy, wy);
 #pragma unroll
         for (int s = 0; s < H; ++s) {
@@ -885,7 +947,7 @@ __device__ __forceinline__ int process_item_twin(const StepParams<TC> &p, const 
 // middle level belongs to the lower half only).  Same operations per value,
 // in the same order, as the runtime-nz split kernels: clamped loads, selects
 // instead of length-dependent branches, predicated stores.
-template <class TS, class TC, int HMAX, int S0>
+template <class TS, class TC, int HMAX, int S0, bool JAC = false>
 __device__ __forceinline__ int process_item_twin_rt(const StepParams<TC> &p, const GridDev &g,
                                                     const VPDev &vp, int chunk, long long t,
                                                     int src, int lane, bool do_mass,
@@ -902,7 +964,15 @@ __device__ __forceinline__ int process_item_twin_rt(const StepParams<TC> &p, con
 
     float2 y2[HMAX];
     const float wx = wgt<float>(g, 1), wy = wgt<float>(g, 2);
-    if (g.xy_only) {
+    if constexpr (JAC) {
+        const JacNbr jn = jac_nbr(g, cg.i, cg.j);
+#pragma unroll
+        for (int s = 0; s < HMAX; ++s) {
+            const float vl = jacobi_level<TS, TC>(g, in, min(s, hb - 1), nz, jn);
+            const float vh = jacobi_level<TS, TC>(g, in, nz - 1 - min(s, ht - 1), nz, jn);
+            y2[s] = f2(s < hb ? vl : 0.f, s < ht ? vh : 0.f);
+        }
+    } else if (g.xy_only) {
         const float2 wx2 = f2(wx, wx), wy2 = f2(wy, wy);
 #pragma unroll
         for (int s = 0; s < HMAX; ++s) {
@@ -1003,32 +1073,31 @@ __device__ __forceinline__ int process_item_twin_rt(const StepParams<TC> &p, con
 
 // Runtime-nz twin item in the smallest bucket of HB, HB - 8, ... pairs that
 // holds the grid's ceil(nz/2) levels.
-template <class TS, class TC, int HB>
+template <class TS, class TC, int HB, bool JAC = false>
 __device__ __forceinline__ int twin_rt_bucket(const StepParams<TC> &p, const GridDev &g,
                                               const VPDev &vp, int chunk, long long t, int src,
                                               int lane, bool do_mass, LaneSum<TC> &acc) {
     if constexpr (HB > 8) {
         if ((g.nz + 1) / 2 <= HB - 8)
-            return twin_rt_bucket<TS, TC, HB - 8>(p, g, vp, chunk, t, src, lane, do_mass, acc);
+            return twin_rt_bucket<TS, TC, HB - 8, JAC>(p, g, vp, chunk, t, src, lane, do_mass, acc);
     }
-    return process_item_twin_rt<TS, TC, HB, (kTwinS0 < HB ? kTwinS0 : HB)>(p, g, vp, chunk, t, src,
-                                                                             lane, do_mass, acc);
+    return process_item_twin_rt<TS, TC, HB, (kTwinS0 < HB ? kTwinS0 : HB), JAC>(
+        p, g, vp, chunk, t, src, lane, do_mass, acc);
 }
 
 // ------------------------------------------------------------ paired warps
 // Split columns on two warps: a work item is a PW x (32 / PW) tile of 32
 // columns (PW = 16); lane l of the lower warp holds levels 0..H-1 of
-// column l, lane l
-// of the upper warp levels NZ-1..H of the same column (the twisted
+// column l, lane l of the upper warp levels NZ-1..H of the same column (the twisted
 // factorisation of the split kernels, with the halves on two warps instead
 // of two half-warps).  Every load and store instruction of a warp then
 // covers 32 columns of one level where the half-warp split touches two
 // levels, 16 columns each; on the 1024 x 1024 x 96 field the memory-only
 // rate of the load-compute-store pattern is 5.2 TB/s for 16 x 2 tiles
 // against 3.3 TB/s for the half-warp split.  The wider tile idles more
-// lanes at the edges of VPs whose widths are not multiples of 16, so the
-// kernel tables choose it only where VP widths allow.  The middle exchange of each
-// solve and the column's reference value go through shared memory, with a
+// lanes at the edges of VPs whose widths are not multiples of 16; it runs
+// when threads_hint asks for it.  The middle exchange of each solve and the
+// column's reference value go through shared memory, with a
 // named barrier of the pair's 64 threads.  Both warps hold the same 32
 // columns, so they see the same k_c values and the same sweep count and
 // reach every barrier together.
@@ -1043,7 +1112,7 @@ __device__ __forceinline__ void pair_sync(int id) {
 }
 
 // Returns the column's k_c on the lower warp, 0 on the upper one.
-template <class TS, class TC, int NZ, int PW>
+template <class TS, class TC, int NZ, int PW, bool JAC = false>
 __device__ __forceinline__ int process_item_pair(const StepParams<TC> &p, const GridDev &g,
                                                  const VPDev &vp, int chunk, long long t, int src,
                                                  int lane, int top, int bar_id, PairXch &x,
@@ -1074,7 +1143,11 @@ __device__ __forceinline__ int process_item_pair(const StepParams<TC> &p, const 
     float2 y2[H / 2];
     float *y = reinterpret_cast<float *>(y2);
     const float wx = wgt<float>(g, 1), wy = wgt<float>(g, 2);
-    if (g.xy_only) {
+    if constexpr (JAC) {
+        const JacNbr jn = jac_nbr(g, i, j);
+#pragma unroll
+        for (int s = 0; s < H; ++s) y[s] = jacobi_level<TS, TC>(g, in, top ? NZ - 1 - s : s, NZ, jn);
+    } else if (g.xy_only) {
         const float2 wx2 = f2(wx, wx), wy2 = f2(wy, wy);
 #pragma unroll
         for (int m = 0; m < H / 2; ++m) {
@@ -1169,6 +1242,62 @@ __device__ __forceinline__ int pop_item(const StepParams<TC> &p, int s, int bin,
     return c < iend ? c : -1;
 }
 
+// ------------------------------------------------------------ item dispatch
+template <class TC>
+struct ItemResult {
+    int kc;
+    LaneSum<TC> acc;
+};
+
+// One work item of the kernel variant, with the advection (JAC false) or the
+// Jacobi form of the dynamics phase.
+template <class TS, class TC, int NZ, bool EXACT, int NZLO, bool SPLIT, bool TWIN, bool JAC>
+__device__ __forceinline__ int run_item(const StepParams<TC> &p, const GridDev &g, const VPDev &vp,
+                                        int chunk, long long t, int src, int lane, bool do_mass,
+                                        LaneSum<TC> &acc) {
+    if constexpr (TWIN && EXACT)
+        return process_item_twin<TS, TC, NZ, kTwinS0, JAC>(p, g, vp, chunk, t, src, lane, do_mass,
+                                                           acc);
+    else if constexpr (TWIN)
+        return twin_rt_bucket<TS, TC, NZ / 2, JAC>(p, g, vp, chunk, t, src, lane, do_mass, acc);
+    else if constexpr (SPLIT && EXACT)
+        return process_item_split<TS, TC, NZ, JAC>(p, g, vp, chunk, t, src, lane, do_mass, acc);
+    else if constexpr (SPLIT)
+        // per item (one grid, warp-uniform): the smallest half-length bucket
+        // (multiples of 8 levels) that holds the grid's ceil(nz/2) levels
+        return split_rt_bucket<TS, TC, NZ / 2, JAC>(p, g, vp, chunk, t, src, lane, do_mass, acc);
+    else
+        return process_item<TS, TC, NZ, EXACT, NZLO, JAC>(p, g, vp, chunk, t, src, lane, do_mass,
+                                                         acc);
+}
+
+// Items of grids with the Jacobi dynamics run through out-of-line copies of
+// the item code, so that the advection path keeps its own register
+// allocation (arguments and the lane sums by value: no address of the
+// caller's registers is taken).
+template <class TS, class TC, int NZ, bool EXACT, int NZLO, bool SPLIT, bool TWIN>
+__device__ __noinline__ ItemResult<TC> run_item_jacobi(const StepParams<TC> &p, const GridDev *g,
+                                                       VPDev vp, int chunk, long long t, int src,
+                                                       int lane, bool do_mass, LaneSum<TC> acc) {
+    ItemResult<TC> r;
+    r.kc = run_item<TS, TC, NZ, EXACT, NZLO, SPLIT, TWIN, true>(p, *g, vp, chunk, t, src, lane,
+                                                               do_mass, acc);
+    r.acc = acc;
+    return r;
+}
+
+template <class TS, class TC, int NZ, int PW>
+__device__ __noinline__ ItemResult<TC> run_pair_jacobi(const StepParams<TC> &p, const GridDev *g,
+                                                       VPDev vp, int chunk, long long t, int src,
+                                                       int lane, int top, int bar_id, PairXch *x,
+                                                       bool do_mass, LaneSum<TC> acc) {
+    ItemResult<TC> r;
+    r.kc = process_item_pair<TS, TC, NZ, PW, true>(p, *g, vp, chunk, t, src, lane, top, bar_id, *x,
+                                                  do_mass, acc);
+    r.acc = acc;
+    return r;
+}
+
 // ------------------------------------------------------------ the kernel
 template <class TS, class TC, int NZ, bool EXACT, int NZLO, int THREADS, bool SPLIT, int PAIRW,
           bool TWIN>
@@ -1247,8 +1376,17 @@ lb_step_kernel(const __grid_constant__ StepParams<TC> p) {
                     cur_grid = vp.grid;
                 }
                 const long long c0 = clock64();
-                const int kc = process_item_pair<TS, TC, NZ, (PAIR ? PAIRW : 16)>(
-                    p, g, vp, it.y, t, src, lane, top, bar_id, x, do_mass, acc);
+                constexpr int PW = PAIR ? PAIRW : 16;
+                int kc;
+                if (g.jacobi) {
+                    const ItemResult<TC> r = run_pair_jacobi<TS, TC, NZ, PW>(
+                        p, &g, vp, it.y, t, src, lane, top, bar_id, &x, do_mass, acc);
+                    kc = r.kc;
+                    acc = r.acc;
+                } else {
+                    kc = process_item_pair<TS, TC, NZ, PW>(p, g, vp, it.y, t, src, lane, top, bar_id,
+                                                            x, do_mass, acc);
+                }
                 __syncwarp();
                 const long long c1 = clock64();
                 const unsigned ksum = __reduce_add_sync(0xffffffffu, (unsigned)kc);
@@ -1282,22 +1420,15 @@ lb_step_kernel(const __grid_constant__ StepParams<TC> p) {
             }
             long long c0 = clock64();
             int kc;
-            if constexpr (TWIN && EXACT)
-                kc = process_item_twin<TS, TC, NZ, kTwinS0>(p, g, vp, it.y, t, src, lane, do_mass,
-                                                            acc);
-            else if constexpr (TWIN)
-                kc = twin_rt_bucket<TS, TC, NZ / 2>(p, g, vp, it.y, t, src, lane, do_mass, acc);
-            else if constexpr (SPLIT && EXACT)
-                kc = process_item_split<TS, TC, NZ>(p, g, vp, it.y, t, src, lane, do_mass, acc);
-            else if constexpr (SPLIT) {
-                // per item (one grid, warp-uniform): the smallest half-length
-                // bucket (multiples of 8 levels) that holds the grid's
-                // ceil(nz/2) levels
-                kc = split_rt_bucket<TS, TC, NZ / 2>(p, g, vp, it.y, t, src, lane, do_mass, acc);
+            if (g.jacobi) {
+                const ItemResult<TC> r = run_item_jacobi<TS, TC, NZ, EXACT, NZLO, SPLIT, TWIN>(
+                    p, &g, vp, it.y, t, src, lane, do_mass, acc);
+                kc = r.kc;
+                acc = r.acc;
+            } else {
+                kc = run_item<TS, TC, NZ, EXACT, NZLO, SPLIT, TWIN, false>(p, g, vp, it.y, t, src,
+                                                                            lane, do_mass, acc);
             }
-            else
-                kc = process_item<TS, TC, NZ, EXACT, NZLO>(p, g, vp, it.y, t, src, lane, do_mass,
-                                                           acc);
             __syncwarp();
             long long c1 = clock64();
             // cell-sweep updates actually performed: sum of k_c * nz over the item

@@ -41,7 +41,8 @@ class Simulation:
                     g.nx, g.ny, g.nz, g.cx, g.cy, g.cz, g.r, L.DTYPES[g.storage],
                     L.DTYPES[g.compute], q0.data_ptr(), q1.data_ptr(),
                     kc_t.data_ptr() if kc_t is not None else None, 1 if g.kc_disk else 0,
-                    x0, y0, vx, vy, R, g.k_in, g.k_out))
+                    x0, y0, vx, vy, R, g.k_in, g.k_out, getattr(g, "dynamics", 0), 0,
+                    getattr(g, "nu", 1.0 / 7.0)))
             torch.cuda.synchronize(self.device)
             self.ctx = L.lb_create(descs, self.vps, options, self.stream.cuda_stream)
         self.nvps = len(self.vps)

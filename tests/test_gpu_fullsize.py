@@ -43,10 +43,13 @@ def run_gpu(w, fields, nsteps, period=10, strategy="auto"):
 
 
 def window_check(w, gi, q0, out, epochs, nsteps, corners, valid=8):
-    """Oracle windows ending at `corners` (lower-left of the valid block)."""
+    """Oracle windows ending at `corners` (lower-left of the valid block).  An
+    advection step reads the upwind side only; the Jacobi sweep reads both
+    sides, so its windows reach nsteps beyond the block on every side."""
     g = w.grids[gi]
     og = oracle.OracleGrid.from_spec(g)
-    side = nsteps + valid
+    both = getattr(g, "dynamics", 0) == 1
+    side = nsteps * (2 if both else 1) + valid
     jobs = []
     for (ci, cj) in corners:
         i0, j0 = ci - nsteps, cj - nsteps
@@ -67,10 +70,10 @@ def window_check(w, gi, q0, out, epochs, nsteps, corners, valid=8):
     scale = 0.0
     sq_d = sq_r = 0.0
     for (i0, j0, _), ref in zip(jobs, refs):
-        r = ref[:, nsteps:, nsteps:]
+        r = ref[:, nsteps:nsteps + valid, nsteps:nsteps + valid]
         assert np.isfinite(r).all()
-        ii = np.arange(i0 + nsteps, i0 + side) % g.nx
-        jj = np.arange(j0 + nsteps, j0 + side) % g.ny
+        ii = np.arange(i0 + nsteps, i0 + nsteps + valid) % g.nx
+        jj = np.arange(j0 + nsteps, j0 + nsteps + valid) % g.ny
         gpu = out[:, jj][:, :, ii]
         errs.append(float(np.abs(gpu - r).max()))
         scale = max(scale, float(np.abs(r).max()))
@@ -123,6 +126,25 @@ def test_lognormal_1024_fp32_windows():
     err, scale = window_check(w, 0, q0, outs[0], epochs, w.steps, corners)
     step_d, tot_d = mass_drift(hist[0], oracle.compensated_sum(q0))
     report("lognormal_fp32_1024x1024x96", max_abs=err, normwise=err / scale,
+           l2_rel=window_check.l2, mass_step_drift=step_d, mass_total_drift=tot_d)
+    assert err / scale <= 1e-5, err / scale
+
+
+def test_jacobi_1024_fp32_windows():
+    """The Jacobi form of the lognormal workload at full size (60 steps, one
+    k_c re-draw): oracle windows around a k_c = 64 hotspot and at the
+    periodic corner."""
+    w = get_config("jacobi_fp32_1024x1024x96")
+    g = w.grids[0]
+    q0 = round_to_storage(g.initial_field(), "f32")
+    nsteps = 60
+    outs, hist, epochs, _ = run_gpu(w, [q0], nsteps)
+    kc = epochs[1][0]
+    j, i = np.unravel_index(np.argmax(kc), kc.shape)
+    corners = [(int(i) - 4, int(j) - 4), (1020, 1019)]
+    err, scale = window_check(w, 0, q0, outs[0], epochs, nsteps, corners)
+    step_d, tot_d = mass_drift(hist[0], oracle.compensated_sum(q0))
+    report("jacobi_fp32_1024x1024x96", max_abs=err, normwise=err / scale,
            l2_rel=window_check.l2, mass_step_drift=step_d, mass_total_drift=tot_d)
     assert err / scale <= 1e-5, err / scale
 

@@ -171,6 +171,71 @@ def test_runtime_nz_twin_and_split_agree_bitwise(nz):
         assert normwise(outs["twin"][gi], ref) <= 1e-5, gi
 
 
+# Jacobi dynamics (Sec. IV "3D Jacobi solver": one weighted 7-point sweep per
+# step in place of the advection) on every kernel family.
+JACOBI_CASES = [
+    # kernel options, nx, nz list (several: a mixed-nz batch), storage, compute
+    ({}, 52, [32], "f32", "f32"),                          # half-warp split (narrow VPs)
+    ({}, 64, [64], "f32", "f32"),                          # twin halves (wide VPs)
+    ({"threads_hint": 3}, 64, [96], "f32", "f32"),         # paired warps
+    ({"threads_hint": 1}, 52, [32], "f32", "f32"),         # one lane per column
+    ({}, 64, [17, 40], "f32", "f32"),                      # runtime nz, twin halves
+    ({"threads_hint": 2}, 64, [17, 40], "f32", "f32"),     # runtime nz, half-warp split
+    ({}, 40, [20], "f64", "f64"),                          # FP64 compute
+    ({}, 40, [33], "bf16", "f32"),                         # BF16 storage
+]
+
+
+@pytest.mark.parametrize("case", range(len(JACOBI_CASES)))
+def test_jacobi_dynamics_parity(case):
+    opt, nx, nzs, storage, compute = JACOBI_CASES[case]
+    grids, fields, vps = [], [], []
+    for gi, nz in enumerate(nzs):
+        g = Grid(nx, 38, nz, 0.0, 0.0, 0.0, 0.2, storage, compute, True, (10 + 7 * gi, 30, 1, 1, 9),
+                 6, 1, dynamics=1, nu=1.0 / 7.0)
+        grids.append(g)
+        fields.append(round_to_storage(gaussian_blob(nx, 38, nz, (nx / 2, 19, nz / 2), 7.0, 1e-3,
+                                                     3 + gi), storage))
+        vps += regular_blocks(nx, 38, 16 if nx % 16 == 0 else 20, 12, grid=gi)
+    sim = make_sim(grids, fields, vps, **opt)
+    sim.step(2)
+    sim.measure()
+    sim.rebalance("greedy_blocked")
+    sim.step(3)
+    outs = [sim.field(gi) for gi in range(len(grids))]
+    sim.close()
+    for gi, g in enumerate(grids):
+        ref, _ = oracle_run(g, fields[gi], 5)
+        assert normwise(outs[gi], ref) <= tolerance(g, 5), (gi, normwise(outs[gi], ref))
+
+
+def test_jacobi_split_family_kernels_agree_bitwise():
+    """Half-warp, paired-warp and twin kernels apply the Jacobi sweep with the
+    same operations in the same order: identical fields."""
+    g = Grid(64, 40, 64, 0.0, 0.0, 0.0, 0.1, "f32", "f32", True, (20, 30, 1, 1, 11), 9, 1,
+             dynamics=1, nu=1.0 / 7.0)
+    q = round_to_storage(gaussian_blob(64, 40, 64, (30, 20, 32), 9.0, 1e-3, 3), "f32")
+    vps = regular_blocks(64, 40, 16, 10)
+    outs = {}
+    for kernel in ("half", "pair", "twin"):
+        sim = make_sim([g], [q], vps, **EXACT_KERNELS[kernel])
+        _check_kernel_shape(sim.info(), kernel)
+        sim.step(4)
+        outs[kernel] = sim.field(0)
+        sim.close()
+    assert np.array_equal(outs["pair"], outs["half"])
+    assert np.array_equal(outs["twin"], outs["half"])
+
+
+def test_jacobi_rejects_bad_weight():
+    from paper_1310_4218_gb300 import lb
+    for nu in (0.0, -0.1, 0.2):
+        g = Grid(16, 16, 8, 0.0, 0.0, 0.0, 0.1, dynamics=1, nu=nu)
+        q = np.zeros((8, 16, 16))
+        with pytest.raises(lb.LBError):
+            make_sim([g], [q], regular_blocks(16, 16, 8, 8))
+
+
 def test_twin_kernel_needs_converged_pivots():
     """Wide VPs take the twin kernel only when the FP32 pivots are one
     constant pair from a fixed level on; with r = 5 they are not, and the

@@ -8,6 +8,8 @@ Names describe the workload; `get_config(name)` builds it.
   hotspot_fp32_512x512x64    512x512x64 FP32, 256 VPs of 32x32, 100 steps, moving disk
   lognormal_fp32_1024x1024x96  1024x1024x96 FP32, 4096 guillotine VPs (x extents on
                                8-column sectors), 200 steps, lognormal k_c re-drawn every 50 steps
+  jacobi_fp32_1024x1024x96     the same with the Jacobi dynamics (7-point sweep) in place of
+                               the advection
   precision_2048x2048x64     2048x2048x64, FP64/FP32/BF16 storage, FP32 compute, 50 steps
   batch64_fp32               64 grids s x s x nz, s in 64..512, nz in 32..96, FP32
 """
@@ -41,6 +43,8 @@ class GridSpec:
     sigma: float = 1.0
     noise: float = 1e-3
     seed: int = 0
+    dynamics: int = 0             # 0: upwind advection; 1: weighted Jacobi sweep (Sec. IV)
+    nu: float = 1.0 / 7.0         # Jacobi weight
 
     def initial_field(self, dtype=np.float64):
         return gaussian_blob(self.nx, self.ny, self.nz, self.center, self.sigma,
@@ -101,6 +105,19 @@ def lognormal_fp32_1024x1024x96():
                     notes="guillotine VPs, lognormal k_c (mu=1, smoothed sigma 4) in 1..64")
 
 
+def jacobi_fp32_1024x1024x96():
+    """The lognormal workload with the Sec. IV dynamics in its Jacobi form:
+    one weighted 7-point Jacobi sweep (nu = 1/7) per step in place of the
+    advection; same grid, VPs, k_c arrays and re-draws."""
+    w = lognormal_fp32_1024x1024x96()
+    g = w.grids[0]
+    g.cx = g.cy = g.cz = 0.0
+    g.dynamics, g.nu = 1, 1.0 / 7.0
+    w.name = "jacobi_fp32_1024x1024x96"
+    w.notes = "Jacobi dynamics (nu 1/7); " + w.notes
+    return w
+
+
 def precision_2048x2048x64(storage="f32"):
     c, s = _blob(2048, 2048, 64)
     g = GridSpec(2048, 2048, 64, 0.5, 0.5, 0.0, 0.1, storage, "f32", True,
@@ -133,6 +150,7 @@ CONFIGS = {
     "plain_fp64_64x64x32": plain_fp64_64x64x32,
     "hotspot_fp32_512x512x64": hotspot_fp32_512x512x64,
     "lognormal_fp32_1024x1024x96": lognormal_fp32_1024x1024x96,
+    "jacobi_fp32_1024x1024x96": jacobi_fp32_1024x1024x96,
     "precision_2048x2048x64": precision_2048x2048x64,
     "batch64_fp32": batch64_fp32,
 }
