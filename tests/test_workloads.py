@@ -72,3 +72,16 @@ def test_autotune_split_layout_tiles():
         assert len(s) >= len(vps)
     s2 = split_layout(vps, 2)
     assert all(w >= 8 and h >= 8 for (_, _, _, w, h) in s2)
+
+
+def test_jacobi_workload_is_the_lognormal_one_with_the_jacobi_sweep():
+    """Same grid, VPs, k_c arrays and re-draws as the lognormal workload; the
+    dynamics phase is the weighted Jacobi sweep (nu = 1/7), no advection."""
+    a = get_config("lognormal_fp32_1024x1024x96")
+    b = get_config("jacobi_fp32_1024x1024x96")
+    ga, gb = a.grids[0], b.grids[0]
+    assert b.vps == a.vps and b.steps == a.steps and b.kc_epoch_steps == a.kc_epoch_steps
+    assert (gb.nx, gb.ny, gb.nz, gb.r) == (ga.nx, ga.ny, ga.nz, ga.r)
+    assert (gb.dynamics, gb.nu) == (1, 1.0 / 7.0) and ga.dynamics == 0
+    assert (gb.cx, gb.cy, gb.cz) == (0.0, 0.0, 0.0)
+    assert np.array_equal(b.kc_array(0, 1), a.kc_array(0, 1))
