@@ -57,7 +57,7 @@ SIZEOF = {"f64": 8, "f32": 4, "bf16": 2}
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
@@ -77,7 +77,10 @@ def dist_env():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    """nvidia-smi clocks and throttle reasons sampled during the timed region:
+    one sample every 20 ms, each stamped with the host time it arrived; only
+    the samples inside the timed window count (the GPU runs the enqueued work
+    between the start of the window and the final synchronize)."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -91,7 +94,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "20"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
@@ -100,9 +103,9 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.monotonic(), line.strip()))
 
-    def stop(self):
+    def stop(self, window=None):
         if not self.proc:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
@@ -113,7 +116,11 @@ class ClockSampler:
         self.thread.join(timeout=2)
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for l in self.lines:
+        lines = self.lines
+        if window:
+            inside = [(t, l) for t, l in lines if window[0] <= t <= window[1]]
+            lines = inside or lines      # a window shorter than one interval
+        for _, l in lines:
             f = [x.strip() for x in l.split(",")]
             if len(f) < 9:
                 continue
@@ -127,7 +134,10 @@ class ClockSampler:
                     reasons.add(n)
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm),
+                "samples_in_timed_window": (sum(1 for t, _ in self.lines
+                                                if window[0] <= t <= window[1])
+                                            if window else None)}
 
 
 def kc_epochs(w, nsteps_total):
@@ -421,6 +431,7 @@ class StrategyRun:
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         kev = []
+        w0 = time.monotonic()
         e0.record(stream)
         for _ in range(nper):
             a = torch.cuda.Event(enable_timing=True)
@@ -433,7 +444,8 @@ class StrategyRun:
             self.t += self.P
         e1.record(stream)
         torch.cuda.synchronize(self.dev)
-        clocks = sampler.stop() if sampler else None
+        w1 = time.monotonic()
+        clocks = sampler.stop((w0, w1)) if sampler else None
         sw1, cs1 = lb.lb_work_done(self.sim.ctx)
         self.collect()
         return {"ms": e0.elapsed_time(e1), "sweeps": sw1 - sw0, "cells": cs1 - cs0,
