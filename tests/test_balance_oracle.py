@@ -2,11 +2,32 @@
 (Sec. VI-A Experiment A, Sec. VI-B Experiment C / Table V, Sec. VII) and
 scheduling-theory facts checked by brute force."""
 import itertools
+import os
 import random
 
 import pytest
 
 from oracle import balance as B
+
+
+def paper_values():
+    """The paper's printed balancer results (tests/golden, with citations)."""
+    path = os.path.join(os.path.dirname(__file__), "golden", "paper_balancer_experiments.txt")
+    out = {}
+    with open(path) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                key, value, _ = [x.strip() for x in line.split("|", 2)]
+                out[key] = value
+    return out
+
+
+PAPER = paper_values()
+
+
+def stays_home(distribution):
+    """Per node, how many of its threads started on it (Table V notation)."""
+    return [grp.count(str(n)) for n, grp in enumerate(distribution.split())]
 
 
 def test_experiment_a_greedy_two_migrations():
@@ -16,7 +37,7 @@ def test_experiment_a_greedy_two_migrations():
     old = B.static_blocks(4, 2)
     assert old == [0, 0, 1, 1]
     new = B.greedy(costs, 2)
-    assert B.migrations(old, new) == 2
+    assert B.migrations(old, new) == int(PAPER["exp_a_greedy_migrations"])
     moved = [v for v in range(4) if old[v] != new[v]]
     assert sorted(old[v] for v in moved) == [0, 1]       # one from each side
     assert B.bin_loads(costs, new, 2) == [3.0, 3.0]
@@ -33,14 +54,19 @@ def test_experiment_c_greedy_twelve_migrations():
     processor with 12 migrations although 8 would do (Table V, Sec. VII)."""
     costs, old = exp_c_first()
     assert old == [0] * 4 + [1] * 4 + [2] * 4 + [3] * 4
+    assert " ".join("".join(str(old[v]) for v in range(4 * n, 4 * n + 4))
+                    for n in range(4)) == PAPER["exp_c_initial_distribution"]
     new = B.greedy(costs, 4)
-    assert B.migrations(old, new) == 12
+    assert B.migrations(old, new) == int(PAPER["exp_c_greedy_migrations"])
+    # Table V: after GreedyLB every node keeps exactly one of its own threads
+    mine = [sum(1 for v in range(16) if new[v] == b and old[v] == b) for b in range(4)]
+    assert mine == stays_home(PAPER["exp_c_greedy_distribution"]) == [1, 1, 1, 1]
     for b in range(4):
         vs = [v for v in range(16) if new[v] == b]
         assert sum(costs[v] == 2.0 for v in vs) == 2 and len(vs) == 4
     assert max(B.bin_loads(costs, new, 4)) == 6.0
     # 8 moves suffice: minimum over all balanced placements, by counting
-    assert min_migrations_to_balance(costs, old, 4) == 8
+    assert min_migrations_to_balance(costs, old, 4) == int(PAPER["exp_c_needed_migrations"])
 
 
 def min_migrations_to_balance(costs, old, nbins):
@@ -72,7 +98,12 @@ def test_experiment_c_refine_swap_after_redistribution():
     assert B.bin_loads(c2, a, 4) == [7.0, 5.0, 7.0, 5.0]
     r = B.refine_swap(c2, a, 4)
     assert B.max_over_mean(c2, r, 4) == 1.0
-    assert B.migrations(a, r) <= 4
+    # the paper's RefineSwapLB moved 4 threads (two per swap, Table V); the
+    # move-first reading needs 2 single moves
+    paper = int(PAPER["exp_c_refine_migrations"])
+    before, after = PAPER["exp_c_greedy_distribution"], PAPER["exp_c_refine_distribution"]
+    assert sum(x != y for x, y in zip(before.replace(" ", ""), after.replace(" ", ""))) == paper
+    assert B.migrations(a, r) <= paper
     assert B.migrations(a, r) == 2
     # greedy from scratch would also balance but moves far more
     assert B.migrations(a, B.greedy(c2, 4)) > 4
