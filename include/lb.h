@@ -404,8 +404,9 @@ typedef struct {
     int32_t item_w, item_h;   /* work item shape: an item_w x item_h tile of a
                                  VP (tiles row-major), or item_h == 0: runs of
                                  item_w columns of the VP in row-major order */
-    int32_t staged_slots;     /* TMA-staged kernel: input boxes in flight per
-                                 processor (shared-memory ring); 0: each warp
+    int32_t staged_slots;     /* TMA-staged kernel: shared-memory box slots
+                                 per processor (one per warp, each holding
+                                 the next work item's input); 0: each warp
                                  loads its own items */
     int32_t pad0;
 } lb_info;

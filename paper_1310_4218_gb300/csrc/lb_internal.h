@@ -101,7 +101,7 @@ struct KernelInfo {
                         // cols_per_item columns in the VP's row-major order
     int twin_s0;        // twin kernels: level from which the FP32 pivots must be one
                         // constant pair, else 0
-    int tma_slots;      // TMA-staged kernel: boxes in the shared-memory ring, else 0
+    int tma_slots;      // TMA-staged kernel: shared-memory box slots (one per warp), else 0
     int tma_slot_bytes; // bytes of one box
 };
 
