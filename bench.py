@@ -114,12 +114,19 @@ class ClockSampler:
         except subprocess.TimeoutExpired:
             self.proc.kill()
         self.thread.join(timeout=2)
+        return self.summarise(self.lines, window)
+
+    @staticmethod
+    def summarise(stamped, window=None):
+        """Median SM clock, highest max clock and active throttle reasons of
+        the (host time, csv line) samples inside window (all samples when
+        none fell inside: a window shorter than one interval)."""
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        lines = self.lines
+        lines = stamped
         if window:
-            inside = [(t, l) for t, l in lines if window[0] <= t <= window[1]]
-            lines = inside or lines      # a window shorter than one interval
+            inside = [(t, l) for t, l in stamped if window[0] <= t <= window[1]]
+            lines = inside or stamped
         for _, l in lines:
             f = [x.strip() for x in l.split(",")]
             if len(f) < 9:
@@ -135,10 +142,9 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None,
                 "reasons": sorted(reasons), "samples": len(sm),
-                "samples_in_timed_window": (sum(1 for t, _ in self.lines
+                "samples_in_timed_window": (sum(1 for t, _ in stamped
                                                 if window[0] <= t <= window[1])
                                             if window else None)}
-
 
 def kc_epochs(w, nsteps_total):
     """Device-independent k_c arrays for every re-draw epoch the run touches."""
