@@ -248,6 +248,32 @@ def cpu_oracle_rate(w, budget_s=12.0):
     return per_step * steps / dt, desc, steps, dt
 
 
+def _oracle_worker(job):
+    """One single-threaded oracle run (spawned process): (workload, budget)."""
+    name, budget_s = job
+    from workloads import get_config
+    v, _, steps, dt = cpu_oracle_rate(get_config(name), budget_s)
+    return v, steps, dt
+
+
+def cpu_oracle_rate_all_cores(w, budget_s=8.0):
+    """The same bounded sample on every host core at once: one unmodified,
+    single-threaded oracle per core (a spawned process pool, so that no
+    process is forked after CUDA was initialised), each stepping its own copy
+    of the patch.  Returns the summed rate and the core count, or an error
+    string instead of failing the benchmark."""
+    import multiprocessing as mp
+    n = os.cpu_count() or 1
+    try:
+        with mp.get_context("spawn").Pool(n) as pool:
+            res = pool.map(_oracle_worker, [(w.name, budget_s)] * n)
+        return {"value": sum(r[0] for r in res), "unit": "cell-sweep updates/s", "cores": n,
+                "sample": "%d processes, each as the one-thread sample (%d-%d steps)"
+                          % (n, min(r[1] for r in res), max(r[1] for r in res))}
+    except Exception as ex:                      # reported, never fatal
+        return {"value": None, "cores": n, "error": repr(ex)[:200]}
+
+
 def run_reference(args, rank, world):
     """The reference arm: the CPU oracle, timed on the host cores."""
     from workloads import get_config
@@ -583,7 +609,7 @@ def main():
     if rank == 0 and not args.no_cpu:
         v, desc, _, _ = cpu_oracle_rate(w)
         cpu = {"value": v, "unit": "cell-sweep updates/s", "cores": 1, "kind": "oracle",
-               "sample": desc}
+               "sample": desc, "all_cores": cpu_oracle_rate_all_cores(w)}
 
     if rank == 0:
         out = {
