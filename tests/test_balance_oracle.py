@@ -22,7 +22,7 @@ def paper_values():
     return out
 
 
-PAPER = paper_values()
+PRINTED = paper_values()
 
 
 def stays_home(distribution):
@@ -37,7 +37,7 @@ def test_experiment_a_greedy_two_migrations():
     old = B.static_blocks(4, 2)
     assert old == [0, 0, 1, 1]
     new = B.greedy(costs, 2)
-    assert B.migrations(old, new) == int(PAPER["exp_a_greedy_migrations"])
+    assert B.migrations(old, new) == int(PRINTED["exp_a_greedy_migrations"])
     moved = [v for v in range(4) if old[v] != new[v]]
     assert sorted(old[v] for v in moved) == [0, 1]       # one from each side
     assert B.bin_loads(costs, new, 2) == [3.0, 3.0]
@@ -55,18 +55,18 @@ def test_experiment_c_greedy_twelve_migrations():
     costs, old = exp_c_first()
     assert old == [0] * 4 + [1] * 4 + [2] * 4 + [3] * 4
     assert " ".join("".join(str(old[v]) for v in range(4 * n, 4 * n + 4))
-                    for n in range(4)) == PAPER["exp_c_initial_distribution"]
+                    for n in range(4)) == PRINTED["exp_c_initial_distribution"]
     new = B.greedy(costs, 4)
-    assert B.migrations(old, new) == int(PAPER["exp_c_greedy_migrations"])
+    assert B.migrations(old, new) == int(PRINTED["exp_c_greedy_migrations"])
     # Table V: after GreedyLB every node keeps exactly one of its own threads
     mine = [sum(1 for v in range(16) if new[v] == b and old[v] == b) for b in range(4)]
-    assert mine == stays_home(PAPER["exp_c_greedy_distribution"]) == [1, 1, 1, 1]
+    assert mine == stays_home(PRINTED["exp_c_greedy_distribution"]) == [1, 1, 1, 1]
     for b in range(4):
         vs = [v for v in range(16) if new[v] == b]
         assert sum(costs[v] == 2.0 for v in vs) == 2 and len(vs) == 4
     assert max(B.bin_loads(costs, new, 4)) == 6.0
     # 8 moves suffice: minimum over all balanced placements, by counting
-    assert min_migrations_to_balance(costs, old, 4) == int(PAPER["exp_c_needed_migrations"])
+    assert min_migrations_to_balance(costs, old, 4) == int(PRINTED["exp_c_needed_migrations"])
 
 
 def min_migrations_to_balance(costs, old, nbins):
@@ -100,8 +100,8 @@ def test_experiment_c_refine_swap_after_redistribution():
     assert B.max_over_mean(c2, r, 4) == 1.0
     # the paper's RefineSwapLB moved 4 threads (two per swap, Table V); the
     # move-first reading needs 2 single moves
-    paper = int(PAPER["exp_c_refine_migrations"])
-    before, after = PAPER["exp_c_greedy_distribution"], PAPER["exp_c_refine_distribution"]
+    paper = int(PRINTED["exp_c_refine_migrations"])
+    before, after = PRINTED["exp_c_greedy_distribution"], PRINTED["exp_c_refine_distribution"]
     assert sum(x != y for x, y in zip(before.replace(" ", ""), after.replace(" ", ""))) == paper
     assert B.migrations(a, r) <= paper
     assert B.migrations(a, r) == 2
