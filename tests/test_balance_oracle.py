@@ -142,6 +142,23 @@ def test_refine_never_increases_max_and_keeps_every_vp(seed):
     assert max(B.bin_loads(costs, r, nb)) <= max(B.bin_loads(costs, a0, nb))
 
 
+def test_refine_swaps_when_no_single_move_fits():
+    """Bins {3, 3} and {2, 2}: every single move overshoots the mean 5 (by
+    more than tol), and the only balanced placements hold one 3 and one 2
+    per bin (checked by enumeration), so RefineSwapLB must swap a 3 with a 2:
+    two migrations, both bins at 5."""
+    costs = [3.0, 3.0, 2.0, 2.0]
+    a0 = [0, 0, 1, 1]
+    balanced = [a for a in itertools.product(range(2), repeat=4)
+                if B.bin_loads(costs, a, 2) == [5.0, 5.0]]
+    assert balanced and all(sorted(costs[v] for v in range(4) if a[v] == 0) == [2.0, 3.0]
+                            for a in balanced)
+    r = B.refine_swap(costs, a0, 2)
+    assert tuple(r) in balanced
+    assert B.migrations(a0, r) == 2
+    assert B.bin_loads(costs, r, 2) == [5.0, 5.0]
+
+
 def test_refine_is_idle_when_balanced():
     costs = [1.0] * 12
     a = B.static_blocks(12, 4)

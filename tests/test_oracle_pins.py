@@ -123,6 +123,67 @@ def test_sweeps_use_the_columns_own_kc():
     assert np.array_equal(out[:, mask], q[:, mask])
 
 
+def solves(col, r, n):
+    """n implicit solves of one column by dense linear algebra."""
+    return np.linalg.solve(np.linalg.matrix_power(dense_operator(col.size, r), n), col)
+
+
+def test_array_kc_gives_each_column_its_own_number_of_solves():
+    """k_c from an array (the lognormal workloads' source): with no advection,
+    column (i, j) after one step is M^-k_c(i,j) applied to it, for every k_c
+    from 0 to 4 on a non-square grid (a transposed lookup lands elsewhere)."""
+    nx, ny, nz, r = 5, 4, 6, 0.3
+    kc = np.fromfunction(lambda j, i: (i + 2 * j) % 5, (ny, nx), dtype=int).astype(np.int32)
+    g = OracleGrid(nx, ny, nz, 0.0, 0.0, 0.0, r, kc_disk=False, kc=kc)
+    assert np.array_equal(oracle.kc_field(g, 0), kc)
+    q = rand_field(nz, ny, nx, 21)
+    out, _ = oracle.run(g, q, 1)
+    for j in range(ny):
+        for i in range(nx):
+            exp = solves(q[:, j, i], r, int(kc[j, i]))
+            assert np.max(np.abs(out[:, j, i] - exp)) < 1e-14
+    assert np.array_equal(out[:, kc == 0], q[:, kc == 0])
+
+
+def test_run_from_t0_takes_the_load_rule_at_t0():
+    """A run that starts at global step t0 uses k_c(t0): the disk rolled by
+    t0 (vy, vx) cells (the motion pinned above), not k_c(0)."""
+    nx, ny, nz, r, t0 = 12, 10, 5, 0.2, 4
+    g = OracleGrid(nx, ny, nz, 0.0, 0.0, 0.0, r, True, (2, 3, 1, 2, 3), 3, 0)
+    kc_t0 = np.roll(oracle.kc_field(g, 0), (2 * t0, t0), axis=(0, 1))
+    assert not np.array_equal(kc_t0, oracle.kc_field(g, 0))
+    q = rand_field(nz, ny, nx, 22)
+    out, _ = oracle.run(g, q, 1, t0=t0)
+    for j in range(ny):
+        for i in range(nx):
+            exp = solves(q[:, j, i], r, int(kc_t0[j, i]))
+            assert np.max(np.abs(out[:, j, i] - exp)) < 1e-14
+
+
+def test_per_step_kc_arrays_are_taken_step_by_step():
+    """Per-step k_c arrays (k_c re-draws): with no advection a column ends as
+    M^-(k_1 + k_2 + k_3) of itself, in whole-grid runs and in window runs."""
+    nx, ny, nz, r, n = 6, 5, 4, 0.25, 3
+    rng = np.random.default_rng(23)
+    kcs = rng.integers(0, 4, size=(n, ny, nx)).astype(np.int32)
+    total = kcs.sum(axis=0)
+    assert not np.array_equal(total, n * kcs[0])
+    g = OracleGrid(nx, ny, nz, 0.0, 0.0, 0.0, r, kc_disk=False, kc=kcs[0])
+    q = rand_field(nz, ny, nx, 24)
+    full, _ = oracle.run(g, q, n, kc_fields=kcs)
+    i0, j0, wx, wy = 4, 3, 4, 3                      # wraps around both edges
+    ii, jj = np.arange(i0, i0 + wx) % nx, np.arange(j0, j0 + wy) % ny
+    win = oracle.run_window(g, q, i0, j0, wx, wy, n, kc_window=kcs[:, jj][:, :, ii])
+    for j in range(ny):
+        for i in range(nx):
+            exp = solves(q[:, j, i], r, int(total[j, i]))
+            assert np.max(np.abs(full[:, j, i] - exp)) < 1e-14
+    for b, j in enumerate(jj):
+        for a, i in enumerate(ii):
+            exp = solves(q[:, j, i], r, int(total[j, i]))
+            assert np.max(np.abs(win[:, b, a] - exp)) < 1e-14
+
+
 # ---------------------------------------------------------------- full step
 
 def test_mass_conserved():
