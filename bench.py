@@ -26,8 +26,9 @@ replay: steps, device measurement, device rebalance; with +dev); kernel
 choices "+pair" (split columns on paired warps), "+half" (on half-warps),
 "+twin" (one lane per column, packed twisted halves), "+tma" (TMA-staged)
 and "+one" (one lane per column, plain Thomas) override the default, which
-takes twin halves where every VP width is a multiple of 16 and half-warps
-otherwise.
+takes twin halves where at least 3/4 of the columns lie in VPs whose width is
+a multiple of 16, or the grid runs the Jacobi sweep (and the FP32 pivots are
+constant from level 8 on), and half-warps otherwise.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--workload NAME] [--period P] [--strategy auto|static|queue|...]
