@@ -150,15 +150,17 @@ typedef struct {
     double refine_tol;            /* RefineSwapLB tolerance (default 0.05) */
     int64_t barrier_timeout_ns;   /* grid-barrier wait limit (default 2 s) */
     int32_t threads_hint;         /* kernel variant for FP32 grids: 0 default
-                                     (nz 32, 64, 96: one lane per column with
-                                     packed twisted halves when every VP
-                                     width is a multiple of 16 and r lets
-                                     the FP32 pivots converge, else split
-                                     columns on half-warps; other nz: split
-                                     columns), 1 one lane per column, 2 split
-                                     columns on half-warps, 3 split columns
-                                     on paired warps, 4 packed twisted
-                                     halves (nz 32, 64, 96) */
+                                     (one lane per column with packed
+                                     twisted halves when at least 3/4 of
+                                     the columns lie in VPs whose width is
+                                     a multiple of 16, or a grid runs the
+                                     Jacobi sweep, and r lets the FP32
+                                     pivots converge; else split columns on
+                                     half-warps), 1 one lane per column, 2
+                                     split columns on half-warps, 3 split
+                                     columns on paired warps (nz 32, 64,
+                                     96), 4 packed twisted halves where the
+                                     pivots allow */
     int32_t steal;                /* 1: with processor tables, a processor
                                      that finishes its VPs takes the next
                                      work items of the processor with the

@@ -84,20 +84,52 @@ def build(force=False, verbose=False, jobs=None):
     return LIB
 
 
-if __name__ == "__main__":
-    build(force="--force" in sys.argv, verbose="-v" in sys.argv)
-    print(LIB)
+def strip_comments(text):
+    """C/C++/CUDA source text without its comments, trailing blanks and empty
+    lines.  String and character literals are kept whole, so a "//" inside
+    one is not taken for a comment."""
+    out, i, n = [], 0, len(text)
+    while i < n:
+        c = text[i]
+        if text.startswith("//", i):
+            j = text.find("\n", i)
+            i = n if j < 0 else j
+        elif text.startswith("/*", i):
+            j = text.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+            out.append(" ")
+        elif c in "\"'":
+            j = i + 1
+            while j < n and text[j] != c and text[j] != "\n":
+                j += 2 if text[j] == "\\" else 1
+            out.append(text[i:j + 1])
+            i = j + 1
+        else:
+            out.append(c)
+            i += 1
+    lines = (line.rstrip() for line in "".join(out).splitlines())
+    return "\n".join(line for line in lines if line)
 
 
-def source_hash():
-    """Hash of every kernel and ABI source: ties a recorded profile to the
-    exact code it measured."""
+def source_hash(csrc=CSRC, include=INCLUDE):
+    """Hash of every kernel and ABI source, comments ignored: ties a recorded
+    profile to the exact code it measured.  An edit that touches only
+    comments or blank lines leaves it unchanged; any other edit changes it."""
     import hashlib
     h = hashlib.sha256()
-    files = sorted(glob.glob(os.path.join(CSRC, "*")) + glob.glob(os.path.join(INCLUDE, "*.h")))
+    # the ABI header first, then the kernel sources, each group by name: the
+    # value does not depend on where the two directories sit
+    files = (sorted(glob.glob(os.path.join(include, "*.h")))
+             + sorted(glob.glob(os.path.join(csrc, "*"))))
     for f in files:
         if os.path.isfile(f):
             h.update(os.path.basename(f).encode())
-            with open(f, "rb") as fh:
-                h.update(fh.read())
+            with open(f, encoding="utf-8") as fh:
+                h.update(strip_comments(fh.read()).encode())
+            h.update(b"\0")
     return h.hexdigest()[:16]
+
+
+if __name__ == "__main__":
+    build(force="--force" in sys.argv, verbose="-v" in sys.argv)
+    print(LIB)

@@ -4,14 +4,15 @@
 
 namespace lbk {
 
-// Exact nz 32 / 64 / 96.  Default: when most columns lie in VPs whose width
-// is a multiple of 16 (wide) and the FP32 pivots converge (twin_ok), one
-// lane per column with both twisted halves in packed pairs, items of 32
-// columns; otherwise split columns on half-warps with 8 x 2 tiles (narrower
-// items idle fewer lanes at the edges of narrow VPs).  threads_hint: 1 one lane per column (plain
-// Thomas), 2 half-warps, 3 paired warps (16 x 2 tiles), 4 twin halves;
-// `staged` the TMA-staged kernels (one box slot per warp, 147-221 KB of
-// shared memory per SM).
+// Exact nz 32 / 64 / 96.  Default: when the layout is wide (at least 3/4 of
+// the columns in VPs whose width is a multiple of 16, or a Jacobi grid) and
+// the FP32 pivots converge (twin_ok), one lane per column with both twisted
+// halves in packed pairs, items of 32 columns; otherwise split columns on
+// half-warps with 8 x 2 tiles (narrower items idle fewer lanes at the edges
+// of narrow VPs).  threads_hint: 1 one lane per column (plain Thomas),
+// 2 half-warps, 3 paired warps (16 x 2 tiles), 4 twin halves; `staged` the
+// TMA-staged kernels (one box slot per warp, 147-221 KB of shared memory
+// per SM).
 bool kernels_f32(int nz_max, int nz_min, bool same, int threads_hint, bool staged, bool wide,
                  bool twin_ok, KernelInfo *out) {
     const bool one_lane = threads_hint == 1;

@@ -4,10 +4,10 @@
 
 namespace lbk {
 
-// Default: twin halves (one lane per column) where most columns lie in VPs
-// whose width is a multiple of 16 and the FP32 pivots converge, else split
-// columns on
-// half-warps; threads_hint 1 one lane per column (plain Thomas), 2 half-warp
+// Default: twin halves (one lane per column) where at least 3/4 of the
+// columns lie in VPs whose width is a multiple of 16, or a grid runs the
+// Jacobi sweep, and the FP32 pivots converge; else split columns on
+// half-warps.  threads_hint 1 one lane per column (plain Thomas), 2 half-warp
 // split columns, 4 twin halves where the pivots allow.
 bool kernels_f32_any(int nz_max, int nz_min, int threads_hint, bool wide, bool twin_ok,
                      KernelInfo *out) {

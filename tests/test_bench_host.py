@@ -120,3 +120,24 @@ def test_roofline_peak_prefers_the_measured_copy_bandwidth(tmp_path, monkeypatch
 def test_whole_job_rate_on_one_rank():
     """Without a process group: this rank's work over its own time."""
     assert bench.whole_job_rate(3.0e9, 1500.0) == 2.0e9
+
+
+def test_source_hash_ignores_comments_and_sees_code(tmp_path):
+    """The hash that keys the recorded DRAM traffic survives comment-only
+    edits and changes with any code edit; literals that contain comment
+    markers are code."""
+    import shutil
+    from paper_1310_4218_gb300 import build
+    csrc, inc = tmp_path / "csrc", tmp_path / "include"
+    shutil.copytree(build.CSRC, csrc)
+    shutil.copytree(build.INCLUDE, inc)
+    h0 = build.source_hash(str(csrc), str(inc))
+    assert h0 == build.source_hash()
+    f = csrc / "lb_step_f32.cu"
+    text = f.read_text()
+    f.write_text("// a new comment\n/* and a block\n   comment */\n" + text + "\n\n")
+    assert build.source_hash(str(csrc), str(inc)) == h0
+    f.write_text(text + "\nstatic const int lb_unused_constant = 1;\n")
+    assert build.source_hash(str(csrc), str(inc)) != h0
+    assert build.strip_comments('a = "//x"; // c\nb = \'/\'; /* d */ c;\n') == \
+        'a = "//x";\nb = \'/\';   c;'
