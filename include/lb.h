@@ -14,7 +14,9 @@
  *   1. dynamics: first-order upwind advection, convex donor-cell form
  *        q* = (1-|cx|-|cy|-|cz|) q + |cx| q[i-sx] + |cy| q[j-sy] + |cz| q[k-sz]
  *      (s = sign of the velocity), periodic in x and y, zero flux through
- *      the bottom and top faces;
+ *      the bottom and top faces; or, with lb_grid_desc.dynamics = 1, one
+ *      weighted Jacobi sweep of the 7-point stencil (the paper's "3D Jacobi
+ *      solver" phase, Sec. IV);
  *   2. physics: per column, k_c(i,j,t) passes of the implicit vertical
  *      diffusion solve M x = d, M = tridiag(-r, 1+2r, -r) with zero-flux
  *      ends (first and last diagonal 1+r) -- the serial-in-k recurrence of

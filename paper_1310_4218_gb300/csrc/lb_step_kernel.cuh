@@ -1,27 +1,37 @@
 // Persistent step kernel: every VP of every grid, nsteps time steps, one
-// cooperative launch.
+// cooperative launch, one CTA (a "processor") per SM by default.
 //
 // Work decomposition.  A VP (Sec. III over-decomposition) is cut into work
-// items of 32 consecutive columns of its row-major column order, one column
-// per lane.  A processor (CTA) owns a contiguous range of the item table;
-// its warps pop items from a shared-memory counter.  In queue mode every warp
-// pops from one global counter instead (the task-queue scheme of Sec. II).
+// items: 8 x 2 column tiles (split kernels on half-warps), 16 x 2 tiles
+// (split kernels on paired warps) or runs of 32 consecutive columns of its
+// row-major column order (one lane per column: twin halves and plain
+// Thomas).  A processor owns a contiguous range of the item table, and its
+// warps pop items from a shared-memory counter, or with stealing from a
+// per-processor global counter that idle processors also draw on.  In queue
+// mode every warp pops from one global counter instead (the task-queue
+// scheme of Sec. II).
 //
-// Per column and step (Fig. 2's JACOBI then PHYSIC kernels, fused):
-//   1. upwind advection of the whole column into registers (level by level,
-//      coalesced across the warp: lanes are x-adjacent columns);
+// Per column and step (Fig. 2's dynamics then physics kernels, fused):
+//   1. dynamics into registers, level by level and coalesced across the
+//      warp (lanes are x-adjacent columns): upwind advection, or with
+//      GridDev::jacobi one weighted 7-point Jacobi sweep (Sec. IV), run in
+//      out-of-line copies of the item code;
 //   2. k_c(i,j,t) from the moving-disk rule or the k_c array (Sec. VI-B);
-//   3. k_c implicit vertical-diffusion solves in registers (Thomas: forward
-//      elimination and back substitution, the serial-in-k recurrence of
-//      Fig. 1 / Fig. 4).  The column is shifted by a reference value c
-//      before the solves and shifted back after: M 1 = 1, so
-//      M^-k (d - c1) + c1 = M^-k d exactly, while the rounding of the FP32
-//      pivots now acts on the small deviation d - c1 instead of on d;
+//   3. k_c implicit vertical-diffusion solves in registers (the serial-in-k
+//      recurrence of Fig. 1 / Fig. 4).  Split and twin forms use the
+//      twisted factorisation: both halves of the column eliminate toward
+//      the middle with the same pivots, solve a 2 x 2 middle system and
+//      back-substitute outward.  The halves sit on two half-warps, on two
+//      warps, or as packed FP32x2 pairs in one lane; FP64 and BF16 storage
+//      use one lane per column with plain Thomas.  The column is shifted by
+//      a reference value c before the solves and shifted back after:
+//      M 1 = 1, so M^-k (d - c1) + c1 = M^-k d exactly, while the rounding
+//      of the FP32 pivots acts on the small deviation d - c1 instead of d;
 //   4. store of the new column; compensated sum of the stored values for
 //      the global sum diagnostic.
-// Each work item's duration (clock64, lane 0) is added to its VP's cost:
-// the on-device load measurement of Sec. V.  A grid-wide barrier with a
-// time limit separates steps.
+// Each work item's duration (clock64) is added to its VP's cost: the
+// on-device load measurement of Sec. V.  A grid-wide barrier with a time
+// limit separates steps.
 #pragma once
 
 #include <cuda_bf16.h>
