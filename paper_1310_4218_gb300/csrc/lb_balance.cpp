@@ -1,4 +1,6 @@
-// Host balancers (Sec. VI): static placement, GreedyLB, RefineSwapLB.
+// Host balancers (Sec. VI): static placement, GreedyLB, RefineSwapLB, and
+// GreedyLB's rule over a given VP order (list scheduling) or block by block
+// (blocked GreedyLB).
 //
 // Costs arrive as FP64 and are rounded once to a fixed-point grid
 // (fixed_point): integers whose every sum stays below 2^53.  Loads are then

@@ -1,5 +1,5 @@
-// Host balancers (Sec. VI): static placement, GreedyLB, RefineSwapLB, on the
-// fixed-point cost grid.
+// Host balancers (Sec. VI): static placement, GreedyLB, RefineSwapLB, list
+// scheduling and blocked GreedyLB, on the fixed-point cost grid.
 #pragma once
 
 #include <vector>
