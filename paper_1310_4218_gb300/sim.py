@@ -68,6 +68,12 @@ class Simulation:
         # the copy ran on torch's current stream; the ctx stream reads the array
         torch.cuda.current_stream(self.device).synchronize()
         L.lb_set_kc(self.ctx, grid, t.data_ptr())
+        # both arrays are read on the ctx stream: steps enqueued before this
+        # call may still read the old one, so neither block may be reused
+        # until the work queued there when it is freed has finished
+        t.record_stream(self.stream)
+        if self.kc[grid] is not None:
+            self.kc[grid].record_stream(self.stream)
         self.kc[grid] = t
 
     def info(self):
