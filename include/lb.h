@@ -120,7 +120,11 @@ typedef struct {
     void *q0;
     void *q1;
     const int32_t *kc;        /* device int32 [ny*nx] (row j, column i); read
-                                 every step when kc_disk == 0, caller-owned */
+                                 every step when kc_disk == 0, caller-owned.
+                                 Each entry is that column's solve count:
+                                 entries <= 0 mean none, and the device
+                                 does not bound them, so a launch lasts as
+                                 long as its largest entry demands */
     int32_t kc_disk;          /* 1: moving-disk rule below; 0: kc array */
     int32_t disk_x0, disk_y0, disk_vx, disk_vy, disk_r;
     int32_t k_in, k_out;      /* k_c inside / outside the disk, >= 0 */

@@ -43,6 +43,9 @@ class Schedule:
                 self.kc_dev[e] = [None if a is None else
                                   torch.as_tensor(np.ascontiguousarray(a, dtype=np.int32)).to(sim.device)
                                   for a in arrs]
+            # the copies ran on torch's current stream; the ctx stream, which
+            # may be another one, reads the arrays from the first re-draw on
+            torch.cuda.current_stream(sim.device).synchronize()
         self.t = 0
         self.history = []
         self._epoch_set = None
