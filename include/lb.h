@@ -108,8 +108,10 @@ typedef enum {
  * One grid.  q0/q1 are caller-owned device buffers of nx*ny*nz elements of
  * the storage type, borrowed for the ctx's lifetime; q0 holds the initial
  * field.  Steps ping-pong between them; lb_current_field says which holds
- * the latest field.  |cx|+|cy|+|cz| <= 1, r >= 0, 1 <= nz <= 128,
- * nx, ny >= 2.  compute must be LB_F32, or LB_F64 with LB_F64 storage.
+ * the latest field.  |cx|+|cy|+|cz| <= 1, r >= 0, 1 <= nz <= 128 (<= 64
+ * with LB_F64 compute), nx, ny >= 1, nx*ny*nz < 2^31.  storage/compute is
+ * F64/F64, F64/F32, F32/F32 or BF16/F32, the same for every grid of a ctx,
+ * as is r.
  */
 typedef struct {
     int32_t nx, ny, nz;

@@ -116,6 +116,33 @@ def test_create_validates_the_dynamics_fields_before_touching_the_device(lbmod):
     assert "overlap" in str(e.value)
 
 
+def test_create_rejects_empty_inputs_and_sizes_out_of_range(lbmod):
+    """No grid, no VP, zero or oversized extents, an FP64-compute column
+    above 64 levels, mixed types or r across grids: each is refused with
+    EINVAL before any device work."""
+    def desc(nx=8, ny=8, nz=4, storage=lbmod.LB_F32, compute=lbmod.LB_F32, r=0.1, q0=0x1000):
+        return lbmod.lb_grid_desc(nx, ny, nz, 0.5, 0.5, 0.0, r, storage, compute,
+                                  q0, q0 + 0x1000, None, 1, 0, 0, 0, 0, 1, 1, 1)
+    whole = [(0, 0, 0, 8, 8)]
+    cases = [([], whole, "ngrids"), ([desc()], [], "VP"),
+             ([desc(nx=0)], whole, "nx"), ([desc(ny=0)], whole, "nx"),
+             ([desc(nz=0)], whole, "nz"), ([desc(nz=129)], whole, "nz"),
+             ([desc(nx=2048, ny=2048, nz=512)], whole, "nz"),
+             ([desc(nx=1 << 16, ny=1 << 16, nz=1)], whole, "2^31"),
+             ([desc(nz=65, storage=lbmod.LB_F64, compute=lbmod.LB_F64)], whole, "nz <= 64"),
+             ([desc(storage=lbmod.LB_BF16, compute=lbmod.LB_F64)], whole, "storage/compute"),
+             ([desc(), desc(storage=lbmod.LB_F64, compute=lbmod.LB_F64, q0=0x9000)],
+              whole + [(1, 0, 0, 8, 8)], "share storage"),
+             ([desc(), desc(r=0.2, q0=0x9000)], whole + [(1, 0, 0, 8, 8)], "share r")]
+    for grids, vps, word in cases:
+        with pytest.raises(lbmod.LBError) as e:
+            lbmod.lb_create(grids, vps)
+        assert e.value.status == lbmod.LB_EINVAL and word in str(e.value), (word, str(e.value))
+    with pytest.raises(lbmod.LBError) as e:
+        lbmod.lb_plan("greedy", [], 4)
+    assert e.value.status == lbmod.LB_EINVAL
+
+
 @pytest.mark.parametrize("seed", range(10))
 def test_plan_greedy_spatial_matches_oracle(lbmod, seed):
     rng = random.Random(500 + seed)
