@@ -52,10 +52,14 @@ def split_layout(vps, factor, min_side=8):
 
 
 def signature(grids, vps, kc_epoch_steps):
+    """Cache key of a workload: every grid field that changes the kernel, the
+    work or the balance (the dynamics and its weight included), the layout
+    and the re-draw interval."""
     h = hashlib.sha256()
     for g in grids:
         h.update(repr((g.nx, g.ny, g.nz, g.cx, g.cy, g.cz, g.r, g.storage, g.compute,
-                       g.kc_disk, tuple(g.disk), g.k_in, g.k_out)).encode())
+                       g.kc_disk, tuple(g.disk), g.k_in, g.k_out,
+                       getattr(g, "dynamics", 0), getattr(g, "nu", 1.0 / 7.0))).encode())
     h.update(repr(sorted(vps)).encode())
     h.update(repr(kc_epoch_steps).encode())
     return h.hexdigest()[:16]
@@ -126,7 +130,10 @@ def autotune(grids, fields, vps, kc_epochs=None, epoch_steps=0, cache=None,
         if log:
             log("split %d variant %d %-12s period %2d: %s" % (split, variant, strategy, period,
                                                             "%.3e" % v if v else "-"))
-    best = max((s for s in scores if s["value"]), key=lambda s: s["value"])
+    ok = [s for s in scores if s["value"]]
+    if not ok:
+        raise RuntimeError("autotune: no candidate ran on these grids")
+    best = max(ok, key=lambda s: s["value"])
     res = dict(best)
     res["candidates"] = scores
     if cache:

@@ -74,6 +74,23 @@ def test_autotune_split_layout_tiles():
     assert all(w >= 8 and h >= 8 for (_, _, _, w, h) in s2)
 
 
+def test_autotune_cache_key_separates_workloads():
+    """The autotuner's cache key changes with the dynamics, the layout and the
+    re-draw interval, so one workload never reuses another's result."""
+    from paper_1310_4218_gb300.autotune import signature, split_layout
+    a = get_config("lognormal_fp32_1024x1024x96")
+    b = get_config("jacobi_fp32_1024x1024x96")
+    ka = signature(a.grids, a.vps, a.kc_epoch_steps)
+    assert ka == signature(a.grids, list(reversed(a.vps)), a.kc_epoch_steps)
+    assert ka != signature(b.grids, b.vps, b.kc_epoch_steps)
+    import dataclasses
+    g = a.grids[0]
+    assert ka != signature([dataclasses.replace(g, dynamics=1)], a.vps, a.kc_epoch_steps)
+    assert ka != signature([dataclasses.replace(g, nu=0.1)], a.vps, a.kc_epoch_steps)
+    assert ka != signature(a.grids, split_layout(a.vps, 2), a.kc_epoch_steps)
+    assert ka != signature(a.grids, a.vps, 0)
+
+
 def test_jacobi_workload_is_the_lognormal_one_with_the_jacobi_sweep():
     """Same grid, VPs, k_c arrays and re-draws as the lognormal workload; the
     dynamics phase is the weighted Jacobi sweep (nu = 1/7), no advection."""
