@@ -232,8 +232,8 @@ lb_status lb_rebalance(lb_ctx *ctx, int32_t strategy, int32_t *migrations,
                        double *pred_max_over_mean);
 
 /*
- * Host-only planning with the library's balancers (no ctx, no GPU): the
- * assignment `strategy` (LB_STATIC, LB_GREEDY, LB_REFINE_SWAP,
+ * Host-only planning with the library's balancers (Sec. VI; no ctx, no
+ * GPU): the assignment `strategy` (LB_STATIC, LB_GREEDY, LB_REFINE_SWAP,
  * LB_GREEDY_SPATIAL or LB_GREEDY_BLOCKED, the last two taking the VPs in id
  * order here) produces for
  * FP64 costs[nvps] on nprocs processors.  current[nvps] is the present
@@ -246,12 +246,14 @@ lb_status lb_plan(int32_t strategy, const double *costs, int32_t nvps, int32_t n
                   int32_t *migrations, double *pred_max_over_mean);
 
 /* Replace the ctx's per-VP cost average by costs[nvps] (host, FP64, >= 0,
-   finite): lets a caller balance on a cost model instead of measurements. */
+   finite): lets a caller balance on a cost model instead of the loads
+   measured on the device (Sec. V). */
 lb_status lb_set_costs(lb_ctx *ctx, const double *costs);
 
-/* Read the current VP -> processor table (host int32[nvps]); *nprocs = number
-   of processors.  Under LB_ATOMIC_QUEUE the table of the last static-type
-   strategy is returned. */
+/* Read the current VP -> processor table (host int32[nvps]), the mapping the
+   balancers of Sec. VI rewrite (Table V prints such tables); *nprocs =
+   number of processors.  Under LB_ATOMIC_QUEUE the table of the last
+   static-type strategy is returned. */
 lb_status lb_get_assignment(lb_ctx *ctx, int32_t *vp_to_proc, int32_t *nprocs);
 
 /* Install a caller-made VP -> processor table (host int32[nvps], each in
@@ -259,7 +261,7 @@ lb_status lb_get_assignment(lb_ctx *ctx, int32_t *vp_to_proc, int32_t *nprocs);
 lb_status lb_set_assignment(lb_ctx *ctx, const int32_t *vp_to_proc);
 
 /* Point grid `grid`'s k_c source at a new device array int32[ny*nx] (the
-   load array re-drawn between segments).  The switch is enqueued on the
+   load array C(i,j) of Fig. 4 and Sec. VI-B, re-drawn between segments).  The switch is enqueued on the
    ctx stream (no synchronisation): steps enqueued after this call read the
    new array, which stays caller-owned and must stay valid while they run.
 
@@ -277,7 +279,8 @@ lb_status lb_set_assignment(lb_ctx *ctx, const int32_t *vp_to_proc);
 lb_status lb_set_kc(lb_ctx *ctx, int32_t grid, const int32_t *dev_kc);
 
 /* Compensated FP64 global sum of grid `grid` after the latest step that
-   computed one (synchronises).  sum: the sum; comp: its compensation term
+   computed one (synchronises).  A diagnostic of this library: the paper
+   prints no such quantity; conservation of the sum checks the step.  sum: the sum; comp: its compensation term
    (may be NULL). */
 lb_status lb_mass(lb_ctx *ctx, int32_t grid, double *sum, double *comp);
 
@@ -286,7 +289,9 @@ lb_status lb_mass(lb_ctx *ctx, int32_t grid, double *sum, double *comp);
 lb_status lb_mass_history(lb_ctx *ctx, int32_t grid, double *sums, int32_t max,
                           int32_t *n);
 
-/* Work done since lb_create, counted on the device (synchronises):
+/* Work done since lb_create, counted on the device (synchronises); the
+   numerator of the cell-sweep throughput this library reports (the
+   paper reports execution times, Sec. VI, Tables III-V):
    cell_sweeps = sum over steps and columns of nz * k_c (the implicit-solve
    row updates actually performed); cell_steps = sum over steps of the cells
    advanced.  Either pointer may be NULL. */
@@ -362,12 +367,13 @@ lb_status lb_device_rebalance(lb_ctx *ctx, int32_t strategy);
 lb_status lb_device_rebalance_if(lb_ctx *ctx, int32_t strategy, double threshold);
 
 /* Per-VP costs, ns per step (host double[nvps] each, may be NULL): the
-   cost average balancers use and the last measurement.  Synchronises. */
+   cost average balancers use and the last measurement (the per-object
+   loads of Sec. V).  Synchronises. */
 lb_status lb_get_costs(lb_ctx *ctx, double *avg_ns, double *last_ns);
 
 /*
- * The last *n (at most max, at most 1024 kept) device rebalances, oldest
- * first, 8 doubles each: step index, strategy applied (LB_AUTO* resolved),
+ * The last *n (at most max, at most 1024 kept) device rebalances (Sec. VI
+ * balancer calls), oldest first, 8 doubles each: step index, strategy applied (LB_AUTO* resolved),
  * migrations, predicted max/mean processor load, measured SM busy max/mean
  * of the preceding measurement, granularity floor max(max cost, mean)/mean,
  * RefineSwapLB iterations, 1 if the table was kept by
