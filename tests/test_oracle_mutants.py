@@ -2,12 +2,12 @@
 
 Each case copies the oracle, plants one plausible mistake in the copy (a
 dropped term, a wrong sign, a wrong index or a transposed operand), and runs
-every pin of test_oracle_pins.py (the step) or test_balance_oracle.py (the
-balancers) against it. At least one pin must fail, so a mistake of that kind
+every pin of test_oracle_pins.py (the step and its ctypes wrapper) or
+test_balance_oracle.py (the balancers) against it. At least one pin must fail, so a mistake of that kind
 in the oracle itself could not pass the pins unnoticed. Everything runs on
 the CPU: the C step is compiled from a mutated copy of lb_oracle.c into a
-temporary library, and the balancers are executed from a mutated copy of
-balance.py. An unmutated copy, built and run the same way, must pass every
+temporary library, and the wrapper and the balancers are executed from
+mutated copies of step.py and balance.py. An unmutated copy, built and run the same way, must pass every
 pin; that guards against a harness fault being counted as a kill.
 
 No mutant indexes outside its arrays: each either keeps its indexes in
@@ -30,6 +30,7 @@ ostep = importlib.import_module("oracle.step")   # the package's `step` is a fun
 ORACLE_DIR = os.path.dirname(os.path.abspath(ostep.__file__))
 C_SRC = os.path.join(ORACLE_DIR, "lb_oracle.c")
 PY_SRC = os.path.join(ORACLE_DIR, "balance.py")
+WRAP_SRC = os.path.join(ORACLE_DIR, "step.py")
 
 # (name, text in lb_oracle.c, replacement)
 C_MUTANTS = [
@@ -102,6 +103,16 @@ C_MUTANTS = [
     ("jacobi_x_plus_is_self", "ip = wrap(ip, nx);", "ip = wrap(i, nx);"),
     ("dynamics_dispatch_inverted", "if (g->dynamics == 1) orc_jacobi",
      "if (g->dynamics != 1) orc_jacobi"),
+]
+
+# (name, text in step.py, replacement): the marshalling between numpy and C
+WRAP_MUTANTS = [
+    ("grid_disk_velocity_swapped", "kc, x0, y0, vx, vy, R,", "kc, x0, y0, vy, vx, R,"),
+    ("grid_k_in_k_out_swapped", "self.k_in, self.k_out, self.dynamics, self.nu",
+     "self.k_out, self.k_in, self.dynamics, self.nu"),
+    ("window_x_wraps_by_ny", "ii = np.arange(i0, i0 + wx) % g.nx",
+     "ii = np.arange(i0, i0 + wx) % g.ny"),
+    ("run_drops_per_step_kc", "        kcp = kc_fields.ctypes.data\n", "        pass\n"),
 ]
 
 # (name, text in balance.py, replacement)
@@ -198,6 +209,26 @@ def _use_balance_source(monkeypatch, src):
             monkeypatch.setattr(B, name, ns[name])
 
 
+def _use_wrapper_source(monkeypatch, src):
+    """Replace the oracle's public step functions (and the grid class the
+    pins imported by name) by their definitions in src; the copy drives the
+    unmutated C library."""
+    ns = {"__name__": "oracle.step", "__file__": WRAP_SRC}
+    exec(compile(src, "step_copy.py", "exec"), ns)
+    import oracle
+    for name in ("OracleGrid", "kc_field", "thomas", "advect", "jacobi", "step", "run",
+                 "run_window", "compensated_sum"):
+        monkeypatch.setattr(oracle, name, ns[name])
+        if hasattr(test_oracle_pins, name):
+            monkeypatch.setattr(test_oracle_pins, name, ns[name])
+
+
+@pytest.fixture(scope="module")
+def wrap_source():
+    with open(WRAP_SRC) as f:
+        return f.read()
+
+
 @pytest.fixture(scope="module")
 def c_source():
     with open(C_SRC) as f:
@@ -210,11 +241,14 @@ def py_source():
         return f.read()
 
 
-def test_unmutated_copies_pass_every_pin(c_source, py_source, tmp_path, monkeypatch):
+def test_unmutated_copies_pass_every_pin(c_source, wrap_source, py_source, tmp_path,
+                                         monkeypatch):
     step_cases = _pin_cases(test_oracle_pins)
     bal_cases = _pin_cases(test_balance_oracle)
     assert len(step_cases) >= 40 and len(bal_cases) >= 100
     _use_c_library(monkeypatch, _build_c(c_source, str(tmp_path / "liborc_copy.so")))
+    assert _first_failing_pin(step_cases) is None
+    _use_wrapper_source(monkeypatch, wrap_source)
     assert _first_failing_pin(step_cases) is None
     _use_balance_source(monkeypatch, py_source)
     assert _first_failing_pin(bal_cases) is None
@@ -233,3 +267,10 @@ def test_balancer_pins_catch_planted_mistake(name, before, after, py_source, mon
     _use_balance_source(monkeypatch, _mutate(py_source, before, after))
     assert _first_failing_pin(_pin_cases(test_balance_oracle)) is not None, \
         "no pin fails with the mistake %r planted in the balancer oracle" % name
+
+
+@pytest.mark.parametrize("name,before,after", WRAP_MUTANTS, ids=[m[0] for m in WRAP_MUTANTS])
+def test_wrapper_pins_catch_planted_mistake(name, before, after, wrap_source, monkeypatch):
+    _use_wrapper_source(monkeypatch, _mutate(wrap_source, before, after))
+    assert _first_failing_pin(_pin_cases(test_oracle_pins)) is not None, \
+        "no pin fails with the mistake %r planted in the oracle's wrapper" % name
