@@ -560,6 +560,8 @@ def main():
     if world > 1:
         dist.barrier()
     m = run.timed(args.steps, ClockSampler(local_rank))
+    if world > 1:
+        dist.barrier()
     ms = max_over_ranks(m["ms"])
     s = ms / 1000.0
     value = whole_job_rate(m["sweeps"], m["ms"])
