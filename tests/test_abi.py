@@ -76,6 +76,10 @@ def test_plan_rejects_bad_input(lbmod):
         lbmod.lb_plan("greedy", [1.0, -2.0], 2)
     with pytest.raises(lbmod.LBError):
         lbmod.lb_plan("queue", [1.0, 2.0], 2)
+    for cur in ([0, 2], [-1, 0]):                # a present table outside [0, nprocs)
+        with pytest.raises(lbmod.LBError) as e:
+            lbmod.lb_plan("refine_swap", [1.0, 2.0], 2, current=cur)
+        assert e.value.status == lbmod.LB_EINVAL and "current" in str(e.value)
 
 
 def test_create_rejects_invalid_layout_before_touching_the_device(lbmod):
