@@ -110,3 +110,9 @@ def test_binding_signatures_match_the_header_prototypes():
         assert len(args) == len(c_args), name
         for i, (a, c) in enumerate(zip(args, c_args)):
             assert _ctypes_class(a) == _c_class(c), "%s argument %d (%s)" % (name, i, c)
+
+
+def test_every_entry_point_has_a_wrapper_of_the_same_name():
+    """The Python binding offers each C entry point under its own name."""
+    missing = [n for n in _c_prototypes() if not callable(getattr(lb, n, None))]
+    assert missing == []
