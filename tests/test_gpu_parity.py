@@ -448,8 +448,8 @@ def test_checkpoint_resume_is_bitwise(tmp_path):
 
 def test_barrier_timeout_is_reported_and_ctx_recovers():
     """A 1 ns wait limit makes the first barrier wait give up: the kernel
-    records LB_ETIMEOUT and returns; the next synchronising call reports it;
-    the ctx then runs normally."""
+    records LB_ETIMEOUT and returns; the next synchronising call reports it,
+    and the one after finds the status word clear."""
     from paper_1310_4218_gb300 import lb
     # one VP carries 200 sweeps per column: every other processor reaches the
     # first barrier long before it and gives up after ~1 us
