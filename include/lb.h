@@ -297,7 +297,9 @@ lb_status lb_mass_history(lb_ctx *ctx, int32_t grid, double *sums, int32_t max,
    advanced.  Either pointer may be NULL. */
 lb_status lb_work_done(lb_ctx *ctx, int64_t *cell_sweeps, int64_t *cell_steps);
 
-/* Device pointer of the buffer holding grid `grid`'s latest field. */
+/* Device pointer of the ping-pong buffer that holds grid `grid`'s field
+   after every step enqueued so far (no synchronisation: the value is
+   there once those steps have finished, e.g. after lb_sync). */
 lb_status lb_current_field(lb_ctx *ctx, int32_t grid, void **dev_ptr);
 
 /*
@@ -393,7 +395,13 @@ lb_status lb_balance_history(lb_ctx *ctx, double *rows, int32_t max, int32_t *n)
 lb_status lb_graph_create_periods(lb_ctx *ctx, int32_t nsteps, int32_t strategy,
                                   int32_t nperiods, double threshold, void **graph_exec);
 
-/* Wait for all work of the ctx; report a pending device-side error. */
+/* Wait for all work enqueued on the ctx stream, then report a device-side
+   error recorded since the last report: LB_ETIMEOUT (a grid-barrier wait
+   ran out of barrier_timeout_ns), LB_ENUMERIC (a global sum was not
+   finite) or LB_ESTATE (a device balancer call found no new measurement).
+   Reporting clears the status word, so each error is reported once.  The
+   ctx stays usable: the steps of a launch that timed out leave undefined
+   field values, and later steps run normally on them. */
 lb_status lb_sync(lb_ctx *ctx);
 
 /*
@@ -427,6 +435,8 @@ typedef struct {
     int32_t pad0;
 } lb_info;
 
+/* Fill *info (fields above).  Synchronises only when a device balancer call
+   or graph replay has changed the assignment since the host last read it. */
 lb_status lb_get_info(lb_ctx *ctx, lb_info *info);
 
 /* Text of the last error of ctx (or of the last lb_create failure when ctx
