@@ -398,7 +398,8 @@ lb_status lb_graph_create_periods(lb_ctx *ctx, int32_t nsteps, int32_t strategy,
 /* Wait for all work enqueued on the ctx stream, then report a device-side
    error recorded since the last report: LB_ETIMEOUT (a grid-barrier wait
    ran out of barrier_timeout_ns), LB_ENUMERIC (a global sum was not
-   finite) or LB_ESTATE (a device balancer call found no new measurement).
+   finite) or LB_ESTATE (a device balancer call came with no step since the
+   last measurement, or before any costs).
    Reporting clears the status word, so each error is reported once.  The
    ctx stays usable: the steps of a launch that timed out leave undefined
    field values, and later steps run normally on them. */
