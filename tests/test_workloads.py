@@ -102,3 +102,21 @@ def test_jacobi_workload_is_the_lognormal_one_with_the_jacobi_sweep():
     assert (gb.dynamics, gb.nu) == (1, 1.0 / 7.0) and ga.dynamics == 0
     assert (gb.cx, gb.cy, gb.cz) == (0.0, 0.0, 0.0)
     assert np.array_equal(b.kc_array(0, 1), a.kc_array(0, 1))
+
+
+def test_headline_workload_realises_the_stated_layout_and_kc():
+    """The 1024x1024x96 lognormal workload as the design notes describe it:
+    4096 guillotine VPs with widths 8..48 in steps of 8 (x on 32-byte FP32
+    sectors), heights 8..50, mean area 256; k_c in 1..64 with mean 4.50 in
+    each of the four re-draw epochs (t = 0, 50, 100, 150), to 0.02."""
+    w = get_config("lognormal_fp32_1024x1024x96")
+    assert len(w.vps) == 4096 and covers_exactly(w.vps, 1024, 1024)
+    assert sorted({v[3] for v in w.vps}) == [8, 16, 24, 32, 40, 48]
+    hs = [v[4] for v in w.vps]
+    assert min(hs) == 8 and max(hs) == 50
+    assert layout_stats(w.vps)["area_mean"] == 256.0
+    assert w.kc_epoch_steps == 50 and w.steps == 200
+    for e in range(4):
+        k = w.kc_array(0, e)
+        assert k.shape == (1024, 1024) and k.min() == 1 and k.max() == 64
+        assert abs(float(k.mean()) - 4.50) < 0.02, (e, k.mean())
