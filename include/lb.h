@@ -475,6 +475,8 @@ void lb_destroy(lb_ctx *ctx);
  * reason in lb_last_error(NULL).  The call synchronises the stream before
  * returning.  The first call on a device looks up the array's device
  * address with that device current; make it before any stream capture.
+ * The address is cached for the life of the process: after a
+ * cudaDeviceReset of that device, do not call this entry point again.
  * Every call reuses the same array and clears the parts that must start at
  * zero; calls whose GPU work overlaps (two streams, two host threads on one
  * device) race on the array -- serialise them.

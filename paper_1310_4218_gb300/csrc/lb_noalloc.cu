@@ -16,7 +16,9 @@
 //     library, until the process exits.
 //   - The first call on a device looks up the array's device address
 //     (cudaGetSymbolAddress, with that device current) and caches it; make
-//     that first call before any stream capture.
+//     that first call before any stream capture.  The cache lives as long
+//     as the process: after a cudaDeviceReset of that device the address
+//     may change, so the entry point must not be called again.
 //   - All calls share the one array and it keeps the previous call's
 //     contents: each call clears what must start at zero.  Calls whose work
 //     overlaps on the GPU (two streams, or two host threads on one device)
