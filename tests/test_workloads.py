@@ -120,3 +120,37 @@ def test_headline_workload_realises_the_stated_layout_and_kc():
         k = w.kc_array(0, e)
         assert k.shape == (1024, 1024) and k.min() == 1 and k.max() == 64
         assert abs(float(k.mean()) - 4.50) < 0.02, (e, k.mean())
+
+
+def lane_efficiency(kc, vps, tile_w, tile_h):
+    """Sum of k_c over the columns / sum over work items of (largest k_c of
+    the item x its column slots).  Items are tile_w x tile_h tiles of each VP
+    in row-major order, or (tile_h == 0) runs of tile_w columns in the VP's
+    row-major order; a partial item at a VP edge keeps all its slots."""
+    num = den = 0
+    for (_, x0, y0, w, h) in vps:
+        b = kc[y0:y0 + h, x0:x0 + w]
+        num += int(b.sum())
+        if tile_h == 0:
+            flat = b.ravel()
+            for c in range(0, flat.size, tile_w):
+                den += int(flat[c:c + tile_w].max()) * tile_w
+        else:
+            for ty in range(0, h, tile_h):
+                for tx in range(0, w, tile_w):
+                    den += int(b[ty:ty + tile_h, tx:tx + tile_w].max()) * tile_w * tile_h
+    return num / den
+
+
+def test_solve_loop_lane_efficiency_per_item_shape():
+    """The lane-efficiency model of the k_c solve loop on the headline
+    workload (a warp loops to the largest k_c among its columns): 8x2 tiles
+    0.61, 8x4 0.52, 32-column runs 0.46, 16x1 0.44, 16x2 0.40, every re-draw
+    epoch within 0.003 of the others."""
+    w = get_config("lognormal_fp32_1024x1024x96")
+    shapes = [(8, 2), (8, 4), (32, 0), (16, 1), (16, 2)]
+    stated = [0.61, 0.52, 0.46, 0.44, 0.40]
+    per_epoch = np.array([[lane_efficiency(w.kc_array(0, e), w.vps, tw, th) for tw, th in shapes]
+                          for e in range(4)])
+    assert np.allclose(per_epoch.mean(axis=0), stated, atol=0.005), per_epoch
+    assert (per_epoch.max(axis=0) - per_epoch.min(axis=0)).max() <= 0.006, per_epoch
