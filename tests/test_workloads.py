@@ -154,3 +154,18 @@ def test_solve_loop_lane_efficiency_per_item_shape():
                           for e in range(4)])
     assert np.allclose(per_epoch.mean(axis=0), stated, atol=0.005), per_epoch
     assert (per_epoch.max(axis=0) - per_epoch.min(axis=0)).max() <= 0.006, per_epoch
+
+
+def test_stated_workload_sizes():
+    """Sizes the design notes quote: the headline workload moves 809.5 MB of
+    algorithmic bytes per time step (read and write of the FP32 field, plus
+    4 B of k_c per column), 8.095 GB per 10-step launch; the 64-grid batch
+    holds about 387 M cells."""
+    w = get_config("lognormal_fp32_1024x1024x96")
+    g = w.grids[0]
+    assert w.cells == 1024 * 1024 * 96 and g.storage == "f32" and not g.kc_disk
+    per_step = 2 * w.cells * 4 + 4 * g.nx * g.ny
+    assert round(per_step / 1e6, 1) == 809.5
+    assert round(per_step * w.period / 1e9, 3) == 8.095
+    b = get_config("batch64_fp32")
+    assert round(b.cells / 1e6) == 387
