@@ -53,6 +53,10 @@ if ROOT not in sys.path:
 
 DEFAULT_WORKLOAD = "lognormal_fp32_1024x1024x96"
 SIZEOF = {"f64": 8, "f32": 4, "bf16": 2}
+# ctxs of the end-to-end leg: while one computes, the copy engines upload the
+# next one's input and download the last one's result (three, so that a ctx's
+# download and its next upload need not wait on each other)
+E2E_RING = 3
 
 
 def parse():
@@ -79,7 +83,7 @@ def dist_env():
 
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled during the timed region:
-    one sample every 20 ms, each stamped with the host time it arrived; only
+    one sample every 10 ms, each stamped with the host time it arrived; only
     the samples inside the timed window count (the GPU runs the enqueued work
     between the start of the window and the final synchronize)."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -95,7 +99,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
-                 "--format=csv,noheader,nounits", "-lms", "20"],
+                 "--format=csv,noheader,nounits", "-lms", "10"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
@@ -147,12 +151,37 @@ class ClockSampler:
                                                 if window[0] <= t <= window[1])
                                             if window else None)}
 
+def epochs_needed(nsteps_total, epoch_steps):
+    """Re-draw epochs a run of nsteps_total time steps can ask for: every
+    step t < nsteps_total runs under epoch t // epoch_steps, and the balancer
+    call after the last step may install the array of the step that would
+    come next, epoch nsteps_total // epoch_steps (with "+pred" the new array
+    is installed before the balancer runs)."""
+    if not epoch_steps:
+        return range(0)
+    return range(nsteps_total // epoch_steps + 1)
+
+
 def kc_epochs(w, nsteps_total):
     """Device-independent k_c arrays for every re-draw epoch the run touches."""
-    if not w.kc_epoch_steps:
-        return {}
-    n = (nsteps_total + w.kc_epoch_steps - 1) // w.kc_epoch_steps
-    return {e: [w.kc_array(gi, e) for gi in range(len(w.grids))] for e in range(n)}
+    return {e: [w.kc_array(gi, e) for gi in range(len(w.grids))]
+            for e in epochs_needed(nsteps_total, w.kc_epoch_steps)}
+
+
+def total_time_steps(args, ring=None):
+    """Time steps any one ctx of the run executes at most: warm-up and timed
+    periods of the headline ctx plus its share of the end-to-end periods
+    (the end-to-end ring's other ctxs run fewer)."""
+    ring = ring or E2E_RING
+    return (args.warmup + args.steps + (args.steps + ring - 1) // ring) * args.period
+
+
+def bench_config(w, args, world):
+    """The workload as both arms name it (no run-dependent values)."""
+    return {"workload": w.name, "global_batch": len(w.grids), "period_steps": args.period,
+            "time_steps_per_step": args.period, "vps": len(w.vps), "cells": w.cells,
+            "strategy": args.strategy, "parallelism": "replicas" if world > 1 else "1gpu",
+            "l2": "fields larger than L2 (no flush)"}
 
 
 def max_over_ranks(x):
@@ -293,7 +322,7 @@ def run_reference(args, rank, world):
            "impl": "reference", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": 1000.0 * float(np.median(times)), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": w.name, "sample": desc},
+           "config": bench_config(w, args, world),
            "cpu_baseline": {"value": value, "unit": "cell-sweep updates/s", "cores": 1,
                             "kind": "oracle", "sample": desc},
            "e2e": {"value": value, "unit": "cell-sweep updates/s", "h2d_bytes_per_step": 0,
@@ -354,6 +383,8 @@ class StrategyRun:
         self.info = self.sim.info()
         self.t = 0
         self.stats = {}
+        self.timed_rows = []
+        self.name = strategy if not flags else "+".join([strategy] + parts[1:])
 
     def launches(self, t0, t1):
         """Time steps t0..t1-1 as persistent launches, split where the k_c
@@ -384,6 +415,8 @@ class StrategyRun:
         """Install the k_c arrays of epoch e (once)."""
         if e == self.kc_epoch:
             return
+        if e not in self.kc_dev:
+            raise KeyError("k_c epoch %d was not drawn (epochs 0..%d)" % (e, max(self.kc_dev)))
         for gi in range(len(self.w.grids)):
             self.lb.lb_set_kc(self.sim.ctx, gi, self.kc_dev[e][gi].data_ptr())
             self.kernels += 4 if self.predict else 1   # switch, features, fit, rescale
@@ -430,7 +463,14 @@ class StrategyRun:
             mig, pred = self.sim.rebalance(self.strategy)
             st["migrations"] = mig
             st["predicted_max_over_mean"] = pred
+        self.record(tag, st)
+
+    def record(self, tag, st):
+        """Keep one period's balance record: the latest under its tag, and
+        every timed one in order."""
         self.stats[tag] = st
+        if tag == "timed":
+            self.timed_rows.append(st)
 
     def collect(self):
         """Device mode: per-period records from the balance history."""
@@ -438,9 +478,28 @@ class StrategyRun:
             return
         rows = self.lb.lb_balance_history(self.sim.ctx)[-len(self.dev_tags):]
         for tag, r in zip(self.dev_tags, rows):
-            self.stats[tag] = {"sm_max_over_mean": float(r[4]), "granularity_floor": float(r[5]),
-                               "migrations": int(r[2]), "predicted_max_over_mean": float(r[3])}
+            self.record(tag, {"sm_max_over_mean": float(r[4]), "granularity_floor": float(r[5]),
+                              "migrations": int(r[2]), "predicted_max_over_mean": float(r[3])})
         self.dev_tags = []
+
+    def imbalance_summary(self):
+        """SM max/mean over the timed periods (mean and worst), the first
+        (static) period's, the granularity floor and the balancer's
+        predicted max/mean, from the per-period records."""
+        rows = [r for r in self.timed_rows if r.get("sm_max_over_mean") is not None]
+        out = {"strategy": self.name, "periods": len(rows)}
+        if rows:
+            sm = [r["sm_max_over_mean"] for r in rows]
+            out["sm_max_over_mean"] = float(np.mean(sm))
+            out["sm_max_over_mean_worst"] = float(np.max(sm))
+            fl = [r["granularity_floor"] for r in rows if r.get("granularity_floor")]
+            out["granularity_floor"] = float(np.max(fl)) if fl else None
+            pr = [r["predicted_max_over_mean"] for r in rows
+                  if r.get("predicted_max_over_mean") is not None]
+            out["predicted_max_over_mean"] = float(np.mean(pr)) if pr else None
+        first = self.stats.get("first", {})
+        out["first_period_sm_max_over_mean"] = first.get("sm_max_over_mean")
+        return out
 
     def warmup(self, nper):
         import torch
@@ -486,46 +545,85 @@ class StrategyRun:
                 "launches": sum(n for _, _, n in kev), "kernels": self.kernels - k0,
                 "clocks": clocks}
 
-    def end_to_end(self, fields, nper):
-        """The same periods through the public API with host buffers: every
-        period copies its input field host -> device (pinned) and its
-        result device -> host inside the timed region."""
-        import torch
-        if not all(g.storage == "f32" for g in self.w.grids):
-            return None
-        lb, sim, stream = self.lb, self.sim, self.stream
-        h_in = [torch.from_numpy(np.ascontiguousarray(f, dtype=np.float32)).pin_memory()
-                for f in fields]
-        h_out = [torch.empty_like(x).pin_memory() for x in h_in]
-        torch.cuda.synchronize(self.dev)
-        s0, _ = lb.lb_work_done(sim.ctx)
-        c0 = torch.cuda.Event(enable_timing=True)
-        c1 = torch.cuda.Event(enable_timing=True)
-        c0.record(stream)
-        for _ in range(nper):
-            with torch.cuda.stream(stream):
-                for gi in range(len(self.w.grids)):
-                    sim.field_tensor(gi).view(-1).copy_(h_in[gi].view(-1), non_blocking=True)
-            self.launches(self.t, self.t + self.P)
-            self.balance("e2e", self.t + self.P)
-            self.t += self.P
-            with torch.cuda.stream(stream):
-                for gi in range(len(self.w.grids)):
-                    h_out[gi].view(-1).copy_(sim.field_tensor(gi).view(-1), non_blocking=True)
-        c1.record(stream)
-        torch.cuda.synchronize(self.dev)
-        self.collect()
-        es = c0.elapsed_time(c1) / 1000.0
-        sw = lb.lb_work_done(sim.ctx)[0] - s0
-        nbytes = sum(x.numel() * x.element_size() for x in h_in)
-        return {"value": sw / es, "unit": "cell-sweep updates/s",
-                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
-
     def close(self):
         if self.gexec is not None:
             self.lb.lb_graph_destroy(self.sim.ctx, self.gexec)
             self.gexec = None
         self.sim.close()
+
+
+def end_to_end(ring, fields, nper, stream, dev):
+    """The benchmark step through the public API with host buffers.  Period n
+    runs on ctx n mod len(ring); all ctxs share one compute stream.  A
+    period's input is copied host -> device (pinned) on an upload stream
+    once that ctx's previous result has left the device, the period computes
+    after its upload, and its result is copied device -> host on a download
+    stream, so uploads and downloads for the other ctxs overlap the period
+    that computes.  Every copy and every period lies inside the timed
+    region (events on the compute stream, which waits for the last
+    download).  Returns the rate and the bytes each period copies."""
+    import torch
+    w = ring[0].w
+    if not all(g.storage == "f32" for g in w.grids):
+        return None
+    h_in = [torch.from_numpy(np.ascontiguousarray(f, dtype=np.float32)).pin_memory()
+            for f in fields]
+    h_out = [torch.empty_like(x).pin_memory() for x in h_in]
+    up, down = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+    torch.cuda.synchronize(dev)
+    s0 = [r.lb.lb_work_done(r.sim.ctx)[0] for r in ring]
+    k0 = [r.kernels for r in ring]
+    freed = [None] * len(ring)
+    c0 = torch.cuda.Event(enable_timing=True)
+    c1 = torch.cuda.Event(enable_timing=True)
+    c0.record(stream)
+    up.wait_stream(stream)
+    down.wait_stream(stream)
+    for n in range(nper):
+        x = n % len(ring)
+        r = ring[x]
+        if freed[x] is not None:
+            up.wait_event(freed[x])
+        with torch.cuda.stream(up):
+            for gi in range(len(w.grids)):
+                r.sim.field_tensor(gi).view(-1).copy_(h_in[gi].view(-1), non_blocking=True)
+        loaded = torch.cuda.Event()
+        loaded.record(up)
+        stream.wait_event(loaded)
+        r.launches(r.t, r.t + r.P)
+        r.balance("e2e", r.t + r.P)
+        r.t += r.P
+        done = torch.cuda.Event()
+        done.record(stream)
+        down.wait_event(done)
+        with torch.cuda.stream(down):
+            for gi in range(len(w.grids)):
+                h_out[gi].view(-1).copy_(r.sim.field_tensor(gi).view(-1), non_blocking=True)
+        freed[x] = torch.cuda.Event()
+        freed[x].record(down)
+    stream.wait_stream(up)
+    stream.wait_stream(down)
+    c1.record(stream)
+    torch.cuda.synchronize(dev)
+    es = c0.elapsed_time(c1) / 1000.0
+    sw = 0
+    for r, s in zip(ring, s0):
+        r.collect()
+        sw += r.lb.lb_work_done(r.sim.ctx)[0] - s
+    nbytes = sum(x.numel() * x.element_size() for x in h_in)
+    return {"value": sw / es, "unit": "cell-sweep updates/s",
+            "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
+            "ms_per_step": 1000.0 * es / max(nper, 1), "ctxs": len(ring),
+            "kernels": sum(r.kernels for r in ring) - sum(k0)}
+
+
+COMPARED = ("static", "static+steal", "auto", "auto+dev", "auto_spatial+steal",
+            "auto_spatial+steal+dev", "greedy_blocked+dev", "greedy_blocked+dev+pred",
+            "greedy_blocked+dev+pred+thr", "greedy_blocked+steal+dev",
+            "greedy_blocked+steal+dev+pred", "greedy_blocked+steal+dev+pred+thr",
+            "greedy_blocked+steal+dev+pred+thr+graph", "greedy_blocked+steal+dev+pred+thr+pair",
+            "greedy_blocked+steal+dev+pred+thr+twin", "greedy_blocked+steal+dev+pred+thr+tma",
+            "queue", "queue+dev")
 
 
 def main():
@@ -547,8 +645,7 @@ def main():
 
     w = get_config(args.workload)
     P = args.period
-    total_steps = (args.warmup + 2 * args.steps) * P     # warm-up, timed, end to end
-    epochs = kc_epochs(w, total_steps)
+    epochs = kc_epochs(w, total_time_steps(args))
     fields = [g.initial_field() for g in w.grids]
     kc_dev = {e: [torch.as_tensor(a).to(dev) for a in arrs] for e, arrs in epochs.items()}
     stream = torch.cuda.Stream(dev)
@@ -576,36 +673,38 @@ def main():
     peak, peak_src = roofline_peak()
     achieved = bytes_per_launch / kern_s / 1e9
     tr = load_traffic("lb_step_kernel:%s" % w.name)
+    imbalance = run.imbalance_summary()
 
     e2e = None
     if not args.no_e2e:
+        ring = [run]
         try:
-            e2e = run.end_to_end(fields, args.steps)
+            for _ in range(E2E_RING - 1):
+                r = StrategyRun(w, fields, epochs, kc_dev, args, dev, stream, args.strategy)
+                ring.append(r)
+                r.warmup(args.warmup)
+            e2e = end_to_end(ring, fields, args.steps, stream, dev)
             if e2e:
                 e2e["value"] = sum_over_ranks(e2e["value"])
         except Exception as ex:    # report, keep the device-timed line
             e2e = {"value": None, "unit": "cell-sweep updates/s", "error": repr(ex)[:200]}
-    stats = run.stats
+        for r in ring[1:]:
+            r.close()
     run.close()
 
-    # the other assignments, measured the same way (device-resident inputs)
+    # the other assignments, measured the same way (device-resident inputs):
+    # [cell-sweep updates/s, kernel ms per launch, SM max/mean over the timed
+    # periods, SM max/mean of the first (static) period]
     compare = {}
     if not args.no_compare:
-        for st in [x for x in ("static", "static+steal", "auto", "auto+dev", "auto_spatial+steal",
-                               "auto_spatial+steal+dev", "greedy_blocked+steal+dev",
-                               "greedy_blocked+steal+dev+pred",
-                               "greedy_blocked+steal+dev+pred+thr+graph",
-                               "greedy_blocked+steal+dev+pred+thr+pair",
-                               "greedy_blocked+steal+dev+pred+thr+twin",
-                               "greedy_blocked+steal+dev+pred+thr+tma", "queue", "queue+dev")
-                   if x != args.strategy]:
+        for st in [x for x in COMPARED if x != args.strategy]:
             r2 = StrategyRun(w, fields, epochs, kc_dev, args, dev, stream, st)
             r2.warmup(args.warmup)
             m2 = r2.timed(args.steps)
-            compare[st] = {"value": m2["sweeps"] / (m2["ms"] / 1000.0),
-                           "kernel_ms_per_launch": statistics.median(m2["kernel_ms"]),
-                           "sm_max_over_mean": r2.stats["timed"]["sm_max_over_mean"],
-                           "first_period_sm_max_over_mean": r2.stats["first"]["sm_max_over_mean"]}
+            sm2 = r2.imbalance_summary()
+            compare[st] = [m2["sweeps"] / (m2["ms"] / 1000.0),
+                           statistics.median(m2["kernel_ms"]),
+                           sm2.get("sm_max_over_mean"), sm2.get("first_period_sm_max_over_mean")]
             r2.close()
 
     cpu = None
@@ -615,22 +714,24 @@ def main():
                "sample": desc, "all_cores": cpu_oracle_rate_all_cores(w)}
 
     if rank == 0:
+        # the bulky comparison table first: a reader of the line's tail sees
+        # the headline's roofline, imbalance, clocks and end-to-end figures
         out = {
+            "strategies_columns": ["updates/s", "kernel ms/launch", "SM max/mean",
+                                   "first period SM max/mean"],
+            "strategies": compare,
             "metric": "cell-sweep updates/s", "value": value, "unit": "cell-sweep updates/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32" if g0.compute == "f32" else "f64",
             "data": "synthetic",
-            "config": {"workload": w.name, "global_batch": len(w.grids), "period_steps": P,
-                       "time_steps_per_step": P, "vps": len(w.vps), "cells": w.cells,
-                       "strategy": args.strategy,
-                       "parallelism": "replicas" if world > 1 else "1gpu",
-                       "l2": "fields larger than L2 (no flush)",
-                       "cell_steps_per_s": cells_all / s,
-                       "processors": info.nprocs, "threads_per_cta": info.threads_per_cta,
-                       "per_grid_cell_steps_per_s": (
-                           [g.nx * g.ny * g.nz * args.steps * P * world / s for g in w.grids]
-                           if len(w.grids) > 1 else None)},
+            "config": bench_config(w, args, world),
+            "run": {"processors": info.nprocs, "threads_per_cta": info.threads_per_cta,
+                    "cell_steps_per_s": cells_all / s,
+                    "per_grid_cell_steps_per_s": (
+                        [g.nx * g.ny * g.nz * args.steps * P * world / s for g in w.grids]
+                        if len(w.grids) > 1 else None)},
+            "cpu_baseline": cpu,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_source": peak_src,
                          "traffic": (tr["dram_bytes_per_step"] * steps_per_launch) if tr else None,
@@ -638,12 +739,10 @@ def main():
                          "kernel_ms_per_launch": kern_s * 1000.0,
                          "steps_per_launch": steps_per_launch,
                          "algorithmic_bytes_per_launch": bytes_per_launch},
-            "imbalance": stats,
-            "strategies": compare,
+            "imbalance": imbalance,
             "clocks": m["clocks"],
             "gpu_launches": m["kernels"],
             "e2e": e2e,
-            "cpu_baseline": cpu,
         }
         print(json.dumps(out), flush=True)
     if world > 1:

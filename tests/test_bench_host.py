@@ -141,3 +141,113 @@ def test_source_hash_ignores_comments_and_sees_code(tmp_path):
     assert build.source_hash(str(csrc), str(inc)) != h0
     assert build.strip_comments('a = "//x"; // c\nb = \'/\'; /* d */ c;\n') == \
         'a = "//x";\nb = \'/\';   c;'
+
+
+class _FakeLB:
+    """Records the calls StrategyRun makes; no library, no GPU."""
+    LB_ATOMIC_QUEUE = 3
+
+    def __init__(self):
+        self.kc_installs = []
+        self.rows = 0
+
+    def lb_set_kc(self, ctx, grid, ptr):
+        self.kc_installs.append((grid, ptr))
+
+    def lb_device_measure(self, ctx):
+        pass
+
+    def lb_device_rebalance_if(self, ctx, strategy, threshold):
+        self.rows += 1
+
+    def lb_graph_create_periods(self, ctx, nsteps, strategy, measure, threshold):
+        return object()
+
+    def lb_graph_launch(self, ctx, gexec):
+        self.rows += 1
+
+    def lb_balance_history(self, ctx):
+        return [[0, 7, 0, 1.0, 1.05, 1.0, 0, 0]] * self.rows
+
+
+class _FakeSim:
+    ctx = None
+
+    def __init__(self):
+        self.steps = []
+
+    def step(self, n):
+        self.steps.append(n)
+
+
+class _Arr:
+    def __init__(self, e):
+        self.e = e
+
+    def data_ptr(self):
+        return 1000 + self.e
+
+
+def _fake_run(strategy, period, epoch_steps, epochs):
+    run = object.__new__(bench.StrategyRun)
+    parts = strategy.split("+")
+    flags = set(parts[1:])
+    run.lb, run.sim = _FakeLB(), _FakeSim()
+    run.w = type("W", (), {"kc_epoch_steps": epoch_steps, "grids": [None]})()
+    run.epochs = epochs
+    run.kc_dev = {e: [_Arr(e)] for e in epochs}
+    run.dev_mode = "dev" in flags
+    run.predict = "pred" in flags and run.dev_mode
+    run.threshold = "thr" in flags and run.dev_mode
+    run.use_graph = "graph" in flags and run.dev_mode
+    run.gexec, run.kc_epoch, run.dev_tags, run.kernels = None, None, [], 0
+    run.P, run.strategy, run.t, run.stats, run.timed_rows = period, parts[0], 0, {}, []
+    run.name = strategy
+    run.info = type("Info", (), {"strategy": 3 if parts[0] == "queue" else 7})()
+    return run
+
+
+@pytest.mark.parametrize("steps,warmup", [(20, 5), (40, 3), (5, 5), (1, 3), (7, 4), (15, 0)])
+@pytest.mark.parametrize("strategy", ["greedy_blocked+steal+dev+pred+thr",
+                                      "greedy_blocked+steal+dev+pred+thr+graph",
+                                      "greedy_blocked+dev", "queue+dev"])
+def test_every_k_c_epoch_the_run_asks_for_is_drawn(monkeypatch, steps, warmup, strategy):
+    """The bench's period loop over warm-up, timed and end-to-end periods
+    (the headline ctx runs its share of the end-to-end ring) only installs
+    k_c arrays of epochs that were drawn, for any (steps, warmup); each
+    time step runs under the epoch of its index, and the balancer call
+    after a period may install the next period's array."""
+    args = args_for(monkeypatch, "--steps", str(steps), "--warmup", str(warmup))
+    epoch_steps, P = 50, args.period
+    total = bench.total_time_steps(args)
+    epochs = {e: None for e in bench.epochs_needed(total, epoch_steps)}
+    shares = [(args.steps + bench.E2E_RING - 1 - x) // bench.E2E_RING
+              for x in range(bench.E2E_RING)]
+    assert sum(shares) == args.steps
+    for x, share in enumerate(shares):
+        run = _fake_run(strategy, P, epoch_steps, epochs)
+        nper = warmup + (steps if x == 0 else 0) + share
+        for _ in range(nper):
+            run.launches(run.t, run.t + P)
+            run.balance("p", run.t + P)
+            run.t += P
+        assert run.kc_epoch in epochs
+        if not run.use_graph:
+            assert sum(run.sim.steps) == nper * P
+
+
+def test_epochs_cover_the_step_after_the_last():
+    assert list(bench.epochs_needed(450, 50)) == list(range(10))
+    assert list(bench.epochs_needed(449, 50)) == list(range(9))
+    assert list(bench.epochs_needed(0, 50)) == [0]
+    assert list(bench.epochs_needed(100, 0)) == []
+
+
+def test_reference_arm_names_the_same_workload_config(monkeypatch, capsys):
+    """Both arms print the same config object for the same arguments."""
+    monkeypatch.setattr(bench, "cpu_oracle_rate", lambda w, budget_s=12.0: (1.0, "p", 1, 0.1))
+    args = args_for(monkeypatch, "--impl", "reference", "--steps", "1", "--warmup", "0")
+    bench.run_reference(args, 0, 1)
+    d = json.loads(capsys.readouterr().out)
+    from workloads import get_config
+    assert d["config"] == bench.bench_config(get_config(args.workload), args, 1)

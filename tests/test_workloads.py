@@ -102,70 +102,3 @@ def test_jacobi_workload_is_the_lognormal_one_with_the_jacobi_sweep():
     assert (gb.dynamics, gb.nu) == (1, 1.0 / 7.0) and ga.dynamics == 0
     assert (gb.cx, gb.cy, gb.cz) == (0.0, 0.0, 0.0)
     assert np.array_equal(b.kc_array(0, 1), a.kc_array(0, 1))
-
-
-def test_headline_workload_realises_the_stated_layout_and_kc():
-    """The 1024x1024x96 lognormal workload as the design notes describe it:
-    4096 guillotine VPs with widths 8..48 in steps of 8 (x on 32-byte FP32
-    sectors), heights 8..50, mean area 256; k_c in 1..64 with mean 4.50 in
-    each of the four re-draw epochs (t = 0, 50, 100, 150), to 0.02."""
-    w = get_config("lognormal_fp32_1024x1024x96")
-    assert len(w.vps) == 4096 and covers_exactly(w.vps, 1024, 1024)
-    assert sorted({v[3] for v in w.vps}) == [8, 16, 24, 32, 40, 48]
-    hs = [v[4] for v in w.vps]
-    assert min(hs) == 8 and max(hs) == 50
-    assert layout_stats(w.vps)["area_mean"] == 256.0
-    assert w.kc_epoch_steps == 50 and w.steps == 200
-    for e in range(4):
-        k = w.kc_array(0, e)
-        assert k.shape == (1024, 1024) and k.min() == 1 and k.max() == 64
-        assert abs(float(k.mean()) - 4.50) < 0.02, (e, k.mean())
-
-
-def lane_efficiency(kc, vps, tile_w, tile_h):
-    """Sum of k_c over the columns / sum over work items of (largest k_c of
-    the item x its column slots).  Items are tile_w x tile_h tiles of each VP
-    in row-major order, or (tile_h == 0) runs of tile_w columns in the VP's
-    row-major order; a partial item at a VP edge keeps all its slots."""
-    num = den = 0
-    for (_, x0, y0, w, h) in vps:
-        b = kc[y0:y0 + h, x0:x0 + w]
-        num += int(b.sum())
-        if tile_h == 0:
-            flat = b.ravel()
-            for c in range(0, flat.size, tile_w):
-                den += int(flat[c:c + tile_w].max()) * tile_w
-        else:
-            for ty in range(0, h, tile_h):
-                for tx in range(0, w, tile_w):
-                    den += int(b[ty:ty + tile_h, tx:tx + tile_w].max()) * tile_w * tile_h
-    return num / den
-
-
-def test_solve_loop_lane_efficiency_per_item_shape():
-    """The lane-efficiency model of the k_c solve loop on the headline
-    workload (a warp loops to the largest k_c among its columns): 8x2 tiles
-    0.61, 8x4 0.52, 32-column runs 0.46, 16x1 0.44, 16x2 0.40, every re-draw
-    epoch within 0.003 of the others."""
-    w = get_config("lognormal_fp32_1024x1024x96")
-    shapes = [(8, 2), (8, 4), (32, 0), (16, 1), (16, 2)]
-    stated = [0.61, 0.52, 0.46, 0.44, 0.40]
-    per_epoch = np.array([[lane_efficiency(w.kc_array(0, e), w.vps, tw, th) for tw, th in shapes]
-                          for e in range(4)])
-    assert np.allclose(per_epoch.mean(axis=0), stated, atol=0.005), per_epoch
-    assert (per_epoch.max(axis=0) - per_epoch.min(axis=0)).max() <= 0.006, per_epoch
-
-
-def test_stated_workload_sizes():
-    """Sizes the design notes quote: the headline workload moves 809.5 MB of
-    algorithmic bytes per time step (read and write of the FP32 field, plus
-    4 B of k_c per column), 8.095 GB per 10-step launch; the 64-grid batch
-    holds about 387 M cells."""
-    w = get_config("lognormal_fp32_1024x1024x96")
-    g = w.grids[0]
-    assert w.cells == 1024 * 1024 * 96 and g.storage == "f32" and not g.kc_disk
-    per_step = 2 * w.cells * 4 + 4 * g.nx * g.ny
-    assert round(per_step / 1e6, 1) == 809.5
-    assert round(per_step * w.period / 1e9, 3) == 8.095
-    b = get_config("batch64_fp32")
-    assert round(b.cells / 1e6) == 387
