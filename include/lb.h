@@ -32,10 +32,12 @@
  *
  * Conventions for every entry point:
  *   - Returns an lb_status and never aborts or exits the process.
- *   - Device-side failures (grid-barrier timeout, non-finite sum) are
- *     recorded in a device status word and reported by the next call that
- *     synchronises (lb_measure_loads, lb_mass, lb_mass_history,
- *     lb_checkpoint, lb_sync, lb_get_costs, lb_balance_history).
+ *   - Device-side failures (grid-barrier timeout, non-finite sum) and
+ *     clamped k_c entries are recorded in device status words and reported
+ *     by the next call that synchronises (lb_measure_loads, lb_mass,
+ *     lb_mass_history, lb_checkpoint, lb_sync, lb_get_costs,
+ *     lb_balance_history); a failure is reported before a clamp, and each
+ *     once.
  *   - lb_last_error(ctx) returns a text for the last failure of that ctx.
  *   - A ctx is not thread-safe; one host thread drives it at a time.
  *   - Work is issued on the stream given to lb_create (a cudaStream_t
@@ -60,8 +62,22 @@ typedef enum {
     LB_ENUMERIC = 4,     /* the global sum of a field became NaN or Inf */
     LB_ESTATE = 5,       /* call not valid in the ctx's current state */
     LB_ENORESIDENT = 6,  /* the requested CTAs cannot all be co-resident */
-    LB_EIO = 7           /* checkpoint file could not be written or read */
+    LB_EIO = 7,          /* checkpoint file could not be written or read */
+    LB_EKCRANGE = 8      /* a k_c array held entries above LB_KC_MAX; the
+                            steps ran with those entries clamped to it */
 } lb_status;
+
+/*
+ * Largest number of k_c solves a column runs in one step.  The kernels read
+ * a k_c array entry e as min(max(e, 0), LB_KC_MAX): an array of garbage
+ * (for instance one read before its copy has landed) then bounds the
+ * launch instead of running it for hours.  A clamped entry sets a device
+ * flag that the next call that synchronises reports once as LB_EKCRANGE.
+ * The disk rule's k_in and k_out must not exceed it (LB_EINVAL).  The paper
+ * puts no limit on its load array (Sec. VI-B); this one is a safety bound
+ * of the library, far above the workloads' 64.
+ */
+#define LB_KC_MAX 1024
 
 typedef enum { LB_F64 = 0, LB_F32 = 1, LB_BF16 = 2 } lb_dtype;
 
@@ -124,12 +140,12 @@ typedef struct {
     const int32_t *kc;        /* device int32 [ny*nx] (row j, column i); read
                                  every step when kc_disk == 0, caller-owned.
                                  Each entry is that column's solve count:
-                                 entries <= 0 mean none, and the device
-                                 does not bound them, so a launch lasts as
-                                 long as its largest entry demands */
+                                 entries <= 0 mean none, entries above
+                                 LB_KC_MAX run LB_KC_MAX solves and are
+                                 reported as LB_EKCRANGE */
     int32_t kc_disk;          /* 1: moving-disk rule below; 0: kc array */
     int32_t disk_x0, disk_y0, disk_vx, disk_vy, disk_r;
-    int32_t k_in, k_out;      /* k_c inside / outside the disk, >= 0 */
+    int32_t k_in, k_out;      /* k_c inside / outside the disk, 0..LB_KC_MAX */
     int32_t dynamics;         /* the step's first phase (Sec. IV dynamics):
                                  0 upwind advection with cx, cy, cz; 1 one
                                  weighted Jacobi sweep of the 7-point stencil,
@@ -465,27 +481,36 @@ void lb_destroy(lb_ctx *ctx);
  * Arguments: grid (host struct; q0 holds the input field, q1 is the other
  * ping-pong buffer; after the call the result is in q0 when nsteps is even,
  * in q1 when odd), vps[nvps] (host, grid index 0, must tile the grid),
- * t0 (global index of the first step: moves the k_c disk), nsteps, the
- * stream, and mass_out (host, may be NULL): the compensated global sum after
- * the last step.  VPs are placed statically, contiguous runs per SM, and
- * every step runs exactly like lb_step's.
+ * opt (host, may be NULL for the defaults; barrier_timeout_ns and
+ * threads_hint are used, as lb_create uses them), t0 (global index of the
+ * first step: moves the k_c disk), nsteps, the stream, and mass_out (host,
+ * may be NULL): the compensated global sum after the last step, left
+ * unchanged when nsteps is 0.  VPs are placed statically, contiguous runs
+ * per SM; the kernel is the one lb_create chooses for the same grid, VPs
+ * and options, so the field after each call equals lb_step's bit for bit
+ * (the global sum adds the same values in another order).
  *
- * Limits: nvps <= LB_NOALLOC_MAX_VPS, work items (ceil(w*h/32) summed over
- * VPs) <= LB_NOALLOC_MAX_ITEMS; larger inputs return LB_EINVAL, with the
- * reason in lb_last_error(NULL).  The call synchronises the stream before
- * returning.  The first call on a device looks up the array's device
- * address with that device current; make it before any stream capture.
- * The address is cached for the life of the process: after a
- * cudaDeviceReset of that device, do not call this entry point again.
- * Every call reuses the same array and clears the parts that must start at
- * zero; calls whose GPU work overlaps (two streams, two host threads on one
- * device) race on the array -- serialise them.
+ * Limits: nvps <= LB_NOALLOC_MAX_VPS, work items (per VP, the item count
+ * of the chosen kernel: ceil(w*h/32) or 8x2 tiles) <= LB_NOALLOC_MAX_ITEMS,
+ * nx*ny <= LB_NOALLOC_MAX_COLUMNS (the host bitmap that checks the tiling);
+ * larger inputs return LB_EINVAL, with the reason in lb_last_error(NULL).
+ * A k_c array entry above LB_KC_MAX returns LB_EKCRANGE after the steps
+ * have run with it clamped (mass_out is written).  The call synchronises
+ * the stream before returning.  The first call on a device looks up the
+ * array's device address with that device current; make it before any
+ * stream capture.  The address is cached for the life of the process:
+ * after a cudaDeviceReset of that device, do not call this entry point
+ * again.  Every call reuses the same array and clears the parts that must
+ * start at zero; calls whose GPU work overlaps (two streams, two host
+ * threads on one device) race on the array -- serialise them.
  */
 #define LB_NOALLOC_MAX_VPS 8192
 #define LB_NOALLOC_MAX_ITEMS 65536
+#define LB_NOALLOC_MAX_COLUMNS (1 << 27)
 #define LB_NOALLOC_SCRATCH_BYTES (2u * 1024u * 1024u)
-lb_status lb_step_noalloc(const lb_grid_desc *grid, const lb_vp *vps, int32_t nvps, int64_t t0,
-                          int32_t nsteps, void *cuda_stream, double *mass_out);
+lb_status lb_step_noalloc(const lb_grid_desc *grid, const lb_vp *vps, int32_t nvps,
+                          const lb_options *opt, int64_t t0, int32_t nsteps, void *cuda_stream,
+                          double *mass_out);
 
 #ifdef __cplusplus
 }

@@ -127,34 +127,25 @@ extern "C" void lb_default_options(lb_options *opt) {
 }
 
 // ------------------------------------------------------------------ helpers
-// Pivots of the zero-flux operator M = tridiag(-r, 1+2r, -r), ends 1+r.
-// exact_nz > 0: the true table of a column of that length.  exact_nz == 0:
-// the length-independent table (every row an interior row except row 0),
-// valid for rows 0..nz-2 of any column; row nz-1 comes from last_pivot().
-static void pivots(double r, int exact_nz, double *m) {
-    for (int k = 0; k < kNzMax; ++k) {
-        double b;
-        if (exact_nz > 0 && k >= exact_nz) { m[k] = 1.0; continue; }
-        const bool last = exact_nz > 0 && k == exact_nz - 1;
-        const int nb = (k > 0 ? 1 : 0) + (last ? 0 : 1);   // neighbours of row k
-        b = 1.0 + r * nb;
-        m[k] = k == 0 ? 1.0 / b : 1.0 / (b - r * r * m[k - 1]);
-    }
-}
-
-static double last_pivot(double r, int nz) {
-    if (nz == 1) return 1.0;
-    double m = 1.0 / (1.0 + r);
-    for (int k = 1; k < nz - 1; ++k) m = 1.0 / (1.0 + 2.0 * r - r * r * m);
-    return 1.0 / (1.0 + r - r * r * m);
-}
-
 static DevBal make_devbal(lb_ctx *ctx);
 
+// The device status words: [0] the sticky failure (lb_status), [1] the k_c
+// range flag.  A failure is reported (and cleared) first, a clamp on the
+// next call.
 static lb_status check_status(lb_ctx *ctx) {
-    int32_t st = 0;
-    CK(cudaMemcpyAsync(&st, ctx->d_status, sizeof(st), cudaMemcpyDeviceToHost, ctx->stream));
+    int32_t w[2] = {0, 0};
+    CK(cudaMemcpyAsync(w, ctx->d_status, sizeof(w), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
+    const int32_t st = w[0];
+    if (st == 0 && w[1] != 0) {
+        int32_t zero = 0;
+        CK(cudaMemcpyAsync(ctx->d_status + 1, &zero, sizeof(zero), cudaMemcpyHostToDevice,
+                           ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        return fail(ctx, LB_EKCRANGE,
+                    "k_c array entries above LB_KC_MAX were clamped to it in the steps since the "
+                    "last report");
+    }
     if (st != 0) {
         int32_t zero = 0;
         CK(cudaMemcpyAsync(ctx->d_status, &zero, sizeof(zero), cudaMemcpyHostToDevice, ctx->stream));
@@ -350,39 +341,11 @@ static lb_status validate(const lb_grid_desc *grids, int32_t ngrids, const lb_vp
     if (!vps || nvps < 1) return fail(nullptr, LB_EINVAL, "need at least one VP");
     for (int g = 0; g < ngrids; ++g) {
         const lb_grid_desc &d = grids[g];
-        char buf[160];
-        std::snprintf(buf, sizeof(buf), "grid %d: ", g);
-        std::string pre(buf);
-        if (d.nx < 1 || d.ny < 1 || d.nz < 1 || d.nz > kNzMax)
-            return fail(nullptr, LB_EINVAL, pre + "need nx, ny >= 1 and 1 <= nz <= 128");
-        if ((long long)d.nx * d.ny * d.nz >= (1LL << 31))
-            return fail(nullptr, LB_EINVAL, pre + "nx*ny*nz must be below 2^31");
-        if (d.dynamics != 0 && d.dynamics != 1)
-            return fail(nullptr, LB_EINVAL, pre + "dynamics is 0 (advection) or 1 (Jacobi)");
-        if (d.pad0 != 0) return fail(nullptr, LB_EINVAL, pre + "pad0 must be 0");
-        if (d.dynamics == 0 &&
-            (!std::isfinite(d.cx) || !std::isfinite(d.cy) || !std::isfinite(d.cz) ||
-             std::fabs(d.cx) + std::fabs(d.cy) + std::fabs(d.cz) > 1.0 + 1e-12))
-            return fail(nullptr, LB_EINVAL, pre + "need |cx|+|cy|+|cz| <= 1");
-        if (d.dynamics == 1 && !(d.nu > 0.0 && d.nu <= 1.0 / 6.0 + 1e-15))
-            return fail(nullptr, LB_EINVAL, pre + "Jacobi weight needs 0 < nu <= 1/6");
-        if (!std::isfinite(d.r) || d.r < 0.0) return fail(nullptr, LB_EINVAL, pre + "need r >= 0");
-        const bool ok_types = (d.storage == LB_F64 && d.compute == LB_F64) ||
-                              (d.storage == LB_F64 && d.compute == LB_F32) ||
-                              (d.storage == LB_F32 && d.compute == LB_F32) ||
-                              (d.storage == LB_BF16 && d.compute == LB_F32);
-        if (!ok_types) return fail(nullptr, LB_EINVAL, pre + "unsupported storage/compute pair");
+        const std::string pre = "grid " + std::to_string(g) + ": ";
+        if (const char *why = check_grid_desc(d)) return fail(nullptr, LB_EINVAL, pre + why);
         if (d.storage != grids[0].storage || d.compute != grids[0].compute)
             return fail(nullptr, LB_EINVAL, pre + "all grids must share storage and compute");
         if (d.r != grids[0].r) return fail(nullptr, LB_EINVAL, pre + "all grids must share r");
-        if (!d.q0 || !d.q1 || d.q0 == d.q1)
-            return fail(nullptr, LB_EINVAL, pre + "q0 and q1 must be distinct device buffers");
-        if (d.kc_disk != 0 && d.kc_disk != 1) return fail(nullptr, LB_EINVAL, pre + "kc_disk is 0 or 1");
-        if (!d.kc_disk && !d.kc) return fail(nullptr, LB_EINVAL, pre + "kc array required");
-        if (d.kc_disk && (d.k_in < 0 || d.k_out < 0 || d.disk_r < 0))
-            return fail(nullptr, LB_EINVAL, pre + "disk needs k_in, k_out, R >= 0");
-        if (d.compute == LB_F64 && d.nz > 64)
-            return fail(nullptr, LB_EINVAL, pre + "FP64 compute supports nz <= 64");
     }
     // the VPs must tile every grid exactly
     std::vector<std::vector<unsigned char>> cover(ngrids);
@@ -446,39 +409,10 @@ extern "C" lb_status lb_create(const lb_grid_desc *grids, int32_t ngrids, const 
         return bail(LB_ENORESIDENT);
     }
 
-    // kernel variant
-    int nzmax = 0, nzmin = kNzMax;
-    for (auto &d : ctx->grids) {
-        nzmax = std::max(nzmax, d.nz);
-        nzmin = std::min(nzmin, d.nz);
-    }
+    // kernel variant: twin halves on wide layouts and for the Jacobi sweep
+    // (where the FP32 pivots converge), else split columns on half-warps
     const bool staged = ctx->opt.staged_loads && staged_eligible(ctx->grids);
-    // wide: at least 3/4 of the columns lie in VPs whose width is a multiple
-    // of 16 (32-column work items then idle few lanes)
-    long long cols_all = 0, cols_wide = 0;
-    for (int v = 0; v < nvps; ++v) {
-        const long long c = (long long)vps[v].w * vps[v].h;
-        cols_all += c;
-        if (vps[v].w % 16 == 0) cols_wide += c;
-    }
-    bool any_jacobi = false;
-    for (const auto &d : ctx->grids) any_jacobi = any_jacobi || d.dynamics == 1;
-    // the twin kernels are the default on wide layouts, and for the Jacobi
-    // sweep (seven loads per value favour 32 columns of one level per
-    // instruction over narrow tiles)
-    const bool wide = 4 * cols_wide >= 3 * cols_all || any_jacobi;
-    // twin kernels: the FP32 pivots of a zero-flux end must be one constant
-    // pair from level kTwinS0 on, through the longest half column
-    bool twin_ok = true;
-    {
-        double mt[kNzMax];
-        pivots(grids[0].r, 0, mt);
-        for (int k = kTwinS0; twin_ok && k < kNzMax / 2; ++k)
-            twin_ok = (float)mt[k] == (float)mt[kTwinS0] &&
-                      (float)(grids[0].r * mt[k]) == (float)(grids[0].r * mt[kTwinS0]);
-    }
-    if (!find_step_kernel(ctx->storage, ctx->compute, nzmax, nzmin, nzmax == nzmin, &ctx->kinfo,
-                          ctx->opt.threads_hint, staged, wide, twin_ok)) {
+    if (!choose_step_kernel(grids, ngrids, vps, nvps, ctx->opt.threads_hint, staged, &ctx->kinfo)) {
         ctx->err = "no kernel variant for these grids";
         return bail(LB_EINVAL);
     }
@@ -493,8 +427,7 @@ extern "C" lb_status lb_create(const lb_grid_desc *grids, int32_t ngrids, const 
         if (need > (size_t)optin || !encode_tmaps(ctx->grids, ctx->kinfo.nz_variant, maps, why)) {
             // register-load kernel instead
             maps.clear();
-            find_step_kernel(ctx->storage, ctx->compute, nzmax, nzmin, nzmax == nzmin, &ctx->kinfo,
-                             ctx->opt.threads_hint, false, wide, twin_ok);
+            choose_step_kernel(grids, ngrids, vps, nvps, ctx->opt.threads_hint, false, &ctx->kinfo);
         }
     }
     ctx->threads = ctx->kinfo.threads;
@@ -537,72 +470,13 @@ extern "C" lb_status lb_create(const lb_grid_desc *grids, int32_t ngrids, const 
     }
     ctx->nbins = ctx->opt.ctas_per_sm * ctx->nsm;
 
-    // coefficients and grid table
-    const double r = grids[0].r;
-    double m[kNzMax];
-    // split kernels eliminate from both ends: the pivots of a column that
-    // starts at a zero-flux end, and the middle 2x2 coupling
-    const bool exact_table = ctx->kinfo.exact && !ctx->kinfo.split;
-    pivots(r, exact_table ? ctx->kinfo.nz_variant : 0, m);
-    for (int k = 0; k < kNzMax; ++k) {
-        ctx->coef_d.m[k] = m[k];
-        ctx->coef_d.rm[k] = r * m[k];
-        ctx->coef_f.m[k] = (float)m[k];
-        ctx->coef_f.rm[k] = (float)(r * m[k]);
-    }
-    {
-        const int h = ctx->kinfo.nz_variant / 2;
-        const double a = ctx->kinfo.split ? r * m[h - 1] : 0.0;
-        const double c = 1.0 / (1.0 - a * a);
-        ctx->coef_d.ifa = a;
-        ctx->coef_d.ifc = c;
-        ctx->coef_f.ifa = (float)a;
-        ctx->coef_f.ifc = (float)c;
-    }
+    // coefficients and grid table (the k_c range flag pointer is set once
+    // the status words exist)
+    fill_coef(grids[0].r, ctx->kinfo, ctx->coef_d);
+    fill_coef(grids[0].r, ctx->kinfo, ctx->coef_f);
     ctx->h_grids.resize(ngrids);
     for (int g = 0; g < ngrids; ++g) ctx->cells += (long long)grids[g].nx * grids[g].ny * grids[g].nz;
-    for (int g = 0; g < ngrids; ++g) {
-        const lb_grid_desc &d = grids[g];
-        GridDev &h = ctx->h_grids[g];
-        std::memset(&h, 0, sizeof(h));
-        h.nx = d.nx;
-        h.ny = d.ny;
-        h.nz = d.nz;
-        h.kc_disk = d.kc_disk;
-        h.plane = d.nx * d.ny;
-        h.sx = d.cx >= 0 ? 1 : -1;
-        h.sy = d.cy >= 0 ? 1 : -1;
-        h.sz = d.cz >= 0 ? 1 : -1;
-        h.q[0] = d.q0;
-        h.q[1] = d.q1;
-        h.kc = d.kc;
-        h.disk_x0 = d.disk_x0;
-        h.disk_y0 = d.disk_y0;
-        h.disk_vx = d.disk_vx;
-        h.disk_vy = d.disk_vy;
-        h.disk_r = d.disk_r;
-        h.k_in = d.k_in;
-        h.k_out = d.k_out;
-        const double w[4] = {1.0 - std::fabs(d.cx) - std::fabs(d.cy) - std::fabs(d.cz),
-                             std::fabs(d.cx), std::fabs(d.cy), std::fabs(d.cz)};
-        for (int n = 0; n < 4; ++n) {
-            h.wd[n] = w[n];
-            h.wf[n] = (float)w[n];
-        }
-        h.xy_only = (d.dynamics == 0 && w[0] == 0.0 && d.cz == 0.0) ? 1 : 0;
-        h.jacobi = d.dynamics == 1 ? 1 : 0;
-        h.nu_d = d.nu;
-        h.w0j_d = 1.0 - 6.0 * d.nu;
-        h.nu_f = (float)d.nu;
-        h.w0j_f = (float)(1.0 - 6.0 * d.nu);
-        h.sweeps_on = d.r > 0.0 ? 1 : 0;
-        const double ml = last_pivot(d.r, d.nz);
-        h.mlast_d = ml;
-        h.rlast_d = d.r * ml;
-        h.mlast_f = (float)ml;
-        h.rlast_f = (float)(d.r * ml);
-        if (d.nz >= 2) split_coupling(d.r, d.nz, &h.ifa_b_f, &h.ifa_t_f, &h.ifc_bt_f);
-    }
+    for (int g = 0; g < ngrids; ++g) fill_grid_dev(grids[g], nullptr, ctx->h_grids[g]);
 
     // VP table and work items
     std::vector<VPDev> hv(nvps);
@@ -625,7 +499,7 @@ extern "C" lb_status lb_create(const lb_grid_desc *grids, int32_t ngrids, const 
     if (e == cudaSuccess) e = dalloc(&ctx->d_qitems, ctx->nitems);
     if (e == cudaSuccess) e = dalloc(&ctx->d_bin_start, nb + 1);
     if (e == cudaSuccess) e = dalloc(&ctx->d_bar, 2);
-    if (e == cudaSuccess) e = dalloc(&ctx->d_status, 1);
+    if (e == cudaSuccess) e = dalloc(&ctx->d_status, 2);
     if (e == cudaSuccess) e = dalloc(&ctx->d_qhead, 2);
     if (e == cudaSuccess) e = dalloc(&ctx->d_vp_cycles, nvps);
     if (e == cudaSuccess) e = dalloc(&ctx->d_bin_busy, nb);
@@ -660,12 +534,13 @@ extern "C" lb_status lb_create(const lb_grid_desc *grids, int32_t ngrids, const 
     const std::vector<int> sp = spatial_order(ctx);
     std::vector<int32_t> sp32(sp.begin(), sp.end()), nch(ctx->vp_nchunks.begin(), ctx->vp_nchunks.end());
     cudaStream_t sm = ctx->stream;
+    for (auto &h : ctx->h_grids) h.kc_range = ctx->d_status + 1;
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(ctx->d_grids, ctx->h_grids.data(), sizeof(GridDev) * ngrids,
                             cudaMemcpyHostToDevice, sm);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(ctx->d_vps, hv.data(), sizeof(VPDev) * nvps, cudaMemcpyHostToDevice, sm);
-    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_status, 0, sizeof(int32_t), sm);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_status, 0, 2 * sizeof(int32_t), sm);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_vp_cycles, 0, sizeof(unsigned long long) * nvps, sm);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_bin_busy, 0, sizeof(unsigned long long) * nb, sm);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_mass_seq, 0, sizeof(unsigned long long), sm);

@@ -747,7 +747,7 @@ __global__ void __launch_bounds__(256) k_features(const DevBal p, int grid, cons
         int k = 0;
         if (ok) {
             const int kv = kc[(size_t)(vp.y0 + yi) * g.nx + vp.x0 + xi];
-            k = kv > 0 ? kv : 0;
+            k = kv > 0 ? (kv < LB_KC_MAX ? kv : LB_KC_MAX) : 0;   // as the step kernel reads it
         }
         for (int o = isz / 2; o > 0; o >>= 1) {
             const int k2 = __shfl_xor_sync(kFull, k, o);

@@ -26,6 +26,7 @@ struct GridDev {
     int32_t sx, sy, sz;            // upwind direction per axis (+1: neighbour at -1)
     void *q[2];                    // ping-pong fields
     const int32_t *kc;             // k_c array (kc_disk == 0)
+    int32_t *kc_range;             // set to 1 when an array entry above LB_KC_MAX was clamped
     int32_t disk_x0, disk_y0, disk_vx, disk_vy, disk_r, k_in, k_out;
     int32_t xy_only;               // w0 == 0 and wz == 0: two-neighbour stencil
     int32_t sweeps_on;             // r > 0
@@ -221,5 +222,30 @@ cudaError_t dev_kc_features(const DevBal &p, int grid, const int32_t *kc, bool i
 
 // Text returned by lb_last_error(NULL) (calls without a ctx).
 void set_ctxless_error(const char *msg);
+
+// Host set-up shared by lb_create and lb_step_noalloc (lb_setup.cpp).
+// Per-grid argument checks: nullptr when the descriptor is valid, else the
+// reason (a static string).
+const char *check_grid_desc(const lb_grid_desc &d);
+// Pivots m[kNzMax] of the zero-flux operator: exact_nz > 0, the table of a
+// column of that length; 0, the length-independent table (rows 0..nz-2 of
+// any column), the last row coming from zero_flux_last_pivot.
+void zero_flux_pivots(double r, int exact_nz, double *m);
+double zero_flux_last_pivot(double r, int nz);
+// The FP32 pivots m_s and r m_s are one constant pair from level kTwinS0 on.
+bool twin_pivots_converge(double r);
+// At least 3/4 of the columns lie in VPs whose width is a multiple of 16,
+// or a grid runs the Jacobi sweep: the twin kernels are the default.
+bool layout_is_wide(const lb_vp *vps, int nvps, bool any_jacobi);
+// The step kernel for these grids and VPs (the choice lb_create makes).
+bool choose_step_kernel(const lb_grid_desc *grids, int ngrids, const lb_vp *vps, int nvps,
+                        int threads_hint, bool staged, KernelInfo *out);
+// The pivot table and coefficients the chosen kernel reads.
+void pivots_for_kernel(double r, const KernelInfo &k, double *m);
+void fill_coef(double r, const KernelInfo &k, Coef<float> &c);
+void fill_coef(double r, const KernelInfo &k, Coef<double> &c);
+// The device record of one grid; kc_range is the device word the kernel
+// sets when it clamps a k_c array entry.
+void fill_grid_dev(const lb_grid_desc &d, int32_t *kc_range, GridDev &h);
 
 }  // namespace lbk

@@ -41,7 +41,7 @@ constexpr int kMaxVps = LB_NOALLOC_MAX_VPS;
 constexpr int kMaxItems = LB_NOALLOC_MAX_ITEMS;
 constexpr int kMaxBins = 1024;
 constexpr int kMaxDevices = 64;
-constexpr int kMaxBitmapCols = 1 << 22;
+constexpr long long kMaxColumns = LB_NOALLOC_MAX_COLUMNS;
 
 // Byte offsets of every table inside the scratch array (256-byte aligned).
 constexpr size_t al(size_t x) { return (x + 255) & ~size_t(255); }
@@ -74,7 +74,7 @@ static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 VPDev h_vps[kMaxVps];
 int2 h_items[kMaxItems];
 int32_t h_bin_start[kMaxBins + 1];
-unsigned char h_cover[kMaxBitmapCols];
+uint64_t h_cover[kMaxColumns / 64];   // one bit per column: covered by a VP
 std::mutex g_mutex;
 unsigned char *g_dev_scratch[kMaxDevices];
 
@@ -84,28 +84,26 @@ lb_status fail(lb_status s, const char *msg) {
     return s;
 }
 
-// Pivots of the zero-flux operator for a column of nz rows (exact table)
-// or the length-independent table plus the grid's last-row pivot.
-void pivot_table(double r, int exact_nz, double *m) {
-    for (int k = 0; k < kNzMax; ++k) {
-        if (exact_nz > 0 && k >= exact_nz) { m[k] = 1.0; continue; }
-        const bool last = exact_nz > 0 && k == exact_nz - 1;
-        const int nb = (k > 0 ? 1 : 0) + (last ? 0 : 1);
-        const double b = 1.0 + r * nb;
-        m[k] = k == 0 ? 1.0 / b : 1.0 / (b - r * r * m[k - 1]);
+// Marks columns [i0, i1) of row j covered; false if one of them already was.
+bool cover_row(long long row0, int i0, int i1) {
+    long long a = row0 + i0;
+    const long long b = row0 + i1;
+    while (a < b) {
+        const long long w = a >> 6;
+        const int lo = (int)(a & 63);
+        const int hi = (b - (w << 6)) >= 64 ? 64 : (int)(b - (w << 6));
+        const uint64_t mask = (hi == 64 ? ~0ull : ((1ull << hi) - 1)) & ~((1ull << lo) - 1);
+        if (h_cover[w] & mask) return false;
+        h_cover[w] |= mask;
+        a = (w + 1) << 6;
     }
-}
-
-double last_row_pivot(double r, int nz) {
-    if (nz == 1) return 1.0;
-    double m = 1.0 / (1.0 + r);
-    for (int k = 1; k < nz - 1; ++k) m = 1.0 / (1.0 + 2.0 * r - r * r * m);
-    return 1.0 / (1.0 + r - r * r * m);
+    return true;
 }
 
 template <class TC>
 cudaError_t launch_noalloc(const KernelInfo &ki, unsigned char *base, int nbins, int nvps,
-                           int nitems, long long t0, int nsteps, double r, cudaStream_t st) {
+                           int nitems, long long t0, int nsteps, double r, long long timeout_ns,
+                           cudaStream_t st) {
     StepParams<TC> p;
     std::memset(&p, 0, sizeof(p));
     p.grids = reinterpret_cast<const GridDev *>(base + kOffGrid);
@@ -121,7 +119,7 @@ cudaError_t launch_noalloc(const KernelInfo &ki, unsigned char *base, int nbins,
     p.parity0 = 0;
     p.nsteps = nsteps;
     p.t0 = t0;
-    p.timeout_ns = 2000000000LL;
+    p.timeout_ns = timeout_ns;
     p.bar = reinterpret_cast<unsigned *>(base + kOffBar);
     p.status = reinterpret_cast<int32_t *>(base + kOffStatus);
     p.qhead = reinterpret_cast<unsigned *>(base + kOffQhead);
@@ -133,15 +131,7 @@ cudaError_t launch_noalloc(const KernelInfo &ki, unsigned char *base, int nbins,
     p.mass_hist = reinterpret_cast<double *>(base + kOffMassHist);
     p.mass_t = reinterpret_cast<long long *>(base + kOffMassT);
     p.mass_seq = reinterpret_cast<unsigned long long *>(base + kOffMassSeq);
-    double m[kNzMax];
-    pivot_table(r, (ki.exact && !ki.split) ? ki.nz_variant : 0, m);
-    for (int k = 0; k < kNzMax; ++k) {
-        p.coef.m[k] = (TC)m[k];
-        p.coef.rm[k] = (TC)(r * m[k]);
-    }
-    const double a = ki.split ? r * m[ki.nz_variant / 2 - 1] : 0.0;
-    p.coef.ifa = (TC)a;
-    p.coef.ifc = (TC)(1.0 / (1.0 - a * a));
+    fill_coef(r, ki, p.coef);
     cudaLaunchConfig_t cfg;
     std::memset(&cfg, 0, sizeof(cfg));
     cfg.gridDim = dim3(nbins);
@@ -160,59 +150,44 @@ cudaError_t launch_noalloc(const KernelInfo &ki, unsigned char *base, int nbins,
 }  // namespace
 
 extern "C" lb_status lb_step_noalloc(const lb_grid_desc *grid, const lb_vp *vps, int32_t nvps,
-                                     int64_t t0, int32_t nsteps, void *cuda_stream,
-                                     double *mass_out) {
+                                     const lb_options *opt, int64_t t0, int32_t nsteps,
+                                     void *cuda_stream, double *mass_out) {
     std::lock_guard<std::mutex> lock(g_mutex);
     // sizes and layout first: nothing touches the device before they pass
     if (!grid || !vps) return fail(LB_EINVAL, "grid and vps must be non-NULL");
     if (nvps < 1 || nvps > kMaxVps) return fail(LB_EINVAL, "nvps must be in 1..LB_NOALLOC_MAX_VPS");
     if (nsteps < 0) return fail(LB_EINVAL, "nsteps < 0");
     const lb_grid_desc &d = *grid;
-    if (d.nx < 1 || d.ny < 1 || d.nz < 1 || d.nz > kNzMax)
-        return fail(LB_EINVAL, "need nx, ny >= 1 and 1 <= nz <= 128");
-    if ((long long)d.nx * d.ny * d.nz >= (1LL << 31)) return fail(LB_EINVAL, "nx*ny*nz must be below 2^31");
-    if (d.dynamics != 0 && d.dynamics != 1) return fail(LB_EINVAL, "dynamics is 0 or 1");
-    if (d.pad0 != 0) return fail(LB_EINVAL, "pad0 must be 0");
-    if (d.dynamics == 0 &&
-        (!std::isfinite(d.cx) || !std::isfinite(d.cy) || !std::isfinite(d.cz) ||
-         std::fabs(d.cx) + std::fabs(d.cy) + std::fabs(d.cz) > 1.0 + 1e-12))
-        return fail(LB_EINVAL, "need |cx|+|cy|+|cz| <= 1");
-    if (d.dynamics == 1 && !(d.nu > 0.0 && d.nu <= 1.0 / 6.0 + 1e-15))
-        return fail(LB_EINVAL, "Jacobi weight needs 0 < nu <= 1/6");
-    if (!std::isfinite(d.r) || d.r < 0.0) return fail(LB_EINVAL, "need r >= 0");
-    const bool ok_types = (d.storage == LB_F64 && (d.compute == LB_F64 || d.compute == LB_F32)) ||
-                          (d.storage == LB_F32 && d.compute == LB_F32) ||
-                          (d.storage == LB_BF16 && d.compute == LB_F32);
-    if (!ok_types) return fail(LB_EINVAL, "unsupported storage/compute pair");
-    if (d.compute == LB_F64 && d.nz > 64) return fail(LB_EINVAL, "FP64 compute supports nz <= 64");
-    if (!d.q0 || !d.q1 || d.q0 == d.q1) return fail(LB_EINVAL, "q0 and q1 must be distinct device buffers");
-    if (!d.kc_disk && !d.kc) return fail(LB_EINVAL, "kc array required");
-    if (d.kc_disk && (d.k_in < 0 || d.k_out < 0 || d.disk_r < 0))
-        return fail(LB_EINVAL, "disk needs k_in, k_out, R >= 0");
+    if (const char *why = check_grid_desc(d)) return fail(LB_EINVAL, why);
+    if ((long long)d.nx * d.ny > kMaxColumns)
+        return fail(LB_EINVAL, "nx*ny above LB_NOALLOC_MAX_COLUMNS");
+    lb_options o;
+    if (opt) o = *opt;
+    else lb_default_options(&o);
+    const long long timeout_ns = o.barrier_timeout_ns > 0 ? o.barrier_timeout_ns : 2000000000LL;
+    for (int v = 0; v < nvps; ++v) {
+        const lb_vp &p = vps[v];
+        if (p.grid != 0 || p.w < 1 || p.h < 1 || p.x0 < 0 || p.y0 < 0 || p.x0 > d.nx - p.w ||
+            p.y0 > d.ny - p.h)
+            return fail(LB_EINVAL, "a VP lies outside the grid (grid index must be 0)");
+    }
+    // the kernel lb_create would choose for this grid and layout
     KernelInfo ki;
-    if (!find_step_kernel(d.storage, d.compute, d.nz, d.nz, true, &ki))
+    if (!choose_step_kernel(&d, 1, vps, nvps, o.threads_hint, false, &ki))
         return fail(LB_EINVAL, "no kernel variant for this grid");
     long long area = 0, nitems = 0;
     for (int v = 0; v < nvps; ++v) {
-        const lb_vp &p = vps[v];
-        if (p.grid != 0 || p.w < 1 || p.h < 1 || p.x0 < 0 || p.y0 < 0 || p.x0 + p.w > d.nx ||
-            p.y0 + p.h > d.ny)
-            return fail(LB_EINVAL, "a VP lies outside the grid (grid index must be 0)");
-        area += (long long)p.w * p.h;
-        nitems += items_of_vp(ki, p.w, p.h);
+        area += (long long)vps[v].w * vps[v].h;
+        nitems += items_of_vp(ki, vps[v].w, vps[v].h);
     }
     if (area != (long long)d.nx * d.ny) return fail(LB_EINVAL, "VPs do not tile the grid");
+    // with the areas equal, no overlap means an exact tiling
+    std::memset(h_cover, 0, sizeof(uint64_t) * (size_t)(((long long)d.nx * d.ny + 63) / 64));
+    for (int v = 0; v < nvps; ++v)
+        for (int j = vps[v].y0; j < vps[v].y0 + vps[v].h; ++j)
+            if (!cover_row((long long)j * d.nx, vps[v].x0, vps[v].x0 + vps[v].w))
+                return fail(LB_EINVAL, "VPs overlap");
     if (nitems > kMaxItems) return fail(LB_EINVAL, "too many work items for LB_NOALLOC_MAX_ITEMS");
-    if ((long long)d.nx * d.ny <= kMaxBitmapCols) {
-        std::memset(h_cover, 0, (size_t)d.nx * d.ny);
-        for (int v = 0; v < nvps; ++v)
-            for (int j = vps[v].y0; j < vps[v].y0 + vps[v].h; ++j)
-                for (int i = vps[v].x0; i < vps[v].x0 + vps[v].w; ++i) {
-                    unsigned char &c = h_cover[(size_t)j * d.nx + i];
-                    if (c) return fail(LB_EINVAL, "VPs overlap");
-                    c = 1;
-                }
-    }
     if (nsteps == 0) return LB_OK;
 
     // per-device set-up: the scratch array's device address
@@ -239,44 +214,7 @@ extern "C" lb_status lb_step_noalloc(const lb_grid_desc *grid, const lb_vp *vps,
 
     // tables: grid, VPs, work items of a static contiguous placement
     GridDev g;
-    std::memset(&g, 0, sizeof(g));
-    g.nx = d.nx;
-    g.ny = d.ny;
-    g.nz = d.nz;
-    g.kc_disk = d.kc_disk;
-    g.plane = d.nx * d.ny;
-    g.sx = d.cx >= 0 ? 1 : -1;
-    g.sy = d.cy >= 0 ? 1 : -1;
-    g.sz = d.cz >= 0 ? 1 : -1;
-    g.q[0] = d.q0;
-    g.q[1] = d.q1;
-    g.kc = d.kc;
-    g.disk_x0 = d.disk_x0;
-    g.disk_y0 = d.disk_y0;
-    g.disk_vx = d.disk_vx;
-    g.disk_vy = d.disk_vy;
-    g.disk_r = d.disk_r;
-    g.k_in = d.k_in;
-    g.k_out = d.k_out;
-    const double w[4] = {1.0 - std::fabs(d.cx) - std::fabs(d.cy) - std::fabs(d.cz), std::fabs(d.cx),
-                         std::fabs(d.cy), std::fabs(d.cz)};
-    for (int n = 0; n < 4; ++n) {
-        g.wd[n] = w[n];
-        g.wf[n] = (float)w[n];
-    }
-    g.xy_only = (d.dynamics == 0 && w[0] == 0.0 && d.cz == 0.0) ? 1 : 0;
-    g.jacobi = d.dynamics == 1 ? 1 : 0;
-    g.nu_d = d.nu;
-    g.w0j_d = 1.0 - 6.0 * d.nu;
-    g.nu_f = (float)d.nu;
-    g.w0j_f = (float)(1.0 - 6.0 * d.nu);
-    g.sweeps_on = d.r > 0.0 ? 1 : 0;
-    const double ml = last_row_pivot(d.r, d.nz);
-    g.mlast_d = ml;
-    g.rlast_d = d.r * ml;
-    g.mlast_f = (float)ml;
-    g.rlast_f = (float)(d.r * ml);
-    if (d.nz >= 2) split_coupling(d.r, d.nz, &g.ifa_b_f, &g.ifa_t_f, &g.ifc_bt_f);
+    fill_grid_dev(d, reinterpret_cast<int32_t *>(base + kOffStatus) + 1, g);
     int ni = 0;
     for (int b = 0, v = 0; b < nbins; ++b) {
         h_bin_start[b] = ni;
@@ -303,18 +241,21 @@ extern "C" lb_status lb_step_noalloc(const lb_grid_desc *grid, const lb_vp *vps,
     if (e == cudaSuccess) e = cudaMemsetAsync(base + kOffZero, 0, kZeroEnd - kOffZero, st);
     if (e == cudaSuccess) {
         e = d.compute == LB_F64
-                ? launch_noalloc<double>(ki, base, nbins, nvps, ni, t0, nsteps, d.r, st)
-                : launch_noalloc<float>(ki, base, nbins, nvps, ni, t0, nsteps, d.r, st);
+                ? launch_noalloc<double>(ki, base, nbins, nvps, ni, t0, nsteps, d.r, timeout_ns, st)
+                : launch_noalloc<float>(ki, base, nbins, nvps, ni, t0, nsteps, d.r, timeout_ns, st);
     }
     // the staging arrays are reused by the next call: wait for the copies
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return fail(LB_ECUDA, cudaGetErrorString(e));
 
-    int32_t status = 0;
-    e = cudaMemcpy(&status, base + kOffStatus, sizeof(status), cudaMemcpyDeviceToHost);
+    // status words: [0] sticky failure, [1] k_c range flag (cleared by the
+    // next call's memset)
+    int32_t status[2] = {0, 0};
+    e = cudaMemcpy(status, base + kOffStatus, sizeof(status), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return fail(LB_ECUDA, cudaGetErrorString(e));
-    if (status == LB_ETIMEOUT) return fail(LB_ETIMEOUT, "grid barrier wait exceeded 2 s");
-    if (status == LB_ENUMERIC) return fail(LB_ENUMERIC, "global sum is not finite");
+    if (status[0] == LB_ETIMEOUT) return fail(LB_ETIMEOUT, "grid barrier wait exceeded barrier_timeout_ns");
+    if (status[0] == LB_ENUMERIC) return fail(LB_ENUMERIC, "global sum is not finite");
+    if (status[0] != 0) return fail((lb_status)status[0], "device reported an error");
     if (mass_out) {
         double ent[2];
         e = cudaMemcpy(ent, base + kOffMassHist + sizeof(double) * 2 * ((nsteps - 1) % kMassHist),
@@ -322,5 +263,7 @@ extern "C" lb_status lb_step_noalloc(const lb_grid_desc *grid, const lb_vp *vps,
         if (e != cudaSuccess) return fail(LB_ECUDA, cudaGetErrorString(e));
         *mass_out = ent[0] + ent[1];
     }
+    if (status[1] != 0)
+        return fail(LB_EKCRANGE, "k_c array entries above LB_KC_MAX were clamped to it");
     return LB_OK;
 }

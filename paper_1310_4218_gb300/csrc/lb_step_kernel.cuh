@@ -138,6 +138,19 @@ __device__ __forceinline__ int kc_disk(const GridDev &g, int i, int j, long long
     return d2 <= (long long)g.disk_r * g.disk_r ? g.k_in : g.k_out;
 }
 
+// k_c of column (i, j) at step t: the disk rule, or the array entry bounded
+// to 0..LB_KC_MAX; an entry above the bound also sets the grid's range flag
+// (every writer stores 1, so the race between lanes is harmless).
+__device__ __forceinline__ int kc_at(const GridDev &g, int i, int j, int oc, long long t) {
+    if (g.kc_disk) return kc_disk(g, i, j, t);
+    int k = g.kc[oc];
+    if (k > LB_KC_MAX) {
+        k = LB_KC_MAX;
+        *(volatile int32_t *)g.kc_range = 1;
+    }
+    return k > 0 ? k : 0;
+}
+
 template <class TC> __device__ __forceinline__ TC wgt(const GridDev &g, int n);
 template <> __device__ __forceinline__ float wgt<float>(const GridDev &g, int n) { return g.wf[n]; }
 template <> __device__ __forceinline__ double wgt<double>(const GridDev &g, int n) { return g.wd[n]; }
@@ -249,7 +262,7 @@ __device__ __forceinline__ int column_physics(const StepParams<TC> &p, const Gri
     const int nz = EXACT ? NZ : g.nz;
     const TS *in = static_cast<const TS *>(g.q[src]);
     const int plane = g.plane;
-    int kc = g.kc_disk ? kc_disk(g, cg.i, cg.j, t) : g.kc[cg.oc];
+    int kc = kc_at(g, cg.i, cg.j, cg.oc, t);
     if (!cg.active || !g.sweeps_on) kc = 0;
 
     // 1. advection (or the Jacobi sweep) into registers (rows >= nz: exact zeros)
@@ -422,7 +435,7 @@ __device__ __forceinline__ SplitGeom split_geom(const GridDev &g, const VPDev &v
 
 template <int NZ>
 __device__ __forceinline__ int split_kc(const GridDev &g, const SplitGeom &sg, long long t) {
-    int kc = g.kc_disk ? kc_disk(g, sg.i, sg.j, t) : g.kc[sg.oc];
+    int kc = kc_at(g, sg.i, sg.j, sg.oc, t);
     if (!sg.active || !g.sweeps_on) kc = 0;
     return kc;
 }
@@ -589,7 +602,7 @@ __device__ __forceinline__ int process_item_split_rt(const StepParams<TC> &p, co
     const TS *in = static_cast<const TS *>(g.q[src]);
     TS *out = static_cast<TS *>(g.q[src ^ 1]);
 
-    int kc = g.kc_disk ? kc_disk(g, i, j, t) : g.kc[oc];
+    int kc = kc_at(g, i, j, oc, t);
     if (!active || !g.sweeps_on) kc = 0;
 
     float2 y2[HMAX / 2];
@@ -856,7 +869,7 @@ __device__ __forceinline__ int process_item_twin(const StepParams<TC> &p, const 
     const int plane = g.plane;
     const TS *in = static_cast<const TS *>(g.q[src]);
     TS *out = static_cast<TS *>(g.q[src ^ 1]);
-    int kc = g.kc_disk ? kc_disk(g, cg.i, cg.j, t) : g.kc[cg.oc];
+    int kc = kc_at(g, cg.i, cg.j, cg.oc, t);
     if (!cg.active || !g.sweeps_on) kc = 0;
 
     float2 y2[H];                      // (level s, level NZ-1-s)
@@ -969,7 +982,7 @@ __device__ __forceinline__ int process_item_twin_rt(const StepParams<TC> &p, con
     const int hb = (nz + 1) / 2, ht = nz / 2;
     const TS *in = static_cast<const TS *>(g.q[src]);
     TS *out = static_cast<TS *>(g.q[src ^ 1]);
-    int kc = g.kc_disk ? kc_disk(g, cg.i, cg.j, t) : g.kc[cg.oc];
+    int kc = kc_at(g, cg.i, cg.j, cg.oc, t);
     if (!cg.active || !g.sweeps_on) kc = 0;
 
     float2 y2[HMAX];
@@ -1147,7 +1160,7 @@ __device__ __forceinline__ int process_item_pair(const StepParams<TC> &p, const 
     const int lstep = top ? -plane : plane;
     const TS *in = static_cast<const TS *>(g.q[src]);
     TS *out = static_cast<TS *>(g.q[src ^ 1]);
-    int kc = g.kc_disk ? kc_disk(g, i, j, t) : g.kc[oc];
+    int kc = kc_at(g, i, j, oc, t);
     if (!active || !g.sweeps_on) kc = 0;
 
     float2 y2[H / 2];

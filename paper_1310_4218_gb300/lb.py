@@ -14,13 +14,15 @@ import numpy as np
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "_build", "liblb.so")
 
-LB_OK, LB_EINVAL, LB_ECUDA, LB_ETIMEOUT, LB_ENUMERIC, LB_ESTATE, LB_ENORESIDENT, LB_EIO = range(8)
+(LB_OK, LB_EINVAL, LB_ECUDA, LB_ETIMEOUT, LB_ENUMERIC, LB_ESTATE, LB_ENORESIDENT, LB_EIO,
+ LB_EKCRANGE) = range(9)
+LB_KC_MAX = 1024
 LB_F64, LB_F32, LB_BF16 = 0, 1, 2
 (LB_STATIC, LB_GREEDY, LB_REFINE_SWAP, LB_ATOMIC_QUEUE, LB_AUTO, LB_GREEDY_SPATIAL,
  LB_AUTO_SPATIAL, LB_GREEDY_BLOCKED) = range(8)
 
 STATUS_NAMES = {0: "LB_OK", 1: "LB_EINVAL", 2: "LB_ECUDA", 3: "LB_ETIMEOUT", 4: "LB_ENUMERIC",
-                5: "LB_ESTATE", 6: "LB_ENORESIDENT", 7: "LB_EIO"}
+                5: "LB_ESTATE", 6: "LB_ENORESIDENT", 7: "LB_EIO", 8: "LB_EKCRANGE"}
 DTYPES = {"f64": LB_F64, "f32": LB_F32, "bf16": LB_BF16}
 STRATEGIES = {"static": LB_STATIC, "greedy": LB_GREEDY, "refine_swap": LB_REFINE_SWAP,
               "queue": LB_ATOMIC_QUEUE, "auto": LB_AUTO, "greedy_spatial": LB_GREEDY_SPATIAL,
@@ -104,7 +106,7 @@ _SIG = {
     "lb_graph_create_periods": (_I32, [_P, _I32, _I32, _I32, ctypes.c_double,
                                        ctypes.POINTER(_P)]),
     "lb_step_noalloc": (_I32, [ctypes.POINTER(lb_grid_desc), ctypes.POINTER(lb_vp), _I32,
-                               ctypes.c_int64, _I32, _P, _P]),
+                               _P, ctypes.c_int64, _I32, _P, _P]),
 }
 EXPORTED = tuple(_SIG)
 
@@ -333,14 +335,16 @@ def lb_destroy(ctx):
         load_library().lb_destroy(ctx)
 
 
-def lb_step_noalloc(grid, vps, t0, nsteps, stream=0, want_mass=True):
+def lb_step_noalloc(grid, vps, t0, nsteps, stream=0, want_mass=True, options=None):
     """nsteps steps of one grid with no memory allocation in the library (a
     fixed device array inside liblb.so holds every table); returns the global
-    sum after the last step, or None."""
+    sum after the last step, or None.  options: an lb_options or None (the
+    defaults)."""
     L = load_library()
     va = (lb_vp * len(vps))(*[lb_vp(*map(int, v)) for v in vps])
     m = ctypes.c_double(0.0)
-    st = L.lb_step_noalloc(ctypes.byref(grid), va, len(vps), int(t0), int(nsteps),
-                           _P(stream or 0), ctypes.addressof(m) if want_mass else None)
+    st = L.lb_step_noalloc(ctypes.byref(grid), va, len(vps),
+                           ctypes.byref(options) if options is not None else None, int(t0),
+                           int(nsteps), _P(stream or 0), ctypes.addressof(m) if want_mass else None)
     _check(st, None)
     return m.value if want_mass else None

@@ -95,3 +95,42 @@ def test_non_finite_global_sum_is_reported_once():
     assert e.value.status == lb.LB_ENUMERIC
     sim.sync()
     sim.close()
+
+
+@pytest.mark.parametrize("threads_hint", [0, 1, 2, 4])
+def test_k_c_entries_above_the_bound_are_clamped_and_reported_once(threads_hint):
+    """A k_c array with entries above LB_KC_MAX (and below 0) runs them
+    clamped to 0..LB_KC_MAX: the field equals the oracle's with the clamped
+    array, the next synchronising call reports LB_EKCRANGE, and the one
+    after that finds the flag clear.  A small grid keeps the launch short
+    (a few columns run LB_KC_MAX solves)."""
+    from paper_1310_4218_gb300 import lb
+    g = Grid(48, 32, 32, kc_disk=False)
+    q = round_to_storage(random_field(g, 34), "f32")
+    rng = np.random.default_rng(35)
+    kc = rng.integers(0, 6, size=(g.ny, g.nx)).astype(np.int32)
+    kc[3, 5] = lb.LB_KC_MAX + 1
+    kc[20, 40] = 2 ** 31 - 1
+    kc[7, 7] = -5
+    kc[9, 30] = lb.LB_KC_MAX               # at the bound: no report of its own
+    clamped = np.clip(kc, 0, lb.LB_KC_MAX)
+    from paper_1310_4218_gb300.sim import Simulation
+    o = lb.lb_default_options()
+    o.threads_hint = threads_hint
+    sim = Simulation([g], [q], regular_blocks(48, 32, 16, 8), kc_arrays=[kc], options=o)
+    sim.step(2)
+    with pytest.raises(lb.LBError) as e:
+        sim.sync()
+    assert e.value.status == lb.LB_EKCRANGE
+    sim.sync()
+    out = sim.field(0)
+    # an array within the bound reports nothing
+    sim.set_kc(0, clamped)
+    sim.step(1)
+    sim.sync()
+    out3 = sim.field(0)
+    sim.close()
+    ref, _ = oracle.run(g.oracle(clamped), q, 2)
+    assert normwise(out, ref) <= tolerance(g, 2)
+    ref3, _ = oracle.run(g.oracle(clamped), q, 3)
+    assert normwise(out3, ref3) <= tolerance(g, 3)
