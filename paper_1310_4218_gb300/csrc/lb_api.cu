@@ -431,7 +431,7 @@ extern "C" lb_status lb_create(const lb_grid_desc *grids, int32_t ngrids, const 
         }
     }
     ctx->threads = ctx->kinfo.threads;
-    ctx->dyn_smem = sizeof(double) * (size_t)(ctx->threads / kWarp) * ngrids;
+    ctx->dyn_smem = step_dyn_smem(ctx->kinfo, ngrids);
     if (ctx->kinfo.tma_slots > 0)
         ctx->dyn_smem += 128 + (size_t)ctx->kinfo.tma_slots * ctx->kinfo.tma_slot_bytes;
     if (ctx->dyn_smem > 48 * 1024) {

@@ -106,6 +106,13 @@ struct KernelInfo {
     int tma_slot_bytes; // bytes of one box
 };
 
+// Dynamic shared memory of a step launch: the per-warp global-sum partials
+// [warps][ngrids] (doubles); TMA-staged kernels add their slots at launch
+// set-up.
+inline size_t step_dyn_smem(const KernelInfo &k, int ngrids) {
+    return sizeof(double) * (size_t)(k.threads / kWarp) * (size_t)ngrids;
+}
+
 // Split kernels' work items: 8 x 2 column tiles.  A compact tile spans less
 // of a smooth k_c field than a 16 x 1 run, so its lanes' sweep counts differ
 // less (the warp runs the largest); each row of 8 FP32 columns is one

@@ -136,7 +136,7 @@ cudaError_t launch_noalloc(const KernelInfo &ki, unsigned char *base, int nbins,
     std::memset(&cfg, 0, sizeof(cfg));
     cfg.gridDim = dim3(nbins);
     cfg.blockDim = dim3(ki.threads);
-    cfg.dynamicSmemBytes = sizeof(double) * (ki.threads / kWarp);
+    cfg.dynamicSmemBytes = step_dyn_smem(ki, 1);
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;
@@ -204,10 +204,13 @@ extern "C" lb_status lb_step_noalloc(const lb_grid_desc *grid, const lb_vp *vps,
     unsigned char *base = g_dev_scratch[dev];
 
     int nsm = 0, occ = 0;
+    const size_t smem = step_dyn_smem(ki, 1);
     e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    // kernels with staged buffers take more than the default 48 KB
+    if (e == cudaSuccess && smem > 48 * 1024)
+        e = cudaFuncSetAttribute(ki.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ki.fn, ki.threads,
-                                                          sizeof(double) * (ki.threads / kWarp));
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ki.fn, ki.threads, smem);
     if (e != cudaSuccess) return fail(LB_ECUDA, cudaGetErrorString(e));
     if (occ < 1) return fail(LB_ENORESIDENT, "step kernel cannot be resident");
     const int nbins = nsm < kMaxBins ? nsm : kMaxBins;

@@ -69,6 +69,7 @@ def window_check(w, gi, q0, out, epochs, nsteps, corners, valid=8):
     errs = []
     scale = 0.0
     sq_d = sq_r = 0.0
+    window_check.per_window = []
     for (i0, j0, _), ref in zip(jobs, refs):
         r = ref[:, nsteps:nsteps + valid, nsteps:nsteps + valid]
         assert np.isfinite(r).all()
@@ -77,6 +78,7 @@ def window_check(w, gi, q0, out, epochs, nsteps, corners, valid=8):
         gpu = out[:, jj][:, :, ii]
         errs.append(float(np.abs(gpu - r).max()))
         scale = max(scale, float(np.abs(r).max()))
+        window_check.per_window.append((errs[-1], float(np.abs(r).max())))
         sq_d += float(((gpu - r) ** 2).sum())
         sq_r += float((r ** 2).sum())
     window_check.l2 = (sq_d / sq_r) ** 0.5 if sq_r > 0 else 0.0
@@ -178,3 +180,69 @@ def test_batch64_windows():
         worst = max(worst, err / scale)
     report("batch64_fp32", normwise=worst)
     assert worst <= 1e-5, worst
+
+
+def run_bench_schedule(w, q0, nsteps, strategy):
+    """The benchmark's own driver (bench.StrategyRun) on the workload: periods
+    of 10 steps, each followed by its device measurement and balancer call,
+    k_c re-drawn every 50 steps with the costs rescaled for the new array."""
+    import argparse
+
+    import bench
+    dev = torch.device("cuda", 0)
+    args = argparse.Namespace(period=10, threads=0)
+    epochs = bench.kc_epochs(w, nsteps)
+    kc_dev = {e: [torch.as_tensor(a).to(dev) for a in arrs] for e, arrs in epochs.items()}
+    stream = torch.cuda.Stream(dev)
+    run = bench.StrategyRun(w, [q0], epochs, kc_dev, args, dev, stream, strategy)
+    for _ in range(nsteps // args.period):
+        run.launches(run.t, run.t + args.period)
+        run.balance("p", run.t + args.period)
+        run.t += args.period
+    torch.cuda.synchronize(dev)
+    run.collect()
+    out = run.sim.field(0)
+    hist = run.sim.mass_history(0)
+    rows = run.lb.lb_balance_history(run.sim.ctx)
+    run.close()
+    return out, hist, epochs, rows
+
+
+def bench_schedule_corners(w, epochs):
+    """Sixteen valid-block corners: four where four VPs meet, the k_c maximum
+    of each re-draw epoch, four across the periodic seam, four seeded."""
+    vps = sorted(w.vps, key=lambda v: -(v[3] * v[4]))
+    corners = []
+    for (_, x0, y0, _, _) in vps[100:3000:725][:4]:
+        corners.append((x0 - 4, y0 - 4))
+    for e in range(4):
+        kc = epochs[e][0]
+        j, i = np.unravel_index(np.argmax(kc), kc.shape)
+        corners.append((int(i) - 4, int(j) - 4))
+    corners += [(1020, 1019), (1021, 511), (255, 1020), (1019, 1021)]
+    rng = np.random.default_rng(2024)
+    corners += [(int(a), int(b)) for a, b in rng.integers(0, 1024, size=(4, 2))]
+    return corners
+
+
+@pytest.mark.parametrize("strategy,nwin", [("greedy_blocked+steal+dev+pred+thr", 16),
+                                           ("greedy_blocked+steal+dev+pred+thr+graph", 4)])
+def test_lognormal_1024_benchmarked_schedule_windows(strategy, nwin):
+    """The headline workload (200 steps, four k_c epochs) under the schedule
+    the benchmark times -- blocked GreedyLB on device-measured costs, work
+    stealing, cost rescale at each re-draw, the 1.15 threshold -- and once
+    more replayed as one CUDA graph per period.  Oracle windows at VP
+    corners, at each epoch's k_c maximum, across the periodic seam and at
+    seeded places; each window within 1e-5 normwise."""
+    w = get_config("lognormal_fp32_1024x1024x96")
+    q0 = round_to_storage(w.grids[0].initial_field(), "f32")
+    out, hist, epochs, rows = run_bench_schedule(w, q0, w.steps, strategy)
+    assert len(rows) >= w.steps // 10
+    corners = bench_schedule_corners(w, epochs)
+    if nwin < len(corners):
+        corners = corners[4:4 + nwin]           # the k_c maxima of the four epochs
+    window_check(w, 0, q0, out, epochs, w.steps, corners)
+    for c, (err, scale) in zip(corners, window_check.per_window):
+        assert err / scale <= 1e-5, (c, err / scale)
+    step_d, _ = mass_drift(hist, oracle.compensated_sum(q0))
+    assert step_d <= 1e-8
