@@ -73,6 +73,10 @@ def parse():
     ap.add_argument("--threads", type=int, default=0, help="threads per processor (0: default)")
     ap.add_argument("--no-compare", action="store_true",
                     help="skip the side-by-side runs of the other strategies")
+    ap.add_argument("--measure-study", action="store_true",
+                    help="instead of the benchmark: per-VP costs measured concurrently with 1, 2 "
+                         "or 4 processors per SM and in serialized steps, how well each balances, "
+                         "and the throughput the serialized steps cost")
     return ap.parse_args()
 
 
@@ -617,6 +621,103 @@ def end_to_end(ring, fields, nper, stream, dev):
             "kernels": sum(r.kernels for r in ring) - sum(k0)}
 
 
+def item_work_model(w, info, kc, kappa=6.0):
+    """Cost model of the k_c work per VP: nz times the sum over the kernel's
+    work items of (kappa + the largest k_c among the item's columns), the
+    sweeps a warp runs for the item plus a fixed item overhead."""
+    out = np.zeros(len(w.vps))
+    iw, ih = info.item_w, info.item_h
+    for v, (gi, x0, y0, ww, hh) in enumerate(w.vps):
+        b = kc[y0:y0 + hh, x0:x0 + ww]
+        if ih == 0:
+            f = b.ravel()
+            mx = [f[c:c + iw].max() for c in range(0, f.size, iw)]
+        else:
+            mx = [b[ty:ty + ih, tx:tx + iw].max() for ty in range(0, hh, ih) for tx in range(0, ww, iw)]
+        out[v] = (kappa * len(mx) + float(np.sum(mx))) * w.grids[gi].nz
+    return out
+
+
+def measurement_study(args):
+    """Sec. V measures each VP's load in serialized steps because concurrent
+    GPU work timed unreliably on the paper's hardware (Table I).  Here: the
+    per-VP costs measured concurrently with 1, 2 and 4 processors (CTAs)
+    sharing each SM, and in serialized steps (one working warp per
+    processor); each cost vector's correlation with the serialized one and
+    with the k_c work model; the SM max/mean and kernel time of a period
+    balanced (blocked GreedyLB) on each; and what measuring in serialized
+    steps would cost the schedule."""
+    import torch
+
+    from paper_1310_4218_gb300 import lb
+    from paper_1310_4218_gb300.sim import Simulation
+    from workloads import get_config
+
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(dev)
+    w = get_config(args.workload)
+    P = args.period
+    kc = [w.kc_array(gi, 0) for gi in range(len(w.grids))] if w.kc_epoch_steps else None
+    fields = [g.initial_field() for g in w.grids]
+
+    def make(ctas=1):
+        o = lb.lb_default_options()
+        o.ctas_per_sm = ctas
+        return Simulation(w.grids, fields, w.vps, kc_arrays=kc, options=o, device=dev,
+                          stream=stream)
+
+    def timed(fn):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        return a.elapsed_time(b)
+
+    costs, ms, infos = {}, {}, {}
+    for mode, ctas, serial in (("concurrent, 1 processor/SM", 1, False),
+                               ("concurrent, 2 processors/SM", 2, False),
+                               ("concurrent, 4 processors/SM", 4, False),
+                               ("serialized steps", 1, True)):
+        sim = make(ctas)
+        infos[mode] = sim.info()
+        sim.step(P)
+        sim.measure()
+        if serial:
+            ms[mode] = timed(lambda: lb.lb_step_serial(sim.ctx, P)) / P
+        else:
+            ms[mode] = timed(lambda: sim.step(P)) / P
+        costs[mode] = sim.measure()[0]
+        sim.close()
+    ref = costs["serialized steps"]
+    model = item_work_model(w, infos["concurrent, 1 processor/SM"], kc[0]) if kc else None
+    out = {"study": "load measurement under concurrency (Sec. V, Table I)",
+           "workload": w.name, "period_steps": P, "modes": {}}
+    for mode, c in costs.items():
+        row = {"step_ms": ms[mode], "processors": infos[mode].nprocs,
+               "threads_per_processor": infos[mode].threads_per_cta,
+               "corr_with_serialized": float(np.corrcoef(c, ref)[0, 1]),
+               "corr_with_kc_model": float(np.corrcoef(c, model)[0, 1]) if model is not None else None}
+        # balance a fresh ctx (1 processor per SM, concurrent) on these costs
+        sim = make(1)
+        sim.step(P)
+        sim.measure()
+        sim.set_costs(c)
+        sim.rebalance("greedy_blocked")
+        row["balanced_period_kernel_ms"] = timed(lambda: sim.step(P))
+        _, busy = sim.measure()
+        used = busy[busy > 0]
+        row["balanced_sm_max_over_mean"] = float(used.max() / used.mean())
+        sim.close()
+        out["modes"][mode] = row
+    tc = ms["concurrent, 1 processor/SM"]
+    ts = ms["serialized steps"]
+    out["serialized_step_over_concurrent"] = ts / tc
+    out["period_time_with_one_serialized_step"] = (ts + (P - 1) * tc) / (P * tc)
+    print(json.dumps(out), flush=True)
+
+
 COMPARED = ("static", "static+steal", "auto", "auto+dev", "auto_spatial+steal",
             "auto_spatial+steal+dev", "greedy_blocked+dev", "greedy_blocked+dev+pred",
             "greedy_blocked+dev+pred+thr", "greedy_blocked+steal+dev",
@@ -631,6 +732,10 @@ def main():
     rank, local_rank, world = dist_env()
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.measure_study:
+        if rank == 0:
+            measurement_study(args)
         return
 
     import torch

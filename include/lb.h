@@ -163,7 +163,11 @@ typedef struct {
 } lb_vp;
 
 typedef struct {
-    int32_t ctas_per_sm;          /* processors per SM (default 1) */
+    int32_t ctas_per_sm;          /* processors per SM (default 1); with 2 or
+                                     4, FP32 grids of nz 96 on the half-warp
+                                     or twin kernels run a variant with 1/2
+                                     or 1/4 of the threads, so the SM holds
+                                     the same warps as with 1 */
     int32_t queue_order;          /* ATOMIC_QUEUE order: 0 VP id order,
                                      1 last measured cost, heaviest first */
     int32_t mass_every;           /* global sum every n-th step; 0 = never
@@ -175,10 +179,7 @@ typedef struct {
     int64_t barrier_timeout_ns;   /* grid-barrier wait limit (default 2 s) */
     int32_t threads_hint;         /* kernel variant for FP32 grids: 0 default
                                      (one lane per column with packed
-                                     twisted halves when at least 3/4 of
-                                     the columns lie in VPs whose width is
-                                     a multiple of 16, or a grid runs the
-                                     Jacobi sweep, and r lets the FP32
+                                     twisted halves when r lets the FP32
                                      pivots converge; else split columns on
                                      half-warps), 1 one lane per column, 2
                                      split columns on half-warps, 3 split
@@ -223,6 +224,17 @@ lb_status lb_create(const lb_grid_desc *grids, int32_t ngrids, const lb_vp *vps,
  * is a no-op.
  */
 lb_status lb_step(lb_ctx *ctx, int32_t nsteps);
+
+/*
+ * Like lb_step, but every processor runs its work items on one warp at a
+ * time while its other warps idle: the serialized measurement of Sec. V
+ * (Table I's synchronous mode), in which each VP's measured cost carries
+ * no interference from other work on its SM.  The results are those of
+ * lb_step; the steps are slower.  Costs read by the next
+ * lb_measure_loads include these steps.  LB_ESTATE with the TMA-staged or
+ * paired-warp kernels.
+ */
+lb_status lb_step_serial(lb_ctx *ctx, int32_t nsteps);
 
 /*
  * Synchronise the stream, read the loads accumulated since the previous
@@ -463,6 +475,38 @@ const char *lb_last_error(const lb_ctx *ctx);
 /* Free the ctx's device tables; the caller's buffers are untouched.
    Synchronises the stream first.  NULL is a no-op. */
 void lb_destroy(lb_ctx *ctx);
+
+/*
+ * Sharding across ranks (processes, one GPU each): every rank's ctx covers
+ * the whole grid, holds full-size field buffers and runs only the VPs it
+ * owns -- the paper's processors of a distributed run (Sec. III, Fig. 2),
+ * with migration of VPs between them (Sec. VI).  Between steps the ranks
+ * exchange the upwind halo columns of their VPs and move migrated VPs'
+ * columns with lb_pack_columns / lb_unpack_columns.
+ *
+ * lb_set_owned: owned[nvps] (host), 1 = this ctx runs the VP, 0 = it does
+ * not.  VPs that are not owned get no work items: their columns are not
+ * written, their costs are not measured, and the global sum (lb_mass)
+ * covers the owned columns only.  Takes effect for the next lb_step and
+ * balancer call; CUDA graphs made earlier keep the old tables, so make
+ * them again.  LB_EINVAL when no VP is owned or an entry is not 0 or 1.
+ */
+lb_status lb_set_owned(lb_ctx *ctx, const uint8_t *owned);
+
+/*
+ * Copy n columns (all nz levels) of the grid's current field into buf
+ * (pack) or from buf into the current field (unpack), on the ctx stream.
+ * cells (device int32 [n]): column indices j*nx + i.  buf (device, n*nz
+ * elements of the grid's storage type): level-major, element (k, c) at
+ * k*n + c.  Both stay caller-owned and must stay valid until the stream
+ * has passed the copy.  An index outside [0, nx*ny) is skipped on the
+ * device and reported as LB_EINVAL by the next call that synchronises;
+ * n < 0, or a NULL pointer with n > 0, returns LB_EINVAL at once.  n = 0
+ * is a no-op.
+ */
+lb_status lb_pack_columns(lb_ctx *ctx, int32_t grid, const int32_t *cells, int32_t n, void *buf);
+lb_status lb_unpack_columns(lb_ctx *ctx, int32_t grid, const int32_t *cells, int32_t n,
+                            const void *buf);
 
 /*
  * lb_step_noalloc -- nsteps time steps of one grid without allocating any

@@ -156,6 +156,10 @@ static lb_status check_status(lb_ctx *ctx) {
         if (st == LB_ESTATE)
             return fail(ctx, LB_ESTATE,
                         "device balancer: no step since the last measurement, or no costs yet");
+        if (st == LB_EINVAL)
+            return fail(ctx, LB_EINVAL,
+                        "a column index given to lb_pack_columns or lb_unpack_columns was outside "
+                        "the grid (that column was skipped)");
         return fail(ctx, (lb_status)st, "device reported an error");
     }
     return LB_OK;
@@ -412,7 +416,8 @@ extern "C" lb_status lb_create(const lb_grid_desc *grids, int32_t ngrids, const 
     // kernel variant: twin halves on wide layouts and for the Jacobi sweep
     // (where the FP32 pivots converge), else split columns on half-warps
     const bool staged = ctx->opt.staged_loads && staged_eligible(ctx->grids);
-    if (!choose_step_kernel(grids, ngrids, vps, nvps, ctx->opt.threads_hint, staged, &ctx->kinfo)) {
+    if (!choose_step_kernel(grids, ngrids, vps, nvps, ctx->opt.threads_hint, staged, &ctx->kinfo,
+                            ctx->opt.ctas_per_sm)) {
         ctx->err = "no kernel variant for these grids";
         return bail(LB_EINVAL);
     }
@@ -427,7 +432,8 @@ extern "C" lb_status lb_create(const lb_grid_desc *grids, int32_t ngrids, const 
         if (need > (size_t)optin || !encode_tmaps(ctx->grids, ctx->kinfo.nz_variant, maps, why)) {
             // register-load kernel instead
             maps.clear();
-            choose_step_kernel(grids, ngrids, vps, nvps, ctx->opt.threads_hint, false, &ctx->kinfo);
+            choose_step_kernel(grids, ngrids, vps, nvps, ctx->opt.threads_hint, false, &ctx->kinfo,
+                               ctx->opt.ctas_per_sm);
         }
     }
     ctx->threads = ctx->kinfo.threads;
@@ -596,9 +602,10 @@ extern "C" lb_status lb_create(const lb_grid_desc *grids, int32_t ngrids, const 
 
 // ------------------------------------------------------------------ step
 template <class TC>
-static lb_status launch(lb_ctx *ctx, int nsteps, const Coef<TC> &coef) {
+static lb_status launch(lb_ctx *ctx, int nsteps, const Coef<TC> &coef, int serial_warps = 0) {
     StepParams<TC> p;
     std::memset(&p, 0, sizeof(p));
+    p.serial_warps = serial_warps;
     p.grids = ctx->d_grids;
     p.vps = ctx->d_vps;
     p.items = ctx->queue_mode ? ctx->d_qitems : ctx->d_items;
@@ -650,18 +657,27 @@ static lb_status launch(lb_ctx *ctx, int nsteps, const Coef<TC> &coef) {
     return LB_OK;
 }
 
-extern "C" lb_status lb_step(lb_ctx *ctx, int32_t nsteps) {
+static lb_status step_launch(lb_ctx *ctx, int32_t nsteps, int serial_warps) {
     if (!ctx) return fail(nullptr, LB_EINVAL, "ctx is NULL");
     if (nsteps < 0) return fail(ctx, LB_EINVAL, "nsteps < 0");
     if (nsteps == 0) return LB_OK;
-    lb_status st = ctx->compute == LB_F64 ? launch<double>(ctx, nsteps, ctx->coef_d)
-                                          : launch<float>(ctx, nsteps, ctx->coef_f);
+    lb_status st = ctx->compute == LB_F64 ? launch<double>(ctx, nsteps, ctx->coef_d, serial_warps)
+                                          : launch<float>(ctx, nsteps, ctx->coef_f, serial_warps);
     if (st != LB_OK) return st;
     ctx->step += nsteps;
     ctx->cell_steps += ctx->cells * nsteps;
     ctx->parity ^= (nsteps & 1);
     ctx->steps_since_measure += nsteps;
     return LB_OK;
+}
+
+extern "C" lb_status lb_step(lb_ctx *ctx, int32_t nsteps) { return step_launch(ctx, nsteps, 0); }
+
+extern "C" lb_status lb_step_serial(lb_ctx *ctx, int32_t nsteps) {
+    if (ctx && (ctx->kinfo.tma_slots > 0 || (ctx->kinfo.tile_w == 16 && ctx->kinfo.split)))
+        return fail(ctx, LB_ESTATE,
+                    "lb_step_serial: the TMA-staged and paired-warp kernels run every warp");
+    return step_launch(ctx, nsteps, 1);
 }
 
 // ------------------------------------------------------------------ graphs
@@ -1064,6 +1080,63 @@ extern "C" lb_status lb_set_assignment(lb_ctx *ctx, const int32_t *vp_to_proc) {
     return upload_items(ctx);
 }
 
+// ------------------------------------------------------------------ sharding
+extern "C" lb_status lb_set_owned(lb_ctx *ctx, const uint8_t *owned) {
+    if (!ctx || !owned) return fail(ctx, LB_EINVAL, "lb_set_owned: bad arguments");
+    const int nv = (int)ctx->vps.size();
+    int any = 0;
+    for (int v = 0; v < nv; ++v) {
+        if (owned[v] > 1) return fail(ctx, LB_EINVAL, "lb_set_owned: entries must be 0 or 1");
+        any |= owned[v];
+    }
+    if (!any) return fail(ctx, LB_EINVAL, "lb_set_owned: no VP owned");
+    lb_status st = pull_state(ctx);
+    if (st != LB_OK) return st;
+    ctx->nitems = 0;
+    std::vector<double> f1(nv, 0.0);
+    for (int v = 0; v < nv; ++v) {
+        const lb_vp &p = ctx->vps[v];
+        ctx->vp_nchunks[v] = owned[v] ? items_of_vp(ctx->kinfo, p.w, p.h) : 0;
+        ctx->nitems += ctx->vp_nchunks[v];
+        f1[v] = (double)ctx->vp_nchunks[v] * ctx->grids[p.grid].nz;
+    }
+    std::vector<int32_t> nch(ctx->vp_nchunks.begin(), ctx->vp_nchunks.end());
+    CK(cudaMemcpyAsync(ctx->d_nchunks, nch.data(), sizeof(int32_t) * nv, cudaMemcpyHostToDevice,
+                       ctx->stream));
+    if (ctx->predict) {
+        CK(cudaMemcpyAsync(ctx->d_feat1, f1.data(), sizeof(double) * nv, cudaMemcpyHostToDevice,
+                           ctx->stream));
+        for (int g = 0; g < (int)ctx->grids.size(); ++g)
+            if (!ctx->grids[g].kc_disk)
+                CK(dev_kc_features(make_devbal(ctx), g, ctx->grids[g].kc, true, ctx->stream));
+    }
+    CK(cudaStreamSynchronize(ctx->stream));
+    return upload_items(ctx);
+}
+
+static lb_status columns(lb_ctx *ctx, bool pack, int32_t grid, const int32_t *cells, int32_t n,
+                         void *buf) {
+    if (!ctx) return fail(nullptr, LB_EINVAL, "ctx is NULL");
+    if (grid < 0 || grid >= (int)ctx->grids.size() || n < 0 || (n > 0 && (!cells || !buf)))
+        return fail(ctx, LB_EINVAL, "lb_pack_columns / lb_unpack_columns: bad arguments");
+    if (n == 0) return LB_OK;
+    const lb_grid_desc &d = ctx->grids[grid];
+    void *field = ctx->parity ? d.q1 : d.q0;
+    CK(dev_columns(pack, field, (int)dtype_size(d.storage), cells, n, d.nz, d.nx * d.ny, buf,
+                   ctx->d_status, ctx->stream));
+    return LB_OK;
+}
+
+extern "C" lb_status lb_pack_columns(lb_ctx *ctx, int32_t grid, const int32_t *cells, int32_t n,
+                                     void *buf) {
+    return columns(ctx, true, grid, cells, n, buf);
+}
+
+extern "C" lb_status lb_unpack_columns(lb_ctx *ctx, int32_t grid, const int32_t *cells, int32_t n,
+                                       const void *buf) {
+    return columns(ctx, false, grid, cells, n, const_cast<void *>(buf));
+}
+
 // ------------------------------------------------------------------ fields
 extern "C" lb_status lb_set_kc(lb_ctx *ctx, int32_t grid, const int32_t *dev_kc) {
     if (!ctx) return fail(nullptr, LB_EINVAL, "ctx is NULL");
@@ -1296,9 +1369,18 @@ extern "C" void lb_destroy(lb_ctx *ctx) {
 
 namespace lbk {
 bool find_step_kernel(int storage, int compute, int nz_max, int nz_min, bool same, KernelInfo *out,
-                      int threads_hint, bool staged, bool wide, bool twin_ok) {
-    if (storage == LB_F32 && compute == LB_F32)
-        return kernels_f32(nz_max, nz_min, same, threads_hint, staged, wide, twin_ok, out);
+                      int threads_hint, bool staged, bool wide, bool twin_ok, int ctas_per_sm) {
+    if (storage == LB_F32 && compute == LB_F32) {
+        if (!kernels_f32(nz_max, nz_min, same, threads_hint, staged, wide, twin_ok, out)) return false;
+        // processors sharing an SM: the same kernel with fewer threads
+        const bool twin = out->twin_s0 > 0;
+        const bool half = out->split && !twin && out->tile_w == kTileW && out->tma_slots == 0;
+        if (ctas_per_sm > 1 && same && (twin || half)) {
+            KernelInfo k;
+            if (kernels_f32_shared_sm(nz_max, twin, ctas_per_sm, &k)) *out = k;
+        }
+        return true;
+    }
     if (storage == LB_F64 && compute == LB_F64) return kernels_f64(nz_max, nz_min, same, out);
     if (storage == LB_F64 && compute == LB_F32) return kernels_f64s(nz_max, nz_min, same, out);
     if (storage == LB_BF16 && compute == LB_F32) return kernels_bf16(nz_max, nz_min, same, out);

@@ -721,6 +721,10 @@ __global__ void __launch_bounds__(256) k_features(const DevBal p, int grid, cons
     if (v >= p.nvps) return;                 // whole warps
     const VPDev vp = p.vps[v];
     if (vp.grid != grid) return;
+    if (p.nchunks[v] == 0) {                 // a VP this ctx does not run (lb_set_owned)
+        if (lane == 0) out[v] = 0.0;
+        return;
+    }
     const GridDev &g = p.grids[grid];
     const bool tiles = p.tile_w > 0;
     const int isz = tiles ? p.tile_w * p.tile_h : p.cols_per_item;

@@ -50,11 +50,27 @@ struct VPDev {
 
 // Thomas coefficients of the zero-flux operator for the kernel's compute
 // type: m[k] = 1/pivot_k, rm[k] = r*m[k] (FP64 values rounded once).
+//
+// Split-family kernels (half-warp, paired-warp, twin, TMA-staged) solve in
+// units of the converged pivot m_inf = lim m_k: a solve maps y to
+// M^-1 y / m_inf, whose forward elimination is q_k = e_k y_k + r m_k q_{k-1}
+// with e_k = m_k / m_inf -- exactly 1 in FP32 once the pivots have
+// converged, so the multiply drops out there -- and whose back substitution
+// (x_k = q_k + r m_k x_{k+1}) and middle 2x2 system are unchanged.  After k
+// solves the column is M^-k y / m_inf^k; the store multiplies it by
+// f[k] = m_inf^k (in the same FMA that adds back the shift).  To stay in
+// range, every resc_every solves the column is multiplied by resc =
+// m_inf^resc_every, and f[k] divides those factors out again (FP64, one
+// rounding).
 template <class TC>
 struct Coef {
     TC m[kNzMax];
     TC rm[kNzMax];
     TC ifa, ifc;   // split kernels: interface coupling a = r m_{H-1}, 1/(1-a^2)
+    TC e[kNzMax];              // forward multipliers m_k / m_inf
+    TC f[LB_KC_MAX + 1];       // f[k] = m_inf^k / resc^floor(k / resc_every)
+    TC resc;                   // m_inf^resc_every
+    int32_t resc_every;
 };
 
 template <class TC>
@@ -81,6 +97,7 @@ struct StepParams {
     unsigned long long *sweeps;    // cell-sweep updates performed (may be null)
     unsigned *bin_ctr;             // [2][nbins] per-processor item counters (stealing)
     int32_t steal;                 // 1: processors that run out take others' items
+    int32_t serial_warps;          // > 0: only this many warps per processor run items
     long long *dclock;             // [0] step index, [1] buffer parity: read at start
                                    // instead of t0/parity0, advanced at the end (may be null)
     const void *tmaps;             // TMA-staged kernels: [ngrids][2] tensor maps of the
@@ -128,9 +145,12 @@ inline int items_of_vp(const KernelInfo &k, int w, int h) {
 // wide: at least 3/4 of the columns lie in VPs whose width is a multiple of
 // 16 (the twin kernels are the default there); twin_ok: the FP32 pivots are
 // one constant pair from level kTwinS0 on (twin kernels may run).
+// ctas_per_sm > 1: a variant with 1/ctas_per_sm of the threads where one
+// exists (exact nz 96, half-warp and twin kernels), so that that many
+// processors share an SM with the same warps per SM.
 bool find_step_kernel(int storage, int compute, int nz_max, int nz_min, bool all_same_nz,
                       KernelInfo *out, int threads_hint = 0, bool staged = false,
-                      bool wide = false, bool twin_ok = false);
+                      bool wide = false, bool twin_ok = false, int ctas_per_sm = 1);
 
 // Per-type kernel tables (one translation unit each, compiled in parallel).
 bool kernels_f32(int nz_max, int nz_min, bool same, int threads_hint, bool staged, bool wide,
@@ -140,6 +160,7 @@ bool kernels_f64s(int nz_max, int nz_min, bool same, KernelInfo *out);
 bool kernels_bf16(int nz_max, int nz_min, bool same, KernelInfo *out);
 bool kernels_f32_any(int nz_max, int nz_min, int threads_hint, bool wide, bool twin_ok,
                      KernelInfo *out);
+bool kernels_f32_shared_sm(int nz, bool twin, int ctas_per_sm, KernelInfo *out);
 
 // Middle coupling of the runtime-nz split kernels for a column of nz >= 2
 // rows: lower half hb = ceil(nz/2) rows, upper ht = floor(nz/2), each
@@ -227,6 +248,11 @@ cudaError_t dev_set_kc(GridDev *g, const int32_t *kc, cudaStream_t s);
 cudaError_t dev_kc_features(const DevBal &p, int grid, const int32_t *kc, bool initial,
                             cudaStream_t s);
 
+// Column copies of a sharded run (lb_shard.cu): pack (field -> buf) or
+// unpack (buf -> field) n columns of nz levels; esize = storage bytes.
+cudaError_t dev_columns(bool pack, void *field, int esize, const int32_t *cells, int n, int nz,
+                        int plane, void *buf, int32_t *status, cudaStream_t s);
+
 // Text returned by lb_last_error(NULL) (calls without a ctx).
 void set_ctxless_error(const char *msg);
 
@@ -239,14 +265,17 @@ const char *check_grid_desc(const lb_grid_desc &d);
 // any column), the last row coming from zero_flux_last_pivot.
 void zero_flux_pivots(double r, int exact_nz, double *m);
 double zero_flux_last_pivot(double r, int nz);
-// The FP32 pivots m_s and r m_s are one constant pair from level kTwinS0 on.
+// From level kTwinS0 on, the FP32 forward multipliers m_s / m_inf are 1 and
+// r m_s is one constant (the twin kernels' packed elimination).
 bool twin_pivots_converge(double r);
+// The converged pivot m_inf of the zero-flux elimination (1 when r = 0).
+double converged_pivot(double r);
 // At least 3/4 of the columns lie in VPs whose width is a multiple of 16,
 // or a grid runs the Jacobi sweep: the twin kernels are the default.
 bool layout_is_wide(const lb_vp *vps, int nvps, bool any_jacobi);
 // The step kernel for these grids and VPs (the choice lb_create makes).
 bool choose_step_kernel(const lb_grid_desc *grids, int ngrids, const lb_vp *vps, int nvps,
-                        int threads_hint, bool staged, KernelInfo *out);
+                        int threads_hint, bool staged, KernelInfo *out, int ctas_per_sm = 1);
 // The pivot table and coefficients the chosen kernel reads.
 void pivots_for_kernel(double r, const KernelInfo &k, double *m);
 void fill_coef(double r, const KernelInfo &k, Coef<float> &c);

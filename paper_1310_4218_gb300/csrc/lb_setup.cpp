@@ -60,11 +60,23 @@ double zero_flux_last_pivot(double r, int nz) {
     return 1.0 / (1.0 + r - r * r * m);
 }
 
+double converged_pivot(double r) {
+    // fixed point of m = 1 / (1 + 2r - r^2 m), a contraction (factor (r m)^2 < 1)
+    double m = 1.0 / (1.0 + r);
+    for (int it = 0; it < 4000; ++it) {
+        const double n = 1.0 / (1.0 + 2.0 * r - r * r * m);
+        if (n == m) break;
+        m = n;
+    }
+    return m;
+}
+
 bool twin_pivots_converge(double r) {
     double mt[kNzMax];
     zero_flux_pivots(r, 0, mt);
+    const double minf = converged_pivot(r);
     for (int k = kTwinS0; k < kNzMax / 2; ++k)
-        if ((float)mt[k] != (float)mt[kTwinS0] || (float)(r * mt[k]) != (float)(r * mt[kTwinS0]))
+        if ((float)(mt[k] / minf) != 1.0f || (float)(r * mt[k]) != (float)(r * mt[kTwinS0]))
             return false;
     return true;
 }
@@ -80,7 +92,7 @@ bool layout_is_wide(const lb_vp *vps, int nvps, bool any_jacobi) {
 }
 
 bool choose_step_kernel(const lb_grid_desc *grids, int ngrids, const lb_vp *vps, int nvps,
-                        int threads_hint, bool staged, KernelInfo *out) {
+                        int threads_hint, bool staged, KernelInfo *out, int ctas_per_sm) {
     int nzmax = 0, nzmin = kNzMax;
     bool any_jacobi = false;
     for (int g = 0; g < ngrids; ++g) {
@@ -90,7 +102,7 @@ bool choose_step_kernel(const lb_grid_desc *grids, int ngrids, const lb_vp *vps,
     }
     return find_step_kernel(grids[0].storage, grids[0].compute, nzmax, nzmin, nzmax == nzmin, out,
                             threads_hint, staged, layout_is_wide(vps, nvps, any_jacobi),
-                            twin_pivots_converge(grids[0].r));
+                            twin_pivots_converge(grids[0].r), ctas_per_sm);
 }
 
 template <class TC>
@@ -106,6 +118,20 @@ static void fill_coef_t(double r, const KernelInfo &k, Coef<TC> &c) {
     const double a = k.split ? r * m[k.nz_variant / 2 - 1] : 0.0;
     c.ifa = (TC)a;
     c.ifc = (TC)(1.0 / (1.0 - a * a));
+    // scaled solves of the split family (the length-independent table)
+    const double minf = converged_pivot(r);
+    for (int i = 0; i < kNzMax; ++i) c.e[i] = (TC)(m[i] / minf);
+    // a solve grows a column by at most 1 / m_inf (M^-1 has unit row sums
+    // and nonnegative entries): rescale before the growth reaches 2^40
+    const double g = -std::log2(minf);
+    int every = g > 0.0 ? (int)std::floor(40.0 / g) : 16;
+    every = every < 1 ? 1 : (every > 16 ? 16 : every);
+    const double resc = std::pow(minf, every);
+    c.resc = (TC)resc;
+    c.resc_every = every;
+    const double lr = std::log((double)c.resc), lm = std::log(minf);
+    for (int kk = 0; kk <= LB_KC_MAX; ++kk)
+        c.f[kk] = (TC)std::exp(kk * lm - (kk / every) * lr);
 }
 
 void pivots_for_kernel(double r, const KernelInfo &k, double *m) {

@@ -4,12 +4,9 @@
 
 namespace lbk {
 
-// Exact nz 32 / 64 / 96.  Default: when the layout is wide (at least 3/4 of
-// the columns in VPs whose width is a multiple of 16, or a Jacobi grid) and
-// the FP32 pivots converge (twin_ok), one lane per column with both twisted
-// halves in packed pairs, items of 32 columns; otherwise split columns on
-// half-warps with 8 x 2 tiles (narrower items idle fewer lanes at the edges
-// of narrow VPs).  threads_hint: 1 one lane per column (plain Thomas),
+// Exact nz 32 / 64 / 96.  Default: when the FP32 pivots converge (twin_ok),
+// one lane per column with both twisted halves in packed pairs, items of 32
+// columns; otherwise split columns on half-warps with 8 x 2 tiles.  threads_hint: 1 one lane per column (plain Thomas),
 // 2 half-warps, 3 paired warps (16 x 2 tiles), 4 twin halves; `staged` the
 // TMA-staged kernels (one box slot per warp, 147-221 KB of shared memory
 // per SM).
@@ -17,8 +14,10 @@ bool kernels_f32(int nz_max, int nz_min, bool same, int threads_hint, bool stage
                  bool twin_ok, KernelInfo *out) {
     const bool one_lane = threads_hint == 1;
     const bool pair = threads_hint == 3;
-    const bool twin = twin_ok && nz_max / 2 > kTwinS0 &&
-                      (threads_hint == 4 || (threads_hint == 0 && wide));
+    // twin halves wherever the pivots allow: with the scaled solves they
+    // beat the half-warp split on narrow layouts as well
+    (void)wide;
+    const bool twin = twin_ok && nz_max / 2 > kTwinS0 && (threads_hint == 4 || threads_hint == 0);
     if (same && nz_max == 32) {
         if (one_lane) *out = kernel_entry<float, float, 32, true, 1, 512>();
         else if (staged) *out = kernel_entry_tma<32, 1024>();

@@ -4,15 +4,14 @@
 
 namespace lbk {
 
-// Default: twin halves (one lane per column) where at least 3/4 of the
-// columns lie in VPs whose width is a multiple of 16, or a grid runs the
-// Jacobi sweep, and the FP32 pivots converge; else split columns on
-// half-warps.  threads_hint 1 one lane per column (plain Thomas), 2 half-warp
+// Default: twin halves (one lane per column) where the FP32 pivots
+// converge; else split columns on half-warps.  threads_hint 1 one lane per column (plain Thomas), 2 half-warp
 // split columns, 4 twin halves where the pivots allow.
 bool kernels_f32_any(int nz_max, int nz_min, int threads_hint, bool wide, bool twin_ok,
                      KernelInfo *out) {
     const bool one_lane = threads_hint == 1;
-    const bool twin = twin_ok && nz_min >= 2 && (threads_hint == 4 || (threads_hint == 0 && wide));
+    (void)wide;
+    const bool twin = twin_ok && nz_min >= 2 && (threads_hint == 4 || threads_hint == 0);
     if (twin) {
         if (nz_max <= 32) { *out = kernel_entry<float, float, 32, false, 1, 1024, false, 0, true>(); return true; }
         if (nz_max <= 64) { *out = kernel_entry<float, float, 64, false, 1, 640, false, 0, true>(); return true; }

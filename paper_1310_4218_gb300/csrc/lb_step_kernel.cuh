@@ -464,14 +464,15 @@ __device__ __forceinline__ int split_finish(const StepParams<TC> &p, const GridD
     }
     const Coef<TC> &cf = p.coef;
     const int kmax = __reduce_max_sync(0xffffffffu, (unsigned)kc);
+    int rc = cf.resc_every;
     for (int r = 0; r < kmax; ++r) {
         const bool act = r < kc;
         if (act) {
-            float pp = y[0] * cf.m[0];
+            float pp = y[0] * cf.e[0];
             y[0] = pp;
 #pragma unroll
             for (int s = 1; s < H; ++s) {
-                pp = fmaT(pp, cf.rm[s], y[s] * cf.m[s]);
+                pp = fmaT(pp, cf.rm[s], y[s] * cf.e[s]);
                 y[s] = pp;
             }
         }
@@ -480,16 +481,22 @@ __device__ __forceinline__ int split_finish(const StepParams<TC> &p, const GridD
             y[H - 1] = fmaT(cf.ifa, other, y[H - 1]) * cf.ifc;
 #pragma unroll
             for (int s = H - 2; s >= 0; --s) y[s] = fmaT(cf.rm[s], y[s + 1], y[s]);
+            if (--rc == 0) {
+                rc = cf.resc_every;
+                const float2 rs = f2(cf.resc, cf.resc);
+#pragma unroll
+                for (int m = 0; m < H / 2; ++m) y2[m] = mul2(y2[m], rs);
+            }
         }
     }
 
     if (sg.active) {
-        const float2 c2 = f2(cref, cref);
+        const float2 c2 = f2(cref, cref), fk2 = f2(cf.f[kc], cf.f[kc]);
         PairSum ps;
         if (do_mass) ps.begin();
 #pragma unroll
         for (int m = 0; m < H / 2; ++m) {
-            const float2 x = add2(y2[m], c2);
+            const float2 x = fma2(fk2, y2[m], c2);
             out[sg.lbase + (2 * m) * sg.lstep + sg.oc] = x.x;
             out[sg.lbase + (2 * m + 1) * sg.lstep + sg.oc] = x.y;
             if (do_mass) ps.add(x);
@@ -663,15 +670,16 @@ __device__ __forceinline__ int process_item_split_rt(const StepParams<TC> &p, co
     const Coef<TC> &cf = p.coef;
     const float ifa = top ? g.ifa_t_f : g.ifa_b_f, ifc = g.ifc_bt_f;
     const int kmax = __reduce_max_sync(0xffffffffu, (unsigned)kc);
+    int rc = cf.resc_every;
     for (int r = 0; r < kmax; ++r) {
         const bool act = r < kc;
         float pp = 0.f;
         if (act) {
-            pp = y[0] * cf.m[0];
+            pp = y[0] * cf.e[0];
             y[0] = pp;
 #pragma unroll
             for (int s = 1; s < HMAX; ++s) {
-                const float np = fmaT(pp, cf.rm[s], y[s] * cf.m[s]);
+                const float np = fmaT(pp, cf.rm[s], y[s] * cf.e[s]);
                 const bool in_half = s < hlen;
                 y[s] = in_half ? np : y[s];
                 pp = in_half ? np : pp;
@@ -686,15 +694,21 @@ __device__ __forceinline__ int process_item_split_rt(const StepParams<TC> &p, co
                 const float bk = fmaT(cf.rm[s], y[s + 1], y[s]);
                 y[s] = s == hlen - 1 ? xl : (s < hlen - 1 ? bk : y[s]);
             }
+            if (--rc == 0) {
+                rc = cf.resc_every;
+                const float2 rs = f2(cf.resc, cf.resc);
+#pragma unroll
+                for (int m = 0; m < HMAX / 2; ++m) y2[m] = mul2(y2[m], rs);
+            }
         }
     }
 
-    const float2 c2 = f2(cref, cref);
+    const float2 c2 = f2(cref, cref), fk2 = f2(cf.f[kc], cf.f[kc]);
     PairSum ps;
     if (do_mass) ps.begin();
 #pragma unroll
     for (int m = 0; m < HMAX / 2; ++m) {
-        float2 x = add2(y2[m], c2);
+        float2 x = fma2(fk2, y2[m], c2);
         const bool v0 = active && 2 * m < hlen, v1 = active && 2 * m + 1 < hlen;
         st_pred(out + (lbase + (v0 ? 2 * m : 0) * lstep + oc), x.x, v0);
         st_pred(out + (lbase + (v1 ? 2 * m + 1 : 0) * lstep + oc), x.y, v1);
@@ -913,18 +927,20 @@ __device__ __forceinline__ int process_item_twin(const StepParams<TC> &p, const 
         for (int s = 0; s < H; ++s) y2[s] = add2(y2[s], nc);
     }
     const Coef<TC> &cf = p.coef;
-    const float2 minf = f2(cf.m[S0], cf.m[S0]), rminf = f2(cf.rm[S0], cf.rm[S0]);
+    const float2 rminf = f2(cf.rm[S0], cf.rm[S0]);
+    int rc = cf.resc_every;
     for (int r = 0; r < kc; ++r) {
-        // both halves eliminate toward the middle
-        float2 pp = f2(y2[0].x * cf.m[0], y2[0].y * cf.m[0]);
+        // both halves eliminate toward the middle (from level S0 on the
+        // forward multiplier e_s is 1: no multiply)
+        float2 pp = f2(y2[0].x * cf.e[0], y2[0].y * cf.e[0]);
         y2[0] = pp;
 #pragma unroll
         for (int s = 1; s < H; ++s) {
             if (s < S0) {
-                pp = f2(fmaT(pp.x, cf.rm[s], y2[s].x * cf.m[s]),
-                        fmaT(pp.y, cf.rm[s], y2[s].y * cf.m[s]));
+                pp = f2(fmaT(pp.x, cf.rm[s], y2[s].x * cf.e[s]),
+                        fmaT(pp.y, cf.rm[s], y2[s].y * cf.e[s]));
             } else {
-                pp = fma2(pp, rminf, mul2(y2[s], minf));
+                pp = fma2(pp, rminf, y2[s]);
             }
             y2[s] = pp;
         }
@@ -938,15 +954,21 @@ __device__ __forceinline__ int process_item_twin(const StepParams<TC> &p, const 
             else
                 y2[s] = fma2(rminf, y2[s + 1], y2[s]);
         }
+        if (--rc == 0) {
+            rc = cf.resc_every;
+            const float2 rs = f2(cf.resc, cf.resc);
+#pragma unroll
+            for (int s = 0; s < H; ++s) y2[s] = mul2(y2[s], rs);
+        }
     }
 
     if (cg.active) {
-        const float2 c2 = f2(cref, cref);
+        const float2 c2 = f2(cref, cref), fk2 = f2(cf.f[kc], cf.f[kc]);
         PairSum ps;
         if (do_mass) ps.begin();
 #pragma unroll
         for (int s = 0; s < H; ++s) {
-            const float2 v = add2(y2[s], c2);
+            const float2 v = fma2(fk2, y2[s], c2);
             out[s * plane + cg.oc] = v.x;
             out[(NZ - 1 - s) * plane + cg.oc] = v.y;
             if (do_mass) ps.add(v);
@@ -1038,18 +1060,19 @@ __device__ __forceinline__ int process_item_twin_rt(const StepParams<TC> &p, con
         for (int s = 0; s < HMAX; ++s) y2[s] = add2(y2[s], nc);
     }
     const Coef<TC> &cf = p.coef;
-    const float2 minf = f2(cf.m[S0], cf.m[S0]), rminf = f2(cf.rm[S0], cf.rm[S0]);
+    const float2 rminf = f2(cf.rm[S0], cf.rm[S0]);
+    int rc = cf.resc_every;
     for (int r = 0; r < kc; ++r) {
-        float2 pp = f2(y2[0].x * cf.m[0], y2[0].y * cf.m[0]);
+        float2 pp = f2(y2[0].x * cf.e[0], y2[0].y * cf.e[0]);
         y2[0] = pp;
 #pragma unroll
         for (int s = 1; s < HMAX; ++s) {
             float2 np;
             if (s < S0)
-                np = f2(fmaT(pp.x, cf.rm[s], y2[s].x * cf.m[s]),
-                        fmaT(pp.y, cf.rm[s], y2[s].y * cf.m[s]));
+                np = f2(fmaT(pp.x, cf.rm[s], y2[s].x * cf.e[s]),
+                        fmaT(pp.y, cf.rm[s], y2[s].y * cf.e[s]));
             else
-                np = fma2(pp, rminf, mul2(y2[s], minf));
+                np = fma2(pp, rminf, y2[s]);
             const bool inl = s < hb, inh = s < ht;
             y2[s] = f2(inl ? np.x : y2[s].x, inh ? np.y : y2[s].y);
             pp = f2(inl ? np.x : pp.x, inh ? np.y : pp.y);
@@ -1068,14 +1091,20 @@ __device__ __forceinline__ int process_item_twin_rt(const StepParams<TC> &p, con
             y2[s] = f2(s == hb - 1 ? xl : (s < hb - 1 ? bk.x : y2[s].x),
                        s == ht - 1 ? xh : (s < ht - 1 ? bk.y : y2[s].y));
         }
+        if (--rc == 0) {
+            rc = cf.resc_every;
+            const float2 rs = f2(cf.resc, cf.resc);
+#pragma unroll
+            for (int s = 0; s < HMAX; ++s) y2[s] = mul2(y2[s], rs);
+        }
     }
 
-    const float2 c2 = f2(cref, cref);
+    const float2 c2 = f2(cref, cref), fk2 = f2(cf.f[kc], cf.f[kc]);
     PairSum ps;
     if (do_mass) ps.begin();
 #pragma unroll
     for (int s = 0; s < HMAX; ++s) {
-        float2 x = add2(y2[s], c2);
+        float2 x = fma2(fk2, y2[s], c2);
         const bool vl = cg.active && s < hb, vh = cg.active && s < ht;
         st_pred(out + ((vl ? s : 0) * plane + cg.oc), x.x, vl);
         st_pred(out + ((nz - 1 - (vh ? s : 0)) * plane + cg.oc), x.y, vh);
@@ -1209,14 +1238,15 @@ __device__ __forceinline__ int process_item_pair(const StepParams<TC> &p, const 
     }
     const Coef<TC> &cf = p.coef;
     const int kmax = __reduce_max_sync(0xffffffffu, (unsigned)kc);
+    int rc = cf.resc_every;
     for (int r = 0; r < kmax; ++r) {
         const bool act = r < kc;
         if (act) {
-            float pp = y[0] * cf.m[0];
+            float pp = y[0] * cf.e[0];
             y[0] = pp;
 #pragma unroll
             for (int s = 1; s < H; ++s) {
-                pp = fmaT(pp, cf.rm[s], y[s] * cf.m[s]);
+                pp = fmaT(pp, cf.rm[s], y[s] * cf.e[s]);
                 y[s] = pp;
             }
         }
@@ -1227,16 +1257,22 @@ __device__ __forceinline__ int process_item_pair(const StepParams<TC> &p, const 
             y[H - 1] = fmaT(cf.ifa, other, y[H - 1]) * cf.ifc;
 #pragma unroll
             for (int s = H - 2; s >= 0; --s) y[s] = fmaT(cf.rm[s], y[s + 1], y[s]);
+            if (--rc == 0) {
+                rc = cf.resc_every;
+                const float2 rs = f2(cf.resc, cf.resc);
+#pragma unroll
+                for (int m = 0; m < H / 2; ++m) y2[m] = mul2(y2[m], rs);
+            }
         }
     }
 
     if (active) {
-        const float2 c2 = f2(cref, cref);
+        const float2 c2 = f2(cref, cref), fk2 = f2(cf.f[kc], cf.f[kc]);
         PairSum ps;
         if (do_mass) ps.begin();
 #pragma unroll
         for (int m = 0; m < H / 2; ++m) {
-            const float2 v = add2(y2[m], c2);
+            const float2 v = fma2(fk2, y2[m], c2);
             out[lbase + (2 * m) * lstep + oc] = v.x;
             out[lbase + (2 * m + 1) * lstep + oc] = v.y;
             if (do_mass) ps.add(v);
@@ -1419,6 +1455,8 @@ lb_step_kernel(const __grid_constant__ StepParams<TC> p) {
                 }
             }
         } else for (;;) {
+            // serial measurement steps: only the first serial_warps warps work
+            if (p.serial_warps > 0 && warp >= p.serial_warps) break;
             int c = 0;
             if (p.steal && !p.queue_mode) {
                 c = pop_with_stealing(p, s & 1, bin, lane);

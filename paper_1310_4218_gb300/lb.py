@@ -107,6 +107,10 @@ _SIG = {
                                        ctypes.POINTER(_P)]),
     "lb_step_noalloc": (_I32, [ctypes.POINTER(lb_grid_desc), ctypes.POINTER(lb_vp), _I32,
                                _P, ctypes.c_int64, _I32, _P, _P]),
+    "lb_set_owned": (_I32, [_P, _P]),
+    "lb_step_serial": (_I32, [_P, _I32]),
+    "lb_pack_columns": (_I32, [_P, _I32, _P, _I32, _P]),
+    "lb_unpack_columns": (_I32, [_P, _I32, _P, _I32, _P]),
 }
 EXPORTED = tuple(_SIG)
 
@@ -348,3 +352,29 @@ def lb_step_noalloc(grid, vps, t0, nsteps, stream=0, want_mass=True, options=Non
                            int(nsteps), _P(stream or 0), ctypes.addressof(m) if want_mass else None)
     _check(st, None)
     return m.value if want_mass else None
+
+
+def lb_set_owned(ctx, owned):
+    """Run only the VPs whose entry of owned (length nvps, 0/1) is 1."""
+    a = np.ascontiguousarray(owned, dtype=np.uint8)
+    _check(load_library().lb_set_owned(ctx, _ptr(a)), ctx)
+
+
+def lb_pack_columns(ctx, grid, cells_ptr, n, buf_ptr):
+    """Enqueue a copy of n columns (device int32 indices at cells_ptr) of the
+    current field into the device buffer at buf_ptr (level-major)."""
+    _check(load_library().lb_pack_columns(ctx, int(grid), _P(cells_ptr or 0), int(n),
+                                          _P(buf_ptr or 0)), ctx)
+
+
+def lb_unpack_columns(ctx, grid, cells_ptr, n, buf_ptr):
+    """Enqueue a copy of a level-major device buffer into n columns of the
+    current field."""
+    _check(load_library().lb_unpack_columns(ctx, int(grid), _P(cells_ptr or 0), int(n),
+                                            _P(buf_ptr or 0)), ctx)
+
+
+def lb_step_serial(ctx, nsteps):
+    """nsteps steps with one working warp per processor (serialized
+    measurement: costs free of interference from co-running warps)."""
+    _check(load_library().lb_step_serial(ctx, int(nsteps)), ctx)

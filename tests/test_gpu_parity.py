@@ -63,11 +63,10 @@ def test_variant_parity(storage, compute, nz):
 
 
 # Kernels of FP32 grids with nz 32, 64 or 96 (lb_options.threads_hint,
-# staged_loads): by default one lane per column with packed twisted halves
-# when every VP width is a multiple of 16 ("wide"), else split columns on
-# half-warps (8 x 2 tiles, "narrow"); forced paired warps; forced
-# half-warps; TMA-staged; one lane per column (plain Thomas); forced twin
-# halves on narrow VPs.
+# staged_loads): by default one lane per column with packed twisted halves,
+# on VPs whose widths are multiples of 16 ("wide") or not ("narrow");
+# forced paired warps; forced half-warps; TMA-staged; one lane per column
+# (plain Thomas); forced twin halves.
 EXACT_KERNELS = {"narrow": {}, "wide": {}, "pair": {"threads_hint": 3},
                  "half": {"threads_hint": 2}, "staged": {"staged_loads": 1},
                  "one_lane": {"threads_hint": 1}, "twin": {"threads_hint": 4}}
@@ -76,7 +75,7 @@ EXACT_KERNELS = {"narrow": {}, "wide": {}, "pair": {"threads_hint": 3},
 def _check_kernel_shape(info, kernel):
     if kernel == "pair":
         assert (info.item_w, info.item_h, info.staged_slots) == (16, 2, 0)
-    elif kernel in ("narrow", "half"):
+    elif kernel == "half":
         assert (info.item_w, info.item_h, info.staged_slots) == (8, 2, 0)
     elif kernel == "staged":
         assert (info.item_w, info.item_h) == (8, 2) and info.staged_slots > 0
@@ -175,7 +174,7 @@ def test_runtime_nz_twin_and_split_agree_bitwise(nz):
 # step in place of the advection) on every kernel family.
 JACOBI_CASES = [
     # kernel options, nx, nz list (several: a mixed-nz batch), storage, compute
-    ({}, 52, [32], "f32", "f32"),                          # half-warp split (narrow VPs)
+    ({"threads_hint": 2}, 52, [32], "f32", "f32"),         # half-warp split (narrow VPs)
     ({}, 64, [64], "f32", "f32"),                          # twin halves (wide VPs)
     ({"threads_hint": 3}, 64, [96], "f32", "f32"),         # paired warps
     ({"threads_hint": 1}, 52, [32], "f32", "f32"),         # one lane per column
