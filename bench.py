@@ -590,7 +590,7 @@ def end_to_end(ring, fields, nper, stream, dev):
             up.wait_event(freed[x])
         with torch.cuda.stream(up):
             for gi in range(len(w.grids)):
-                r.sim.field_tensor(gi).view(-1).copy_(h_in[gi].view(-1), non_blocking=True)
+                r.sim.field_tensor(gi).copy_(h_in[gi], non_blocking=True)
         loaded = torch.cuda.Event()
         loaded.record(up)
         stream.wait_event(loaded)
@@ -602,7 +602,7 @@ def end_to_end(ring, fields, nper, stream, dev):
         down.wait_event(done)
         with torch.cuda.stream(down):
             for gi in range(len(w.grids)):
-                h_out[gi].view(-1).copy_(r.sim.field_tensor(gi).view(-1), non_blocking=True)
+                h_out[gi].copy_(r.sim.field_tensor(gi), non_blocking=True)
         freed[x] = torch.cuda.Event()
         freed[x].record(down)
     stream.wait_stream(up)

@@ -28,7 +28,8 @@
  *      caller-supplied array;
  *   4. optional diagnostic: compensated FP64 global sum of the new field.
  *
- * Layout of every field: x fastest, element (i,j,k) at (k*ny + j)*nx + i.
+ * Layout of every field: x fastest, element (i,j,k) at (k*ny + j)*nx + i,
+ * or (k*ny + j)*pitch + i with a row pitch (lb_grid_desc.pitch).
  *
  * Conventions for every entry point:
  *   - Returns an lb_status and never aborts or exits the process.
@@ -152,7 +153,13 @@ typedef struct {
                                  q* = (1 - 6 nu) q + nu * (sum of the six face
                                  neighbours), periodic in x/y, mirror ghosts
                                  (zero flux) in z; cx, cy, cz are then unused */
-    int32_t pad0;             /* must be 0 */
+    int32_t pitch;            /* elements from one row (j) of q0/q1 to the
+                                 next: 0 = nx (dense), else >= nx, so that
+                                 rows can start on 32-byte sectors; the
+                                 buffers then hold pitch*ny*nz elements,
+                                 level k at k*pitch*ny, and the padding
+                                 columns nx..pitch-1 are never read or
+                                 written.  k_c arrays stay dense [ny*nx] */
     double nu;                /* Jacobi weight, 0 < nu <= 1/6 (dynamics 1) */
 } lb_grid_desc;
 
@@ -169,7 +176,10 @@ typedef struct {
                                      or 1/4 of the threads, so the SM holds
                                      the same warps as with 1 */
     int32_t queue_order;          /* ATOMIC_QUEUE order: 0 VP id order,
-                                     1 last measured cost, heaviest first */
+                                     1 last measured cost, heaviest first,
+                                     2 VP id order over the VPs at or above
+                                     the median measured cost, then over
+                                     the rest (light items end the step) */
     int32_t mass_every;           /* global sum every n-th step; 0 = never
                                      (default 1) */
     int32_t device_balancer;      /* reserved, must be 0 */

@@ -252,6 +252,16 @@ static lb_status upload_items(lb_ctx *ctx) {
     if (ctx->opt.queue_order == 1 && ctx->have_costs)
         std::stable_sort(order.begin(), order.end(),
                          [&](int a, int b) { return ctx->cost[a] > ctx->cost[b]; });
+    if (ctx->opt.queue_order == 2 && ctx->have_costs && nv > 1) {
+        // two spatial sweeps: the VPs at or above the median cost, then the
+        // rest, so that the items still running when the queue empties are
+        // the light ones
+        std::vector<double> c(ctx->cost.begin(), ctx->cost.end());
+        std::nth_element(c.begin(), c.begin() + nv / 2, c.end());
+        const double med = c[nv / 2];
+        std::stable_partition(order.begin(), order.end(),
+                              [&](int v) { return ctx->cost[v] >= med; });
+    }
     std::vector<int2> qitems;
     qitems.reserve(ctx->nitems);
     for (int v : order)
@@ -299,6 +309,7 @@ static bool staged_eligible(const std::vector<lb_grid_desc> &grids) {
         // the box holds the upwind neighbours only: advection grids
         if (d.dynamics != 0) return false;
         if (d.storage != LB_F32 || d.compute != LB_F32 || d.nx % 4 != 0) return false;
+        if ((d.pitch ? d.pitch : d.nx) % 4 != 0) return false;
         if ((reinterpret_cast<uintptr_t>(d.q0) | reinterpret_cast<uintptr_t>(d.q1)) & 15u) return false;
     }
     return true;
@@ -319,7 +330,8 @@ static bool encode_tmaps(const std::vector<lb_grid_desc> &grids, int nz_box,
     for (size_t g = 0; g < grids.size(); ++g) {
         const lb_grid_desc &d = grids[g];
         const cuuint64_t dims[3] = {(cuuint64_t)d.nx, (cuuint64_t)d.ny, (cuuint64_t)d.nz};
-        const cuuint64_t strides[2] = {(cuuint64_t)d.nx * 4, (cuuint64_t)d.nx * d.ny * 4};
+        const cuuint64_t pitch = (cuuint64_t)(d.pitch ? d.pitch : d.nx);
+        const cuuint64_t strides[2] = {pitch * 4, pitch * d.ny * 4};
         const cuuint32_t box[3] = {(cuuint32_t)kBoxW, (cuuint32_t)kBoxH, (cuuint32_t)nz_box};
         const cuuint32_t estr[3] = {1, 1, 1};
         for (int b = 0; b < 2; ++b) {
@@ -1122,8 +1134,8 @@ static lb_status columns(lb_ctx *ctx, bool pack, int32_t grid, const int32_t *ce
     if (n == 0) return LB_OK;
     const lb_grid_desc &d = ctx->grids[grid];
     void *field = ctx->parity ? d.q1 : d.q0;
-    CK(dev_columns(pack, field, (int)dtype_size(d.storage), cells, n, d.nz, d.nx * d.ny, buf,
-                   ctx->d_status, ctx->stream));
+    CK(dev_columns(pack, field, (int)dtype_size(d.storage), cells, n, d.nz, d.nx, d.ny,
+                   d.pitch ? d.pitch : d.nx, buf, ctx->d_status, ctx->stream));
     return LB_OK;
 }
 
@@ -1247,7 +1259,7 @@ extern "C" lb_status lb_checkpoint(lb_ctx *ctx, const char *path) {
     W(ctx->cost.data(), sizeof(double) * ctx->cost.size());
     std::vector<char> buf;
     for (auto &g : ctx->grids) {
-        size_t bytes = (size_t)g.nx * g.ny * g.nz * dtype_size(g.storage);
+        size_t bytes = (size_t)(g.pitch ? g.pitch : g.nx) * g.ny * g.nz * dtype_size(g.storage);
         buf.resize(bytes);
         cudaError_t e = cudaMemcpyAsync(buf.data(), ctx->parity ? g.q1 : g.q0, bytes,
                                         cudaMemcpyDeviceToHost, ctx->stream);
@@ -1297,7 +1309,7 @@ extern "C" lb_status lb_restore(lb_ctx *ctx, const char *path) {
     const int parity = hdr[3] & 1;
     std::vector<char> buf;
     for (auto &g : ctx->grids) {
-        size_t bytes = (size_t)g.nx * g.ny * g.nz * dtype_size(g.storage);
+        size_t bytes = (size_t)(g.pitch ? g.pitch : g.nx) * g.ny * g.nz * dtype_size(g.storage);
         buf.resize(bytes);
         R(buf.data(), bytes);
         if (!ok) break;

@@ -22,7 +22,8 @@ constexpr int kTwinS0 = 8;
 // One grid as the kernel sees it.
 struct GridDev {
     int32_t nx, ny, nz, kc_disk;
-    int32_t plane;                 // nx*ny
+    int32_t plane;                 // pitch*ny: elements between levels
+    int32_t pitch;                 // elements between rows (nx when dense)
     int32_t sx, sy, sz;            // upwind direction per axis (+1: neighbour at -1)
     void *q[2];                    // ping-pong fields
     const int32_t *kc;             // k_c array (kc_disk == 0)
@@ -251,7 +252,7 @@ cudaError_t dev_kc_features(const DevBal &p, int grid, const int32_t *kc, bool i
 // Column copies of a sharded run (lb_shard.cu): pack (field -> buf) or
 // unpack (buf -> field) n columns of nz levels; esize = storage bytes.
 cudaError_t dev_columns(bool pack, void *field, int esize, const int32_t *cells, int n, int nz,
-                        int plane, void *buf, int32_t *status, cudaStream_t s);
+                        int nx, int ny, int pitch, void *buf, int32_t *status, cudaStream_t s);
 
 // Text returned by lb_last_error(NULL) (calls without a ctx).
 void set_ctxless_error(const char *msg);

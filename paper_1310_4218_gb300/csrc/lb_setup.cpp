@@ -14,7 +14,9 @@ const char *check_grid_desc(const lb_grid_desc &d) {
         return "need nx, ny >= 1 and 1 <= nz <= 128";
     if ((long long)d.nx * d.ny * d.nz >= (1LL << 31)) return "nx*ny*nz must be below 2^31";
     if (d.dynamics != 0 && d.dynamics != 1) return "dynamics is 0 (advection) or 1 (Jacobi)";
-    if (d.pad0 != 0) return "pad0 must be 0";
+    if (d.pitch != 0 && d.pitch < d.nx) return "pitch must be 0 or at least nx";
+    if ((long long)(d.pitch ? d.pitch : d.nx) * d.ny * d.nz >= (1LL << 31))
+        return "pitch*ny*nz must be below 2^31";
     if (d.dynamics == 0 &&
         (!std::isfinite(d.cx) || !std::isfinite(d.cy) || !std::isfinite(d.cz) ||
          std::fabs(d.cx) + std::fabs(d.cy) + std::fabs(d.cz) > 1.0 + 1e-12))
@@ -147,7 +149,8 @@ void fill_grid_dev(const lb_grid_desc &d, int32_t *kc_range, GridDev &h) {
     h.ny = d.ny;
     h.nz = d.nz;
     h.kc_disk = d.kc_disk;
-    h.plane = d.nx * d.ny;
+    h.pitch = d.pitch ? d.pitch : d.nx;
+    h.plane = h.pitch * d.ny;
     h.sx = d.cx >= 0 ? 1 : -1;
     h.sy = d.cy >= 0 ? 1 : -1;
     h.sz = d.cz >= 0 ? 1 : -1;

@@ -9,12 +9,12 @@ namespace lbk {
 bool kernels_f32_shared_sm(int nz, bool twin, int ctas_per_sm, KernelInfo *out) {
     if (nz != 96) return false;
     if (twin) {
-        if (ctas_per_sm == 2) { *out = kernel_entry<float, float, 96, true, 1, 256, false, 0, true>(); return true; }
-        if (ctas_per_sm == 4) { *out = kernel_entry<float, float, 96, true, 1, 128, false, 0, true>(); return true; }
+        if (ctas_per_sm == 2) { *out = kernel_entry<float, float, 96, true, 1, 256, false, 0, true, 2>(); return true; }
+        if (ctas_per_sm == 4) { *out = kernel_entry<float, float, 96, true, 1, 128, false, 0, true, 4>(); return true; }
         return false;
     }
-    if (ctas_per_sm == 2) { *out = kernel_entry<float, float, 96, true, 1, 384, true>(); return true; }
-    if (ctas_per_sm == 4) { *out = kernel_entry<float, float, 96, true, 1, 192, true>(); return true; }
+    if (ctas_per_sm == 2) { *out = kernel_entry<float, float, 96, true, 1, 384, true, 0, false, 2>(); return true; }
+    if (ctas_per_sm == 4) { *out = kernel_entry<float, float, 96, true, 1, 192, true, 0, false, 4>(); return true; }
     return false;
 }
 

@@ -138,12 +138,13 @@ __device__ __forceinline__ int kc_disk(const GridDev &g, int i, int j, long long
     return d2 <= (long long)g.disk_r * g.disk_r ? g.k_in : g.k_out;
 }
 
-// k_c of column (i, j) at step t: the disk rule, or the array entry bounded
-// to 0..LB_KC_MAX; an entry above the bound also sets the grid's range flag
-// (every writer stores 1, so the race between lanes is harmless).
-__device__ __forceinline__ int kc_at(const GridDev &g, int i, int j, int oc, long long t) {
+// k_c of column (i, j) at step t: the disk rule, or the array entry (dense
+// [ny][nx], whatever the field's row pitch) bounded to 0..LB_KC_MAX; an
+// entry above the bound also sets the grid's range flag (every writer
+// stores 1, so the race between lanes is harmless).
+__device__ __forceinline__ int kc_at(const GridDev &g, int i, int j, int, long long t) {
     if (g.kc_disk) return kc_disk(g, i, j, t);
-    int k = g.kc[oc];
+    int k = g.kc[j * g.nx + i];
     if (k > LB_KC_MAX) {
         k = LB_KC_MAX;
         *(volatile int32_t *)g.kc_range = 1;
@@ -176,7 +177,8 @@ struct JacNbr {
 __device__ __forceinline__ JacNbr jac_nbr(const GridDev &g, int i, int j) {
     const int im = i > 0 ? i - 1 : g.nx - 1, ip = i + 1 < g.nx ? i + 1 : 0;
     const int jm = j > 0 ? j - 1 : g.ny - 1, jp = j + 1 < g.ny ? j + 1 : 0;
-    return JacNbr{j * g.nx + i, j * g.nx + im, j * g.nx + ip, jm * g.nx + i, jp * g.nx + i};
+    return JacNbr{j * g.pitch + i, j * g.pitch + im, j * g.pitch + ip, jm * g.pitch + i,
+                  jp * g.pitch + i};
 }
 template <class TC> __device__ __forceinline__ TC jac_nu(const GridDev &g);
 template <> __device__ __forceinline__ float jac_nu<float>(const GridDev &g) { return g.nu_f; }
@@ -248,9 +250,9 @@ __device__ __forceinline__ ColGeom col_geom(const GridDev &g, const VPDev &vp, i
     int im = c.i - g.sx, jm = c.j - g.sy;
     im = im < 0 ? im + g.nx : (im >= g.nx ? im - g.nx : im);
     jm = jm < 0 ? jm + g.ny : (jm >= g.ny ? jm - g.ny : jm);
-    c.oc = c.j * g.nx + c.i;
-    c.oi = c.j * g.nx + im;
-    c.oj = jm * g.nx + c.i;
+    c.oc = c.j * g.pitch + c.i;
+    c.oi = c.j * g.pitch + im;
+    c.oj = jm * g.pitch + c.i;
     return c;
 }
 
@@ -425,9 +427,9 @@ __device__ __forceinline__ SplitGeom split_geom(const GridDev &g, const VPDev &v
     int im = sg.i - g.sx, jm = sg.j - g.sy;
     im = im < 0 ? im + g.nx : (im >= g.nx ? im - g.nx : im);
     jm = jm < 0 ? jm + g.ny : (jm >= g.ny ? jm - g.ny : jm);
-    sg.oc = sg.j * g.nx + sg.i;
-    sg.oi = sg.j * g.nx + im;
-    sg.oj = jm * g.nx + sg.i;
+    sg.oc = sg.j * g.pitch + sg.i;
+    sg.oi = sg.j * g.pitch + im;
+    sg.oj = jm * g.pitch + sg.i;
     sg.lbase = sg.top ? (NZ - 1) * g.plane : 0;
     sg.lstep = sg.top ? -g.plane : g.plane;
     return sg;
@@ -603,7 +605,7 @@ __device__ __forceinline__ int process_item_split_rt(const StepParams<TC> &p, co
     jm = jm < 0 ? jm + g.ny : (jm >= g.ny ? jm - g.ny : jm);
     const int plane = g.plane, nz = g.nz;
     const int hlen = top ? nz / 2 : (nz + 1) / 2;     // levels this lane holds
-    const int oc = j * g.nx + i, oi = j * g.nx + im, oj = jm * g.nx + i;
+    const int oc = j * g.pitch + i, oi = j * g.pitch + im, oj = jm * g.pitch + i;
     const int lbase = top ? (nz - 1) * plane : 0;
     const int lstep = top ? -plane : plane;
     const TS *in = static_cast<const TS *>(g.q[src]);
@@ -1184,7 +1186,7 @@ __device__ __forceinline__ int process_item_pair(const StepParams<TC> &p, const 
     im = im < 0 ? im + g.nx : (im >= g.nx ? im - g.nx : im);
     jm = jm < 0 ? jm + g.ny : (jm >= g.ny ? jm - g.ny : jm);
     const int plane = g.plane;
-    const int oc = j * g.nx + i, oi = j * g.nx + im, oj = jm * g.nx + i;
+    const int oc = j * g.pitch + i, oi = j * g.pitch + im, oj = jm * g.pitch + i;
     const int lbase = top ? (NZ - 1) * plane : 0;
     const int lstep = top ? -plane : plane;
     const TS *in = static_cast<const TS *>(g.q[src]);
@@ -1358,9 +1360,11 @@ __device__ __noinline__ ItemResult<TC> run_pair_jacobi(const StepParams<TC> &p, 
 }
 
 // ------------------------------------------------------------ the kernel
+// MINB: CTAs that must fit on one SM (processors sharing an SM), which caps
+// the registers per thread at 65536 / (THREADS * MINB).
 template <class TS, class TC, int NZ, bool EXACT, int NZLO, int THREADS, bool SPLIT, int PAIRW,
-          bool TWIN>
-__global__ void __launch_bounds__(THREADS, 1)
+          bool TWIN, int MINB = 1>
+__global__ void __launch_bounds__(THREADS, MINB)
 lb_step_kernel(const __grid_constant__ StepParams<TC> p) {
     constexpr bool PAIR = PAIRW > 0;
     static_assert(!TWIN || (!SPLIT && !PAIR), "twin kernels: one lane per column");
@@ -1534,12 +1538,12 @@ lb_step_kernel(const __grid_constant__ StepParams<TC> p) {
 }
 
 template <class TS, class TC, int NZ, bool EXACT, int NZLO, int THREADS, bool SPLIT = false,
-          int PAIRW = 0, bool TWIN = false>
+          int PAIRW = 0, bool TWIN = false, int MINB = 1>
 inline KernelInfo kernel_entry() {
     static_assert(!SPLIT || NZ % 4 == 0, "split kernels hold nz/2 levels in register pairs");
     constexpr bool PAIR = PAIRW > 0;
     KernelInfo k;
-    k.fn = (const void *)&lb_step_kernel<TS, TC, NZ, EXACT, NZLO, THREADS, SPLIT, PAIRW, TWIN>;
+    k.fn = (const void *)&lb_step_kernel<TS, TC, NZ, EXACT, NZLO, THREADS, SPLIT, PAIRW, TWIN, MINB>;
     k.threads = THREADS;
     k.nz_variant = NZ;
     k.exact = EXACT ? 1 : 0;

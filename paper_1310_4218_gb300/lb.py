@@ -44,7 +44,7 @@ class lb_grid_desc(ctypes.Structure):
                 ("disk_y0", ctypes.c_int32), ("disk_vx", ctypes.c_int32),
                 ("disk_vy", ctypes.c_int32), ("disk_r", ctypes.c_int32),
                 ("k_in", ctypes.c_int32), ("k_out", ctypes.c_int32),
-                ("dynamics", ctypes.c_int32), ("pad0", ctypes.c_int32), ("nu", ctypes.c_double)]
+                ("dynamics", ctypes.c_int32), ("pitch", ctypes.c_int32), ("nu", ctypes.c_double)]
 
 
 class lb_vp(ctypes.Structure):

@@ -27,9 +27,13 @@ class Simulation:
         with torch.cuda.device(self.device):
             for gi, g in enumerate(self.grids):
                 dt = _TORCH[g.storage]
-                q0 = torch.as_tensor(np.asarray(fields[gi], dtype=np.float64)).to(
-                    device=self.device, dtype=dt).contiguous()
-                q1 = torch.empty_like(q0)
+                pitch = getattr(g, "pitch", 0) or g.nx
+                src = torch.as_tensor(np.asarray(fields[gi], dtype=np.float64)).to(
+                    device=self.device, dtype=dt)
+                # rows of `pitch` elements; the padding columns stay zero
+                q0 = torch.zeros((g.nz, g.ny, pitch), dtype=dt, device=self.device)
+                q0[:, :, :g.nx] = src.reshape(g.nz, g.ny, g.nx)
+                q1 = torch.zeros_like(q0)
                 self.bufs.append((q0, q1))
                 kc_t = None
                 if not g.kc_disk:
@@ -43,6 +47,7 @@ class Simulation:
                     kc_t.data_ptr() if kc_t is not None else None, 1 if g.kc_disk else 0,
                     x0, y0, vx, vy, R, g.k_in, g.k_out, getattr(g, "dynamics", 0), 0,
                     getattr(g, "nu", 1.0 / 7.0)))
+                descs[-1].pitch = 0 if pitch == g.nx else pitch
             torch.cuda.synchronize(self.device)
             self.ctx = L.lb_create(descs, self.vps, options, self.stream.cuda_stream)
         self.nvps = len(self.vps)
@@ -84,15 +89,17 @@ class Simulation:
 
     # -- results
     def field_tensor(self, grid=0):
+        """The buffer holding the latest field of `grid`, (nz, ny, nx): a
+        strided view when the rows are padded."""
         ptr = L.lb_current_field(self.ctx, grid)
         q0, q1 = self.bufs[grid]
-        return q0 if q0.data_ptr() == ptr else q1
+        g = self.grids[grid]
+        return (q0 if q0.data_ptr() == ptr else q1)[:, :, :g.nx]
 
     def field(self, grid=0):
         """Latest field of `grid` as float64 numpy (nz, ny, nx)."""
         L.lb_sync(self.ctx)
-        g = self.grids[grid]
-        return self.field_tensor(grid).to(torch.float64).cpu().numpy().reshape(g.nz, g.ny, g.nx)
+        return self.field_tensor(grid).to(torch.float64).cpu().numpy()
 
     def mass(self, grid=0):
         return L.lb_mass(self.ctx, grid)

@@ -14,8 +14,9 @@ class Grid:
 
     def __init__(self, nx, ny, nz, cx=0.5, cy=0.5, cz=0.0, r=0.1, storage="f32",
                  compute="f32", kc_disk=True, disk=(0, 0, 1, 1, 3), k_in=4, k_out=1,
-                 dynamics=0, nu=1.0 / 7.0):
+                 dynamics=0, nu=1.0 / 7.0, pitch=0):
         self.nx, self.ny, self.nz = nx, ny, nz
+        self.pitch = pitch
         self.cx, self.cy, self.cz, self.r = cx, cy, cz, r
         self.storage, self.compute = storage, compute
         self.kc_disk, self.disk, self.k_in, self.k_out = kc_disk, tuple(disk), k_in, k_out

@@ -102,14 +102,16 @@ def test_create_rejects_invalid_layout_before_touching_the_device(lbmod):
 
 def test_create_validates_the_dynamics_fields_before_touching_the_device(lbmod):
     """dynamics is 0 (advection) or 1 (Jacobi); the Jacobi weight must lie in
-    (0, 1/6]; a Jacobi grid ignores the Courant numbers; pad0 must be 0."""
+    (0, 1/6]; a Jacobi grid ignores the Courant numbers; a row pitch is 0
+    (dense) or at least nx, and pitch*ny*nz stays below 2^31."""
     def desc(cx, dynamics, nu, pad=0):
         return lbmod.lb_grid_desc(8, 8, 4, cx, 0.5, 0.0, 0.1, lbmod.LB_F32, lbmod.LB_F32,
                                   0x1000, 0x2000, None, 1, 0, 0, 0, 0, 1, 1, 1, dynamics, pad, nu)
     overlap = [(0, 0, 0, 8, 8), (0, 0, 0, 1, 1)]
     for d, word in ((desc(0.5, 2, 0.1), "dynamics"), (desc(0.5, 1, 0.0), "nu"),
                     (desc(0.5, 1, 0.2), "nu"), (desc(0.5, 1, -0.1), "nu"),
-                    (desc(0.5, 0, 0.0, pad=1), "pad0")):
+                    (desc(0.5, 0, 0.0, pad=1), "pitch"), (desc(0.5, 0, 0.0, pad=-8), "pitch"),
+                    (desc(0.5, 0, 0.0, pad=1 << 27), "pitch*ny*nz")):
         with pytest.raises(lbmod.LBError) as e:
             lbmod.lb_create([d], overlap)
         assert e.value.status == lbmod.LB_EINVAL and word in str(e.value), str(e.value)

@@ -11,7 +11,8 @@ Names describe the workload; `get_config(name)` builds it.
   jacobi_fp32_1024x1024x96     the same with the Jacobi dynamics (7-point sweep) in place of
                                the advection
   precision_2048x2048x64     2048x2048x64, FP64/FP32/BF16 storage, FP32 compute, 50 steps
-  batch64_fp32               64 grids s x s x nz, s in 64..512, nz in 32..96, FP32
+  batch64_fp32               64 grids s x s x nz, s in 64..512, nz in 32..96, FP32, rows
+                             padded to multiples of 8 values in device memory
 """
 from dataclasses import dataclass, field
 from typing import List, Optional, Tuple
@@ -45,6 +46,7 @@ class GridSpec:
     seed: int = 0
     dynamics: int = 0             # 0: upwind advection; 1: weighted Jacobi sweep (Sec. IV)
     nu: float = 1.0 / 7.0         # Jacobi weight
+    pitch: int = 0                # row pitch of the device buffers (0: dense rows of nx)
 
     def initial_field(self, dtype=np.float64):
         return gaussian_blob(self.nx, self.ny, self.nz, self.center, self.sigma,
@@ -127,7 +129,11 @@ def precision_2048x2048x64(storage="f32"):
                     notes="disk R=256 moving (1,1)/step from (512,512), k_c 32/1")
 
 
-def batch64_fp32(ngrids=64):
+def batch64_fp32(ngrids=64, pad=True):
+    """64 grids of side s in 64..512: the device buffers pad each row to a
+    multiple of 8 FP32 values (pad=True), so that every row, and every VP
+    row segment (VPs start on multiples of 32 columns), begins on a 32-byte
+    sector; the fields themselves are s x s x nz."""
     seed = 5
     grids, vps = [], []
     rs = subseed(seed, 21)
@@ -140,7 +146,7 @@ def batch64_fp32(ngrids=64):
         c, s = _blob(side, side, nz)
         grids.append(GridSpec(side, side, nz, 0.5, 0.5, 0.0, 0.1, "f32", "f32", True,
                               (x0, y0, 1, 1, side // 8), kin, 1, c, s, 1e-3,
-                              subseed(seed, 100 + gi)))
+                              subseed(seed, 100 + gi), pitch=(side + 7) // 8 * 8 if pad else 0))
         vps += regular_blocks(side, side, 32, 32, grid=gi)
     return Workload("batch64_fp32", grids, vps, 50, seed, period=10,
                     notes="64 grids, side U{64..512}, nz U{32..96}, k_in U{2..48}")
