@@ -176,10 +176,8 @@ typedef struct {
                                      or 1/4 of the threads, so the SM holds
                                      the same warps as with 1 */
     int32_t queue_order;          /* ATOMIC_QUEUE order: 0 VP id order,
-                                     1 last measured cost, heaviest first,
-                                     2 VP id order over the VPs at or above
-                                     the median measured cost, then over
-                                     the rest (light items end the step) */
+                                     1 last measured cost, heaviest first;
+                                     other values act as 0 */
     int32_t mass_every;           /* global sum every n-th step; 0 = never
                                      (default 1) */
     int32_t device_balancer;      /* reserved, must be 0 */

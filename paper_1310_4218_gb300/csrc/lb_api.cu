@@ -252,16 +252,6 @@ static lb_status upload_items(lb_ctx *ctx) {
     if (ctx->opt.queue_order == 1 && ctx->have_costs)
         std::stable_sort(order.begin(), order.end(),
                          [&](int a, int b) { return ctx->cost[a] > ctx->cost[b]; });
-    if (ctx->opt.queue_order == 2 && ctx->have_costs && nv > 1) {
-        // two spatial sweeps: the VPs at or above the median cost, then the
-        // rest, so that the items still running when the queue empties are
-        // the light ones
-        std::vector<double> c(ctx->cost.begin(), ctx->cost.end());
-        std::nth_element(c.begin(), c.begin() + nv / 2, c.end());
-        const double med = c[nv / 2];
-        std::stable_partition(order.begin(), order.end(),
-                              [&](int v) { return ctx->cost[v] >= med; });
-    }
     std::vector<int2> qitems;
     qitems.reserve(ctx->nitems);
     for (int v : order)
@@ -425,8 +415,8 @@ extern "C" lb_status lb_create(const lb_grid_desc *grids, int32_t ngrids, const 
         return bail(LB_ENORESIDENT);
     }
 
-    // kernel variant: twin halves on wide layouts and for the Jacobi sweep
-    // (where the FP32 pivots converge), else split columns on half-warps
+    // kernel variant: twin halves for FP32 grids where the FP32 pivots
+    // converge, else split columns on half-warps (threads_hint overrides)
     const bool staged = ctx->opt.staged_loads && staged_eligible(ctx->grids);
     if (!choose_step_kernel(grids, ngrids, vps, nvps, ctx->opt.threads_hint, staged, &ctx->kinfo,
                             ctx->opt.ctas_per_sm)) {

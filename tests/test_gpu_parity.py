@@ -253,7 +253,8 @@ def test_twin_kernel_needs_converged_pivots():
 
 
 @pytest.mark.parametrize("kernel", ["narrow", "wide", "pair", "staged", "twin"])
-@pytest.mark.parametrize("cx,cy,cz", [(-0.4, 0.25, -0.3), (0.2, -0.5, 0.0), (-0.3, -0.3, 0.2)])
+@pytest.mark.parametrize("cx,cy,cz", [(-0.4, 0.25, -0.3), (0.2, -0.5, 0.0), (-0.3, -0.3, 0.2),
+                                      (-0.5, 0.5, 0.0), (0.5, -0.5, 0.0)])
 def test_exact_nz_kernels_general_advection(kernel, cx, cy, cz):
     """Either upwind side on every axis, and vertical advection, on the
     exact-nz kernels (for the TMA-staged kernel the box origin follows the
@@ -624,3 +625,4 @@ def test_row_pitch_checkpoint_and_column_copies(tmp_path):
     b.step(2)
     assert np.array_equal(b.field(0), ref)
     b.close()
+
