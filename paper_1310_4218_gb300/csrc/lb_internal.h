@@ -72,6 +72,8 @@ struct Coef {
     TC f[LB_KC_MAX + 1];       // f[k] = m_inf^k / resc^floor(k / resc_every)
     TC resc;                   // m_inf^resc_every
     int32_t resc_every;
+    // twin kernels' head levels as packed pairs (c, c) of the FP32 values
+    float2 e2[kTwinS0], rm2[kTwinS0];
 };
 
 template <class TC>

@@ -123,6 +123,11 @@ static void fill_coef_t(double r, const KernelInfo &k, Coef<TC> &c) {
     // scaled solves of the split family (the length-independent table)
     const double minf = converged_pivot(r);
     for (int i = 0; i < kNzMax; ++i) c.e[i] = (TC)(m[i] / minf);
+    for (int i = 0; i < kTwinS0; ++i) {
+        const float e = (float)(m[i] / minf), rm = (float)(r * m[i]);
+        c.e2[i] = {e, e};
+        c.rm2[i] = {rm, rm};
+    }
     // a solve grows a column by at most 1 / m_inf (M^-1 has unit row sums
     // and nonnegative entries): rescale before the growth reaches 2^40
     const double g = -std::log2(minf);

@@ -868,19 +868,18 @@ __device__ __forceinline__ int split_rt_bucket(const StepParams<TC> &p, const Gr
 // one chain of packed FP32x2 operations -- the same operations, in the same
 // order, as the split kernels, on half the instructions, without a shuffle.
 // A warp's load and store instructions cover 32 columns of one level (runs
-// of 32 columns in the VP's row-major order).  A packed operation needs its
-// coefficient pair in registers; the pivots m_s, r m_s of a zero-flux end
-// converge, and from level S0 on their FP32 values are one constant pair
-// (the host selects this kernel only when that holds), so levels below S0
-// use scalar operations on the per-level constants and the rest four
-// registers.
+// of 32 columns in the VP's row-major order).  The pivots m_s, r m_s of a
+// zero-flux end converge, and from level S0 on their FP32 values are one
+// constant pair (the host selects this kernel only when that holds): those
+// levels use one coefficient pair held in registers, levels below S0 the
+// per-level pairs (c, c) of the kernel parameters.
 template <class TS, class TC, int NZ, int S0, bool JAC = false>
 __device__ __forceinline__ int process_item_twin(const StepParams<TC> &p, const GridDev &g,
                                                  const VPDev &vp, int chunk, long long t, int src,
                                                  int lane, bool do_mass, LaneSum<TC> &acc) {
     static_assert(sizeof(TS) == 4 && sizeof(TC) == 4, "twin kernels are FP32");
     constexpr int H = NZ / 2;
-    static_assert(S0 >= 1 && S0 < H, "converged pivots from level S0");
+    static_assert(S0 >= 1 && S0 < H && S0 <= kTwinS0, "converged pivots from level S0");
     const ColGeom cg = col_geom(g, vp, chunk, lane);
     const int plane = g.plane;
     const TS *in = static_cast<const TS *>(g.q[src]);
@@ -934,13 +933,12 @@ __device__ __forceinline__ int process_item_twin(const StepParams<TC> &p, const 
     for (int r = 0; r < kc; ++r) {
         // both halves eliminate toward the middle (from level S0 on the
         // forward multiplier e_s is 1: no multiply)
-        float2 pp = f2(y2[0].x * cf.e[0], y2[0].y * cf.e[0]);
+        float2 pp = mul2(y2[0], cf.e2[0]);
         y2[0] = pp;
 #pragma unroll
         for (int s = 1; s < H; ++s) {
             if (s < S0) {
-                pp = f2(fmaT(pp.x, cf.rm[s], y2[s].x * cf.e[s]),
-                        fmaT(pp.y, cf.rm[s], y2[s].y * cf.e[s]));
+                pp = fma2(pp, cf.rm2[s], mul2(y2[s], cf.e2[s]));
             } else {
                 pp = fma2(pp, rminf, y2[s]);
             }
@@ -952,7 +950,7 @@ __device__ __forceinline__ int process_item_twin(const StepParams<TC> &p, const 
 #pragma unroll
         for (int s = H - 2; s >= 0; --s) {
             if (s < S0)
-                y2[s] = f2(fmaT(cf.rm[s], y2[s + 1].x, y2[s].x), fmaT(cf.rm[s], y2[s + 1].y, y2[s].y));
+                y2[s] = fma2(cf.rm2[s], y2[s + 1], y2[s]);
             else
                 y2[s] = fma2(rminf, y2[s + 1], y2[s]);
         }
@@ -1000,7 +998,7 @@ __device__ __forceinline__ int process_item_twin_rt(const StepParams<TC> &p, con
                                                     int src, int lane, bool do_mass,
                                                     LaneSum<TC> &acc) {
     static_assert(sizeof(TS) == 4 && sizeof(TC) == 4, "twin kernels are FP32");
-    static_assert(HMAX >= 1 && S0 >= 1, "bucket");
+    static_assert(HMAX >= 1 && S0 >= 1 && S0 <= kTwinS0, "bucket");
     const ColGeom cg = col_geom(g, vp, chunk, lane);
     const int plane = g.plane, nz = g.nz;
     const int hb = (nz + 1) / 2, ht = nz / 2;
@@ -1065,14 +1063,13 @@ __device__ __forceinline__ int process_item_twin_rt(const StepParams<TC> &p, con
     const float2 rminf = f2(cf.rm[S0], cf.rm[S0]);
     int rc = cf.resc_every;
     for (int r = 0; r < kc; ++r) {
-        float2 pp = f2(y2[0].x * cf.e[0], y2[0].y * cf.e[0]);
+        float2 pp = mul2(y2[0], cf.e2[0]);
         y2[0] = pp;
 #pragma unroll
         for (int s = 1; s < HMAX; ++s) {
             float2 np;
             if (s < S0)
-                np = f2(fmaT(pp.x, cf.rm[s], y2[s].x * cf.e[s]),
-                        fmaT(pp.y, cf.rm[s], y2[s].y * cf.e[s]));
+                np = fma2(pp, cf.rm2[s], mul2(y2[s], cf.e2[s]));
             else
                 np = fma2(pp, rminf, y2[s]);
             const bool inl = s < hb, inh = s < ht;
@@ -1087,7 +1084,7 @@ __device__ __forceinline__ int process_item_twin_rt(const StepParams<TC> &p, con
         for (int s = HMAX - 2; s >= 0; --s) {
             float2 bk;
             if (s < S0)
-                bk = f2(fmaT(cf.rm[s], y2[s + 1].x, y2[s].x), fmaT(cf.rm[s], y2[s + 1].y, y2[s].y));
+                bk = fma2(cf.rm2[s], y2[s + 1], y2[s]);
             else
                 bk = fma2(rminf, y2[s + 1], y2[s]);
             y2[s] = f2(s == hb - 1 ? xl : (s < hb - 1 ? bk.x : y2[s].x),
