@@ -806,8 +806,8 @@ __device__ __forceinline__ void reduce_mass(const StepParams<TC> &p, long long t
 // ------------------------------------------------------------ work stealing
 // Table mode with stealing: a processor's warps take items from its own
 // counter; once it runs dry they scan every processor's remaining count
-// (one lane per processor, 32 at a time) and take the next item of the
-// processor with the most left.  Each counter hands out every index once,
+// (a lane reads up to 8 processors' counts at once) and take the next item
+// of the processor with the most left (ties: the lowest index).  Each counter hands out every index once,
 // so no item runs twice.  Returns the global item index, or -1 when no
 // processor has work left.
 template <class TC>
@@ -818,23 +818,32 @@ __device__ __forceinline__ int pop_with_stealing(const StepParams<TC> &p, int pa
     if (lane == 0) c = (int)atomicAdd(&ctr[bin], 1u);
     c = __shfl_sync(0xffffffffu, c, 0);
     if (c < p.bin_start[bin + 1] - p.bin_start[bin]) return p.bin_start[bin] + c;
+    constexpr int kScan = 8;           // processors per lane read before reducing
     for (int attempt = 0; attempt < 4 * p.nbins + 8; ++attempt) {
         int best_rem = 0, best_v = -1;
-        for (int base = 0; base < p.nbins; base += kWarp) {
-            const int v = base + lane;
-            int rem = 0;
-            if (v < p.nbins) {
-                const int len = p.bin_start[v + 1] - p.bin_start[v];
-                rem = len - (int)*(volatile unsigned *)&ctr[v];
+        for (int base = 0; base < p.nbins; base += kScan * kWarp) {
+            // all of this lane's counts first (independent loads, one
+            // latency), then the lane's best, then the warp's
+            int rem[kScan];
+#pragma unroll
+            for (int u = 0; u < kScan; ++u) {
+                const int v = base + u * kWarp + lane;
+                rem[u] = 0;
+                if (v < p.nbins)
+                    rem[u] = (p.bin_start[v + 1] - p.bin_start[v]) -
+                             (int)*(volatile unsigned *)&ctr[v];
             }
-            int vv = v;
+            int lr = 0, vv = p.nbins;
+#pragma unroll
+            for (int u = 0; u < kScan; ++u)
+                if (rem[u] > lr) { lr = rem[u]; vv = base + u * kWarp + lane; }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
-                const int r2 = __shfl_xor_sync(0xffffffffu, rem, o);
+                const int r2 = __shfl_xor_sync(0xffffffffu, lr, o);
                 const int v2 = __shfl_xor_sync(0xffffffffu, vv, o);
-                if (r2 > rem || (r2 == rem && v2 < vv)) { rem = r2; vv = v2; }
+                if (r2 > lr || (r2 == lr && v2 < vv)) { lr = r2; vv = v2; }
             }
-            if (rem > best_rem) { best_rem = rem; best_v = vv; }
+            if (lr > best_rem) { best_rem = lr; best_v = vv; }
         }
         if (best_rem <= 0) return -1;
         int got = 0;
