@@ -870,6 +870,26 @@ __device__ __forceinline__ int split_rt_bucket(const StepParams<TC> &p, const Gr
     return process_item_split_rt<TS, TC, HB, JAC>(p, g, vp, chunk, t, src, lane, do_mass, acc);
 }
 
+// Head levels (below S0) of the twin solves: packed pairs (c, c) from the
+// kernel parameters, or scalar operations on the per-level constants -- the
+// latter for the out-of-line Jacobi item code, where the pairs' registers
+// would spill.  The operations per value are the same either way.
+template <bool PACKED>
+__device__ __forceinline__ float2 twin_head_first(const Coef<float> &cf, float2 y) {
+    if constexpr (PACKED) return mul2(y, cf.e2[0]);
+    else return f2(y.x * cf.e[0], y.y * cf.e[0]);
+}
+template <bool PACKED>
+__device__ __forceinline__ float2 twin_head_fwd(const Coef<float> &cf, int s, float2 pp, float2 y) {
+    if constexpr (PACKED) return fma2(pp, cf.rm2[s], mul2(y, cf.e2[s]));
+    else return f2(fmaT(pp.x, cf.rm[s], y.x * cf.e[s]), fmaT(pp.y, cf.rm[s], y.y * cf.e[s]));
+}
+template <bool PACKED>
+__device__ __forceinline__ float2 twin_head_back(const Coef<float> &cf, int s, float2 x1, float2 y) {
+    if constexpr (PACKED) return fma2(cf.rm2[s], x1, y);
+    else return f2(fmaT(cf.rm[s], x1.x, y.x), fmaT(cf.rm[s], x1.y, y.y));
+}
+
 // ------------------------------------------------------------ twin halves
 // One lane per column with the twisted factorisation of the split kernels
 // inside the lane: y2[s] holds (level s, level NZ-1-s), so both halves'
@@ -942,12 +962,12 @@ __device__ __forceinline__ int process_item_twin(const StepParams<TC> &p, const 
     for (int r = 0; r < kc; ++r) {
         // both halves eliminate toward the middle (from level S0 on the
         // forward multiplier e_s is 1: no multiply)
-        float2 pp = mul2(y2[0], cf.e2[0]);
+        float2 pp = twin_head_first<!JAC>(cf, y2[0]);
         y2[0] = pp;
 #pragma unroll
         for (int s = 1; s < H; ++s) {
             if (s < S0) {
-                pp = fma2(pp, cf.rm2[s], mul2(y2[s], cf.e2[s]));
+                pp = twin_head_fwd<!JAC>(cf, s, pp, y2[s]);
             } else {
                 pp = fma2(pp, rminf, y2[s]);
             }
@@ -959,7 +979,7 @@ __device__ __forceinline__ int process_item_twin(const StepParams<TC> &p, const 
 #pragma unroll
         for (int s = H - 2; s >= 0; --s) {
             if (s < S0)
-                y2[s] = fma2(cf.rm2[s], y2[s + 1], y2[s]);
+                y2[s] = twin_head_back<!JAC>(cf, s, y2[s + 1], y2[s]);
             else
                 y2[s] = fma2(rminf, y2[s + 1], y2[s]);
         }
@@ -1072,13 +1092,13 @@ __device__ __forceinline__ int process_item_twin_rt(const StepParams<TC> &p, con
     const float2 rminf = f2(cf.rm[S0], cf.rm[S0]);
     int rc = cf.resc_every;
     for (int r = 0; r < kc; ++r) {
-        float2 pp = mul2(y2[0], cf.e2[0]);
+        float2 pp = twin_head_first<!JAC>(cf, y2[0]);
         y2[0] = pp;
 #pragma unroll
         for (int s = 1; s < HMAX; ++s) {
             float2 np;
             if (s < S0)
-                np = fma2(pp, cf.rm2[s], mul2(y2[s], cf.e2[s]));
+                np = twin_head_fwd<!JAC>(cf, s, pp, y2[s]);
             else
                 np = fma2(pp, rminf, y2[s]);
             const bool inl = s < hb, inh = s < ht;
@@ -1093,7 +1113,7 @@ __device__ __forceinline__ int process_item_twin_rt(const StepParams<TC> &p, con
         for (int s = HMAX - 2; s >= 0; --s) {
             float2 bk;
             if (s < S0)
-                bk = fma2(cf.rm2[s], y2[s + 1], y2[s]);
+                bk = twin_head_back<!JAC>(cf, s, y2[s + 1], y2[s]);
             else
                 bk = fma2(rminf, y2[s + 1], y2[s]);
             y2[s] = f2(s == hb - 1 ? xl : (s < hb - 1 ? bk.x : y2[s].x),

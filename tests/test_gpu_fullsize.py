@@ -12,7 +12,7 @@ torch = pytest.importorskip("torch")
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 
 import oracle  # noqa: E402
-from gpu_common import mass_drift, normwise, report, round_to_storage, tolerance  # noqa: E402
+from gpu_common import Grid, mass_drift, normwise, report, round_to_storage, tolerance  # noqa: E402
 from workloads import get_config  # noqa: E402
 
 
@@ -246,3 +246,71 @@ def test_lognormal_1024_benchmarked_schedule_windows(strategy, nwin):
         assert err / scale <= 1e-5, (c, err / scale)
     step_d, _ = mass_drift(hist, oracle.compensated_sum(q0))
     assert step_d <= 1e-8
+
+
+@pytest.mark.parametrize("nx,ny,nz", [(4720, 4720, 96), (4096, 4095, 128)])
+def test_largest_grids_windows(nx, ny, nz):
+    """The largest grids the ABI takes (nx*ny*nz below 2^31): the last
+    level's offsets come within 0.5% of the int32 limit.  nz 96 runs the
+    twin kernel, nz 128 the one-lane kernel.  64x64 VPs with ragged edges,
+    a seeded k_c array, a field drawn on the device by a seeded torch
+    generator; one step on the static table, then blocked GreedyLB on the
+    measured costs with stealing for a second.  Oracle windows at the
+    highest addresses (the grid's last columns), across the periodic seam
+    and in the middle, each window's input read back from the device before
+    the steps."""
+    from paper_1310_4218_gb300 import lb
+    from workloads import regular_blocks
+    assert 0.99 * 2 ** 31 < nx * ny * nz < 2 ** 31
+    g = Grid(nx, ny, nz, kc_disk=False)
+    dev = torch.device("cuda", 0)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(77 + nz)
+    q0 = torch.rand((nz, ny, nx), generator=gen, device=dev, dtype=torch.float32)
+    q0.mul_(0.8).add_(0.2)
+    q1 = torch.zeros_like(q0)
+    kc = np.random.default_rng(78 + nz).integers(0, 9, size=(ny, nx)).astype(np.int32)
+    kc_t = torch.as_tensor(kc).to(dev)
+
+    nsteps, valid = 2, 8
+    side = nsteps + valid
+    corners = [(nx - 8, ny - 8), (nx - 4, ny // 2), (0, 0), (nx // 2, ny - 3), (1234, 2345)]
+    blocks = []
+    for ci, cj in corners:
+        ii = np.arange(ci - nsteps, ci - nsteps + side) % nx
+        jj = np.arange(cj - nsteps, cj - nsteps + side) % ny
+        sub = q0.index_select(1, torch.as_tensor(jj, device=dev)).index_select(
+            2, torch.as_tensor(ii, device=dev)).to(torch.float64).cpu().numpy()
+        blocks.append((ii, jj, sub))
+
+    x0, y0, vx, vy, R = g.disk
+    d = lb.lb_grid_desc(nx, ny, nz, g.cx, g.cy, g.cz, g.r, lb.DTYPES["f32"], lb.DTYPES["f32"],
+                        q0.data_ptr(), q1.data_ptr(), kc_t.data_ptr(), 0, x0, y0, vx, vy, R,
+                        g.k_in, g.k_out, 0, 0, g.nu)
+    opt = lb.lb_default_options()
+    opt.steal = 1
+    vps = regular_blocks(nx, ny, 64, 64)
+    torch.cuda.synchronize(dev)
+    ctx = lb.lb_create([d], vps, opt, torch.cuda.current_stream(dev).cuda_stream)
+    try:
+        lb.lb_step(ctx, 1)
+        cost, _ = lb.lb_measure_loads(ctx, len(vps))
+        assert (cost > 0).all()
+        lb.lb_rebalance(ctx, "greedy_blocked")
+        lb.lb_step(ctx, 1)
+        lb.lb_sync(ctx)
+        out = q0 if lb.lb_current_field(ctx, 0) == q0.data_ptr() else q1
+        errs, scale = [], 0.0
+        for ii, jj, sub in blocks:
+            og = oracle.OracleGrid(side, side, nz, g.cx, g.cy, g.cz, g.r, False)
+            ref = oracle.run_window(og, sub, 0, 0, side, side, nsteps,
+                                    kc_window=kc[jj][:, ii])[:, nsteps:, nsteps:]
+            assert np.isfinite(ref).all()
+            gpu = out.index_select(1, torch.as_tensor(jj[nsteps:], device=dev)).index_select(
+                2, torch.as_tensor(ii[nsteps:], device=dev)).to(torch.float64).cpu().numpy()
+            errs.append(float(np.abs(gpu - ref).max()))
+            scale = max(scale, float(np.abs(ref).max()))
+    finally:
+        lb.lb_destroy(ctx)
+    report("largest_fp32_%dx%dx%d" % (nx, ny, nz), max_abs=max(errs), normwise=max(errs) / scale)
+    assert max(errs) / scale <= 1e-5, (errs, scale)
