@@ -355,6 +355,9 @@ class StrategyRun:
         pair = "pair" in flags
         one = "one" in flags          # "+one": one lane per column
         twin = "twin" in flags        # "+twin": one lane per column, packed halves
+        # "+df": the dataflow kernel (no grid barrier between steps) where it
+        # applies: the atomic queue on the exact-nz twin kernels
+        dataflow = "df" in flags
         # "+pred": at a k_c re-draw the new array is installed before the
         # balancer runs and the costs are rescaled by the fitted model
         self.predict = "pred" in flags and self.dev_mode
@@ -381,6 +384,7 @@ class StrategyRun:
             opt.threads_hint = 1
         if twin:
             opt.threads_hint = 4
+        opt.dataflow = 1 if dataflow else 0
         kc0 = [epochs[0][gi] for gi in range(len(w.grids))] if epochs else None
         self.sim = Simulation(w.grids, fields, w.vps, kc_arrays=kc0, options=opt, device=dev,
                               stream=stream)
@@ -724,7 +728,7 @@ COMPARED = ("static", "static+steal", "auto", "auto+dev", "auto_spatial+steal",
             "greedy_blocked+steal+dev+pred", "greedy_blocked+steal+dev+pred+thr",
             "greedy_blocked+steal+dev+pred+thr+graph", "greedy_blocked+steal+dev+pred+thr+pair",
             "greedy_blocked+steal+dev+pred+thr+twin", "greedy_blocked+steal+dev+pred+thr+tma",
-            "queue", "queue+dev")
+            "queue", "queue+dev", "queue+dev+df")
 
 
 def main():

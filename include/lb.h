@@ -205,7 +205,17 @@ typedef struct {
                                      (FP32 split columns of nz 32, 64 or 96,
                                      nx % 4 == 0, 16-byte aligned fields);
                                      default 0 */
-    int32_t reserved[4];          /* must be 0 */
+    int32_t dataflow;             /* 1: with the ATOMIC_QUEUE strategy, the
+                                     exact-nz twin kernels (FP32 grids of nz
+                                     32, 64 or 96) run a launch's steps
+                                     without a grid barrier: a work item of
+                                     step s starts once the items owning its
+                                     columns' 4-neighbours have finished step
+                                     s - 1 (same fields bit for bit; global
+                                     sums added in another order); other
+                                     configurations run the barrier kernel
+                                     (lb_info.dataflow says which); default 0 */
+    int32_t reserved[3];          /* must be 0 */
 } lb_options;
 
 /* Fill *opt with the defaults listed above. */
@@ -469,7 +479,8 @@ typedef struct {
                                  per processor (one per warp, each holding
                                  the next work item's input); 0: each warp
                                  loads its own items */
-    int32_t pad0;
+    int32_t dataflow;         /* 1: lb_step currently runs the dataflow
+                                 kernel (lb_options.dataflow) */
 } lb_info;
 
 /* Fill *info (fields above).  Synchronises only when a device balancer call

@@ -66,6 +66,14 @@ struct lb_ctx {
     double *d_feat1 = nullptr, *d_feat2 = nullptr, *d_featn = nullptr;   // predictive cost model
     double *d_fit = nullptr;
     CUtensorMap *d_tmaps = nullptr;    // TMA-staged kernel: [ngrids][2] field maps
+    // dataflow launches (lb_options.dataflow): one block holding the DfState,
+    // the [kDfSlots][ngrids] step sums and the [nitems] done flags, zeroed
+    // before each launch; the queue items' dependency lists (CSR)
+    unsigned char *d_df = nullptr;
+    size_t df_mass_off = 0, df_done_off = 0;
+    int32_t *d_df_dep_start = nullptr;
+    int32_t *d_df_deps = nullptr;
+    size_t df_deps_cap = 0;
     bool predict = false;              // predict_kc active
     bool dev_newer = false;            // device balancer state newer than the host copy
     std::string devbal_off;            // why the device balancer is unavailable ("" = available)
@@ -222,6 +230,50 @@ static std::vector<int> spatial_order(const lb_ctx *ctx) {
 }
 
 // Work items {vp, chunk} for the processor tables and the queue.
+// Dataflow launches: for each queue item, the queue items owning a column
+// of its closed 4-neighbourhood (periodic, itself included), as CSR.  The
+// columns of an item are those the kernel gives its lanes: cols_per_item
+// consecutive columns of the VP in row-major order.
+static void df_dependencies(const lb_ctx *ctx, const std::vector<int2> &qitems,
+                            std::vector<int32_t> &start, std::vector<int32_t> &deps) {
+    const int cpi = ctx->kinfo.cols_per_item;
+    std::vector<std::vector<int32_t>> owner(ctx->grids.size());
+    for (size_t g = 0; g < ctx->grids.size(); ++g)
+        owner[g].assign((size_t)ctx->grids[g].nx * ctx->grids[g].ny, -1);
+    auto each_col = [&](int q, auto &&fn) {
+        const int2 it = qitems[q];
+        const lb_vp &vp = ctx->vps[it.x];
+        const int ncols = vp.w * vp.h;
+        for (int l = 0; l < cpi; ++l) {
+            const int k = it.y * cpi + l;
+            if (k >= ncols) break;
+            const int ly = k / vp.w;
+            fn(vp.grid, vp.x0 + (k - ly * vp.w), vp.y0 + ly);
+        }
+    };
+    for (int q = 0; q < (int)qitems.size(); ++q)
+        each_col(q, [&](int g, int i, int j) { owner[g][(size_t)j * ctx->grids[g].nx + i] = q; });
+    start.assign(qitems.size() + 1, 0);
+    deps.clear();
+    std::vector<int32_t> nb;
+    const int di[5] = {0, 1, -1, 0, 0}, dj[5] = {0, 0, 0, 1, -1};
+    for (int q = 0; q < (int)qitems.size(); ++q) {
+        nb.clear();
+        each_col(q, [&](int g, int i, int j) {
+            const int nx = ctx->grids[g].nx, ny = ctx->grids[g].ny;
+            for (int d = 0; d < 5; ++d) {
+                const int ii = (i + di[d] + nx) % nx, jj = (j + dj[d] + ny) % ny;
+                const int o = owner[g][(size_t)jj * nx + ii];
+                if (o >= 0) nb.push_back(o);
+            }
+        });
+        std::sort(nb.begin(), nb.end());
+        nb.erase(std::unique(nb.begin(), nb.end()), nb.end());
+        deps.insert(deps.end(), nb.begin(), nb.end());
+        start[q + 1] = (int32_t)deps.size();
+    }
+}
+
 static lb_status upload_items(lb_ctx *ctx) {
     const int nv = (int)ctx->vps.size();
     std::vector<int2> items;
@@ -264,6 +316,23 @@ static lb_status upload_items(lb_ctx *ctx) {
                        cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemcpyAsync(ctx->d_bin_start, start.data(), sizeof(int32_t) * start.size(),
                        cudaMemcpyHostToDevice, ctx->stream));
+    std::vector<int32_t> dstart, deps;
+    if (ctx->d_df) {
+        df_dependencies(ctx, qitems, dstart, deps);
+        if (deps.size() > ctx->df_deps_cap) {
+            // the old list may still be read by a launch in flight: cudaFree
+            // waits for the device
+            if (ctx->d_df_deps) cudaFree(ctx->d_df_deps);
+            ctx->d_df_deps = nullptr;
+            ctx->df_deps_cap = 0;
+            CK(cudaMalloc((void **)&ctx->d_df_deps, sizeof(int32_t) * std::max<size_t>(deps.size(), 1)));
+            ctx->df_deps_cap = deps.size();
+        }
+        CK(cudaMemcpyAsync(ctx->d_df_dep_start, dstart.data(), sizeof(int32_t) * dstart.size(),
+                           cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaMemcpyAsync(ctx->d_df_deps, deps.data(), sizeof(int32_t) * deps.size(),
+                           cudaMemcpyHostToDevice, ctx->stream));
+    }
     CK(cudaStreamSynchronize(ctx->stream));
     return push_state(ctx);
 }
@@ -277,7 +346,8 @@ static void free_ctx(lb_ctx *ctx) {
                     ctx->d_last,      ctx->d_assign,   ctx->d_order,     ctx->d_spatial,
                     ctx->d_nchunks,   ctx->d_bstate,   ctx->d_pend,      ctx->d_bhist,
                     ctx->d_ticket,    ctx->d_q,        ctx->d_feat1,     ctx->d_feat2,
-                    ctx->d_featn,     ctx->d_fit,      ctx->d_tmaps};
+                    ctx->d_featn,     ctx->d_fit,      ctx->d_tmaps,     ctx->d_df,
+                    ctx->d_df_dep_start, ctx->d_df_deps};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete ctx;
@@ -388,6 +458,7 @@ extern "C" lb_status lb_create(const lb_grid_desc *grids, int32_t ngrids, const 
     else lb_default_options(&ctx->opt);
     if (ctx->opt.ctas_per_sm < 1) ctx->opt.ctas_per_sm = 1;
     if (ctx->opt.mass_every < 0) ctx->opt.mass_every = 0;
+    ctx->opt.dataflow = ctx->opt.dataflow ? 1 : 0;
     if (!(ctx->opt.ema_alpha > 0.0 && ctx->opt.ema_alpha <= 1.0)) ctx->opt.ema_alpha = 0.5;
     if (!(ctx->opt.refine_tol >= 0.0)) ctx->opt.refine_tol = 0.05;
     if (ctx->opt.barrier_timeout_ns <= 0) ctx->opt.barrier_timeout_ns = 2000000000LL;
@@ -536,6 +607,13 @@ extern "C" lb_status lb_create(const lb_grid_desc *grids, int32_t ngrids, const 
     if (e == cudaSuccess) e = dalloc(&ctx->d_bhist, (size_t)kBalHist * kBalHistCols);
     if (e == cudaSuccess) e = dalloc(&ctx->d_ticket, 1);
     if (e == cudaSuccess && !maps.empty()) e = dalloc(&ctx->d_tmaps, maps.size());
+    if (e == cudaSuccess && ctx->opt.dataflow && ctx->kinfo.df_fn) {
+        ctx->df_mass_off = (sizeof(DfState) + 255) / 256 * 256;
+        ctx->df_done_off =
+            ctx->df_mass_off + (sizeof(double) * kDfSlots * (size_t)ngrids + 255) / 256 * 256;
+        e = dalloc(&ctx->d_df, ctx->df_done_off + sizeof(int32_t) * (size_t)ctx->nitems);
+        if (e == cudaSuccess) e = dalloc(&ctx->d_df_dep_start, (size_t)ctx->nitems + 1);
+    }
     if (e == cudaSuccess && !maps.empty())
         e = cudaMemcpyAsync(ctx->d_tmaps, maps.data(), sizeof(CUtensorMap) * maps.size(),
                             cudaMemcpyHostToDevice, ctx->stream);
@@ -603,6 +681,11 @@ extern "C" lb_status lb_create(const lb_grid_desc *grids, int32_t ngrids, const 
 }
 
 // ------------------------------------------------------------------ step
+// lb_step runs the dataflow kernel: asked for, the kernel has one, queue mode
+static bool df_active(const lb_ctx *ctx) {
+    return ctx->d_df && ctx->kinfo.df_fn && ctx->queue_mode;
+}
+
 template <class TC>
 static lb_status launch(lb_ctx *ctx, int nsteps, const Coef<TC> &coef, int serial_warps = 0) {
     StepParams<TC> p;
@@ -643,11 +726,21 @@ static lb_status launch(lb_ctx *ctx, int nsteps, const Coef<TC> &coef, int seria
     CK(cudaMemsetAsync(ctx->d_bar, 0, 2 * sizeof(unsigned), ctx->stream));
     CK(cudaMemsetAsync(ctx->d_qhead, 0, 2 * sizeof(unsigned), ctx->stream));
     CK(cudaMemsetAsync(ctx->d_bin_ctr, 0, 2 * sizeof(unsigned) * ctx->nbins, ctx->stream));
+    const bool df = df_active(ctx) && serial_warps == 0;
+    if (df) {
+        p.df = reinterpret_cast<DfState *>(ctx->d_df);
+        p.df_mass = reinterpret_cast<double *>(ctx->d_df + ctx->df_mass_off);
+        p.df_done = reinterpret_cast<int32_t *>(ctx->d_df + ctx->df_done_off);
+        p.df_dep_start = ctx->d_df_dep_start;
+        p.df_deps = ctx->d_df_deps;
+        CK(cudaMemsetAsync(ctx->d_df, 0, ctx->df_done_off + sizeof(int32_t) * ctx->nitems,
+                           ctx->stream));
+    }
     cudaLaunchConfig_t cfg;
     std::memset(&cfg, 0, sizeof(cfg));
     cfg.gridDim = dim3(ctx->nbins);
     cfg.blockDim = dim3(ctx->threads);
-    cfg.dynamicSmemBytes = ctx->dyn_smem;
+    cfg.dynamicSmemBytes = df ? 0 : ctx->dyn_smem;
     cfg.stream = ctx->stream;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;
@@ -655,7 +748,7 @@ static lb_status launch(lb_ctx *ctx, int nsteps, const Coef<TC> &coef, int seria
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     void *args[] = {&p};
-    CK(cudaLaunchKernelExC(&cfg, ctx->kinfo.fn, args));
+    CK(cudaLaunchKernelExC(&cfg, df ? ctx->kinfo.df_fn : ctx->kinfo.fn, args));
     return LB_OK;
 }
 
@@ -1355,6 +1448,7 @@ extern "C" lb_status lb_get_info(lb_ctx *ctx, lb_info *info) {
     info->item_w = ctx->kinfo.tile_w ? ctx->kinfo.tile_w : ctx->kinfo.cols_per_item;
     info->item_h = ctx->kinfo.tile_w ? ctx->kinfo.tile_h : 0;
     info->staged_slots = ctx->kinfo.tma_slots;
+    info->dataflow = df_active(ctx) ? 1 : 0;
     return LB_OK;
 }
 

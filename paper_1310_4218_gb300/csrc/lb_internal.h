@@ -76,6 +76,18 @@ struct Coef {
     float2 e2[kTwinS0], rm2[kTwinS0];
 };
 
+// Dataflow launches (lb_options.dataflow): the per-launch state, zeroed by
+// the host before each launch.  Items of every step come from one queue
+// (index step * nitems + item); steps are reduced in order through
+// kDfSlots slots of per-step counts and sums.
+constexpr int kDfSlots = 4;
+struct DfState {
+    unsigned long long qhead;      // next queue index
+    unsigned reduced;              // steps of this launch reduced, in order
+    unsigned started;              // CTAs that have read the step clock
+    unsigned cnt[kDfSlots];        // finished items of the step in each slot
+};
+
 template <class TC>
 struct StepParams {
     const GridDev *grids;
@@ -105,6 +117,11 @@ struct StepParams {
                                    // instead of t0/parity0, advanced at the end (may be null)
     const void *tmaps;             // TMA-staged kernels: [ngrids][2] tensor maps of the
                                    // fields (128 bytes each), else null
+    DfState *df;                   // dataflow launches: per-launch state (else null)
+    double *df_mass;               // [kDfSlots][ngrids] global-sum partials per step slot
+    int32_t *df_done;              // [nitems] steps each queue item has finished
+    const int32_t *df_dep_start;   // [nitems + 1] CSR of each queue item's dependencies:
+    const int32_t *df_deps;        // the items owning its closed 4-neighbourhood
     Coef<TC> coef;
 };
 
@@ -112,6 +129,7 @@ struct StepParams {
 // nz-variant) triple, or nullptr.  exact=1: specialised to nz == variant.
 struct KernelInfo {
     const void *fn;
+    const void *df_fn;  // the dataflow variant of fn (exact-nz twin kernels), else null
     int threads;
     int nz_variant;
     int exact;

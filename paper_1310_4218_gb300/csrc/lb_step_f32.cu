@@ -1,5 +1,6 @@
 // FP32 storage, FP32 compute: the persistent step kernels specialised to
 // one column length.
+#include "lb_step_df.cuh"
 #include "lb_step_tma.cuh"
 
 namespace lbk {
@@ -21,7 +22,7 @@ bool kernels_f32(int nz_max, int nz_min, bool same, int threads_hint, bool stage
     if (same && nz_max == 32) {
         if (one_lane) *out = kernel_entry<float, float, 32, true, 1, 512>();
         else if (staged) *out = kernel_entry_tma<32, 1024>();
-        else if (twin) *out = kernel_entry<float, float, 32, true, 1, 1024, false, 0, true>();
+        else if (twin) *out = kernel_entry_twin_df<32, 1024>();
         else if (pair) *out = kernel_entry<float, float, 32, true, 1, 960, true, 16>();
         else *out = kernel_entry<float, float, 32, true, 1, 1024, true>();
         return true;
@@ -29,7 +30,7 @@ bool kernels_f32(int nz_max, int nz_min, bool same, int threads_hint, bool stage
     if (same && nz_max == 64) {
         if (one_lane) *out = kernel_entry<float, float, 64, true, 1, 512>();
         else if (staged) *out = kernel_entry_tma<64, 768>();
-        else if (twin) *out = kernel_entry<float, float, 64, true, 1, 640, false, 0, true>();
+        else if (twin) *out = kernel_entry_twin_df<64, 640>();
         else if (pair) *out = kernel_entry<float, float, 64, true, 1, 768, true, 16>();
         else *out = kernel_entry<float, float, 64, true, 1, 768, true>();
         return true;
@@ -37,7 +38,7 @@ bool kernels_f32(int nz_max, int nz_min, bool same, int threads_hint, bool stage
     if (same && nz_max == 96) {
         if (one_lane) *out = kernel_entry<float, float, 96, true, 1, 384>();
         else if (staged) *out = kernel_entry_tma<96, 512>();
-        else if (twin) *out = kernel_entry<float, float, 96, true, 1, 512, false, 0, true>();
+        else if (twin) *out = kernel_entry_twin_df<96, 512>();
         else if (pair) *out = kernel_entry<float, float, 96, true, 1, 768, true, 16>();
         else *out = kernel_entry<float, float, 96, true, 1, 768, true>();
         return true;

@@ -1570,6 +1570,7 @@ inline KernelInfo kernel_entry() {
     constexpr bool PAIR = PAIRW > 0;
     KernelInfo k;
     k.fn = (const void *)&lb_step_kernel<TS, TC, NZ, EXACT, NZLO, THREADS, SPLIT, PAIRW, TWIN, MINB>;
+    k.df_fn = nullptr;
     k.threads = THREADS;
     k.nz_variant = NZ;
     k.exact = EXACT ? 1 : 0;

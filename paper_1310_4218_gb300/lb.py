@@ -58,7 +58,8 @@ class lb_options(ctypes.Structure):
                 ("ema_alpha", ctypes.c_double), ("refine_tol", ctypes.c_double),
                 ("barrier_timeout_ns", ctypes.c_int64), ("threads_hint", ctypes.c_int32),
                 ("steal", ctypes.c_int32), ("predict_kc", ctypes.c_int32),
-                ("staged_loads", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
+                ("staged_loads", ctypes.c_int32), ("dataflow", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 3)]
 
 
 class lb_info(ctypes.Structure):
@@ -68,7 +69,7 @@ class lb_info(ctypes.Structure):
                 ("step", ctypes.c_int64), ("work_items", ctypes.c_int64),
                 ("strategy", ctypes.c_int32), ("regs_per_thread", ctypes.c_int32),
                 ("item_w", ctypes.c_int32), ("item_h", ctypes.c_int32),
-                ("staged_slots", ctypes.c_int32), ("pad0", ctypes.c_int32)]
+                ("staged_slots", ctypes.c_int32), ("dataflow", ctypes.c_int32)]
 
 
 _P = ctypes.c_void_p

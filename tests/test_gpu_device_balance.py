@@ -146,17 +146,15 @@ def test_auto_strategies_switch_on_the_device():
     host.close()
 
 
-def test_more_processors_than_the_register_greedy():
-    """Two processors per SM (over 256; the 256-thread FP64 kernel fits
-    twice): GreedyLB keeps its loads in shared memory instead of registers."""
+@pytest.mark.parametrize("ctas", [2, 4])
+def test_more_processors_than_the_register_greedy(ctas):
+    """Two or four processors per SM (304 or 608 processors, over 256: the
+    nz-96 FP32 kernels for shared SMs): GreedyLB keeps its loads in shared
+    memory instead of registers."""
     from paper_1310_4218_gb300 import lb
-    from paper_1310_4218_gb300.lb import LBError
-    try:
-        g, q, vps, dev, host = twin("4800vps", nz=32, prec="f64", ctas_per_sm=2)
-    except LBError as e:
-        pytest.skip("two processors per SM not co-resident: %s" % e)
+    g, q, vps, dev, host = twin("4800vps", nz=96, prec="f32", ctas_per_sm=ctas)
     nb = dev.info().nprocs
-    assert nb > 256
+    assert nb == ctas * dev.info().nsm and nb > 256
     costs = costs_of("ties", len(vps), 5)
     for strategy in ("greedy", "greedy_spatial", "greedy_blocked", "refine_swap"):
         dev.set_costs(costs)
