@@ -74,6 +74,8 @@ struct lb_ctx {
     int32_t *d_df_dep_start = nullptr;
     int32_t *d_df_deps = nullptr;
     size_t df_deps_cap = 0;
+    int32_t *d_df_inl = nullptr;       // [nitems][kDfDeps] lists padded with -1
+    bool df_inline = false;            // every item has at most kDfDeps
     bool predict = false;              // predict_kc active
     bool dev_newer = false;            // device balancer state newer than the host copy
     std::string devbal_off;            // why the device balancer is unavailable ("" = available)
@@ -316,7 +318,7 @@ static lb_status upload_items(lb_ctx *ctx) {
                        cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemcpyAsync(ctx->d_bin_start, start.data(), sizeof(int32_t) * start.size(),
                        cudaMemcpyHostToDevice, ctx->stream));
-    std::vector<int32_t> dstart, deps;
+    std::vector<int32_t> dstart, deps, inl;
     if (ctx->d_df) {
         df_dependencies(ctx, qitems, dstart, deps);
         if (deps.size() > ctx->df_deps_cap) {
@@ -332,6 +334,17 @@ static lb_status upload_items(lb_ctx *ctx) {
                            cudaMemcpyHostToDevice, ctx->stream));
         CK(cudaMemcpyAsync(ctx->d_df_deps, deps.data(), sizeof(int32_t) * deps.size(),
                            cudaMemcpyHostToDevice, ctx->stream));
+        ctx->df_inline = true;
+        for (size_t q = 0; q + 1 < dstart.size(); ++q)
+            ctx->df_inline = ctx->df_inline && dstart[q + 1] - dstart[q] <= kDfDeps;
+        if (ctx->df_inline) {
+            inl.assign((dstart.size() - 1) * kDfDeps, -1);
+            for (size_t q = 0; q + 1 < dstart.size(); ++q)
+                for (int32_t k = dstart[q]; k < dstart[q + 1]; ++k)
+                    inl[q * kDfDeps + (k - dstart[q])] = deps[k];
+            CK(cudaMemcpyAsync(ctx->d_df_inl, inl.data(), sizeof(int32_t) * inl.size(),
+                               cudaMemcpyHostToDevice, ctx->stream));
+        }
     }
     CK(cudaStreamSynchronize(ctx->stream));
     return push_state(ctx);
@@ -347,7 +360,7 @@ static void free_ctx(lb_ctx *ctx) {
                     ctx->d_nchunks,   ctx->d_bstate,   ctx->d_pend,      ctx->d_bhist,
                     ctx->d_ticket,    ctx->d_q,        ctx->d_feat1,     ctx->d_feat2,
                     ctx->d_featn,     ctx->d_fit,      ctx->d_tmaps,     ctx->d_df,
-                    ctx->d_df_dep_start, ctx->d_df_deps};
+                    ctx->d_df_dep_start, ctx->d_df_deps, ctx->d_df_inl};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete ctx;
@@ -613,6 +626,7 @@ extern "C" lb_status lb_create(const lb_grid_desc *grids, int32_t ngrids, const 
             ctx->df_mass_off + (sizeof(double) * kDfSlots * (size_t)ngrids + 255) / 256 * 256;
         e = dalloc(&ctx->d_df, ctx->df_done_off + sizeof(int32_t) * (size_t)ctx->nitems);
         if (e == cudaSuccess) e = dalloc(&ctx->d_df_dep_start, (size_t)ctx->nitems + 1);
+        if (e == cudaSuccess) e = dalloc(&ctx->d_df_inl, (size_t)ctx->nitems * kDfDeps);
     }
     if (e == cudaSuccess && !maps.empty())
         e = cudaMemcpyAsync(ctx->d_tmaps, maps.data(), sizeof(CUtensorMap) * maps.size(),
@@ -733,6 +747,7 @@ static lb_status launch(lb_ctx *ctx, int nsteps, const Coef<TC> &coef, int seria
         p.df_done = reinterpret_cast<int32_t *>(ctx->d_df + ctx->df_done_off);
         p.df_dep_start = ctx->d_df_dep_start;
         p.df_deps = ctx->d_df_deps;
+        p.df_inl = ctx->df_inline ? ctx->d_df_inl : nullptr;
         CK(cudaMemsetAsync(ctx->d_df, 0, ctx->df_done_off + sizeof(int32_t) * ctx->nitems,
                            ctx->stream));
     }

@@ -81,6 +81,7 @@ struct Coef {
 // (index step * nitems + item); steps are reduced in order through
 // kDfSlots slots of per-step counts and sums.
 constexpr int kDfSlots = 4;
+constexpr int kDfDeps = 16;        // dependencies per item held inline (else the CSR)
 struct DfState {
     unsigned long long qhead;      // next queue index
     unsigned reduced;              // steps of this launch reduced, in order
@@ -122,6 +123,8 @@ struct StepParams {
     int32_t *df_done;              // [nitems] steps each queue item has finished
     const int32_t *df_dep_start;   // [nitems + 1] CSR of each queue item's dependencies:
     const int32_t *df_deps;        // the items owning its closed 4-neighbourhood
+    const int32_t *df_inl;         // [nitems][kDfDeps] the same lists padded with -1
+                                   // (null when an item has more than kDfDeps)
     Coef<TC> coef;
 };
 

@@ -28,8 +28,10 @@
 //
 // Ordering: a finished item publishes done[c] = s + 1 with a release (every
 // lane fences after its stores, then lane 0 writes the flag); waiting lanes
-// read the flags with acquire loads, and every lane fences before the
-// item's loads.  Every wait is bounded by the ctx's time limit
+// read the flags with acquire loads, and a warp barrier orders every lane's
+// loads of the item after them.  An item's dependency list (at most
+// kDfDeps entries, else the CSR) and its table entries load before the
+// waits, so the flags cost one load latency beside the table lookups.  Every wait is bounded by the ctx's time limit
 // (LB_ETIMEOUT; a status set elsewhere ends the wait at once), after which
 // the warp leaves the launch.  The protocol, with its deadlock freedom, is
 // modelled on the host in tests/test_dataflow_model.py.
@@ -176,20 +178,27 @@ lb_step_kernel_df(const __grid_constant__ StepParams<TC> p) {
             w = df_wait_ge(reinterpret_cast<const int *>(&p.df->reduced), s - kDfSlots + 1,
                            p.timeout_ns, p.status);
         if (!__shfl_sync(0xffffffffu, w, 0)) { ok = false; break; }
+        // the item's tables (never written during a launch) load beside its
+        // dependency list, before the waits
+        const int2 it = p.items[c];
+        const int dl = (p.df_inl && lane < kDfDeps) ? p.df_inl[(size_t)c * kDfDeps + lane] : -1;
+        const VPDev vp = p.vps[it.x];
         // every item owning a column of c's closed neighbourhood has finished step s - 1
         if (s > 0) {
             bool got = true;
-            for (int k = p.df_dep_start[c] + lane; k < p.df_dep_start[c + 1]; k += kWarp)
-                got = got && df_wait_ge(p.df_done + p.df_deps[k], s, p.timeout_ns, p.status);
+            if (p.df_inl) {
+                if (dl >= 0) got = df_wait_ge(p.df_done + dl, s, p.timeout_ns, p.status);
+            } else {
+                for (int k = p.df_dep_start[c] + lane; k < p.df_dep_start[c + 1]; k += kWarp)
+                    got = got && df_wait_ge(p.df_done + p.df_deps[k], s, p.timeout_ns, p.status);
+            }
             if (!__all_sync(0xffffffffu, got)) { ok = false; break; }
-            __threadfence();                    // every lane after the observed flags
+            __syncwarp();                       // every lane's loads after the acquiring lanes'
         }
 
         const long long t = t0 + s;
         const int src = (parity0 + s) & 1;
         const bool do_mass = p.mass_every > 0 && ((t + 1) % p.mass_every) == 0;
-        const int2 it = p.items[c];
-        const VPDev vp = p.vps[it.x];
         const GridDev &g = p.grids[vp.grid];
         if (do_mass && vp.grid != cur_grid) {
             if (cur_grid >= 0) df_add_mass(p, s, cur_grid, acc, lane);
