@@ -77,6 +77,11 @@ def parse():
                     help="instead of the benchmark: per-VP costs measured concurrently with 1, 2 "
                          "or 4 processors per SM and in serialized steps, how well each balances, "
                          "and the throughput the serialized steps cost")
+    ap.add_argument("--shard-study", action="store_true",
+                    help="instead of the benchmark: a sharded run of two ranks emulated on one "
+                         "GPU (two ctxs, halo columns packed and unpacked every step): each "
+                         "rank's step, the exchange per step and its bytes, and the assembled "
+                         "field against one ctx")
     return ap.parse_args()
 
 
@@ -722,6 +727,102 @@ def measurement_study(args):
     print(json.dumps(out), flush=True)
 
 
+def shard_study(args, nranks=2, nsteps=20):
+    """The sharded run of shard.py (the paper's processors as ranks, Sec. III,
+    with the halo exchange of Fig. 2) on one GPU: `nranks` ctxs over the same
+    grid, each running the VPs of one 2D block, with the halo columns moved
+    by lb_pack_columns / lb_unpack_columns before every step.  The ranks run
+    one after the other here, so the numbers are each rank's step and the
+    exchange's cost, not a scaling curve; the assembled owned columns must
+    equal one ctx running every VP, bit for bit."""
+    import time
+
+    import torch
+
+    from paper_1310_4218_gb300 import lb, shard
+    from paper_1310_4218_gb300.sim import Simulation
+    from workloads import get_config
+
+    dev = torch.device("cuda", 0)
+    w = get_config(args.workload)
+    kc = [w.kc_array(gi, 0) for gi in range(len(w.grids))] if w.kc_epoch_steps else None
+    fields = [g.initial_field() for g in w.grids]
+
+    def make():
+        s = Simulation(w.grids, fields, w.vps, kc_arrays=kc, options=lb.lb_default_options(),
+                       device=dev)
+        s.rebalance("queue")
+        return s
+
+    whole = make()
+    parts = [make() for _ in range(nranks)]
+    st = [shard.GPUStepper(s) for s in parts]
+    owner = shard.block_owners(w.vps, w.grids, nranks)
+    for r in range(nranks):
+        st[r].set_owned((owner == r).astype(np.uint8))
+    plans = [shard.HaloPlan(w.vps, w.grids, owner, r, nranks) for r in range(nranks)]
+
+    def exchange():
+        for r in range(nranks):
+            for (gi, p), cells in plans[r].send.items():
+                st[p].unpack(gi, cells, st[r].pack(gi, cells))
+        for s in parts:
+            s.stream.synchronize()
+
+    def event():
+        return torch.cuda.Event(enable_timing=True)
+
+    for _ in range(3):
+        exchange()
+        for s in st:
+            s.step(1)
+        whole.step(1)
+    torch.cuda.synchronize(dev)
+    t_x, t_rank, t_whole = [], [[] for _ in range(nranks)], []
+    for _ in range(nsteps):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        exchange()
+        t_x.append((time.perf_counter() - t0) * 1e3)
+        for r in range(nranks):
+            a, b = event(), event()
+            a.record(parts[r].stream)
+            st[r].step(1)
+            b.record(parts[r].stream)
+            t_rank[r].append((a, b))
+        a, b = event(), event()
+        a.record(whole.stream)
+        whole.step(1)
+        b.record(whole.stream)
+        t_whole.append((a, b))
+    torch.cuda.synchronize(dev)
+    equal = True
+    for gi, g in enumerate(w.grids):
+        ref = whole.field(gi).reshape(g.nz, -1)
+        got = np.zeros_like(ref)
+        for r in range(nranks):
+            cols = np.concatenate([shard.vp_cells(vp, g.nx) for v, vp in enumerate(w.vps)
+                                   if owner[v] == r and vp[0] == gi])
+            got[:, cols] = parts[r].field(gi).reshape(g.nz, -1)[:, cols]
+        equal = equal and bool(np.array_equal(got, ref))
+    esize = {"f64": 8, "f32": 4, "bf16": 2}
+    halo = [sum(len(c) * w.grids[gi].nz * esize[w.grids[gi].storage]
+                for (gi, _), c in plans[r].recv.items()) for r in range(nranks)]
+    med = lambda ts: statistics.median(a.elapsed_time(b) for a, b in ts)
+    out = {"study": "sharded run, ranks emulated on one GPU (Sec. III, Fig. 2)",
+           "workload": w.name, "ranks": nranks, "steps": nsteps,
+           "one_ctx_step_ms": med(t_whole),
+           "rank_step_ms": [med(t) for t in t_rank],
+           "owned_columns": [int(sum(vp[3] * vp[4] for v, vp in enumerate(w.vps) if owner[v] == r))
+                             for r in range(nranks)],
+           "halo_bytes_received_per_step": halo,
+           "exchange_ms_per_step": statistics.median(t_x),
+           "assembled_field_equals_one_ctx": equal}
+    for s in parts + [whole]:
+        s.close()
+    print(json.dumps(out), flush=True)
+
+
 COMPARED = ("static", "static+steal", "auto", "auto+dev", "auto_spatial+steal",
             "auto_spatial+steal+dev", "greedy_blocked+dev", "greedy_blocked+dev+pred",
             "greedy_blocked+dev+pred+thr", "greedy_blocked+steal+dev",
@@ -740,6 +841,10 @@ def main():
     if args.measure_study:
         if rank == 0:
             measurement_study(args)
+        return
+    if args.shard_study:
+        if rank == 0:
+            shard_study(args)
         return
 
     import torch
