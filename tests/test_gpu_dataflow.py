@@ -144,3 +144,44 @@ def test_dataflow_wait_limit_is_reported_and_ctx_recovers():
     assert e.value.status == lb.LB_ETIMEOUT
     sim.sync()
     sim.close()
+
+
+def test_dataflow_two_grids_and_owned_subsets():
+    """Two grids in one ctx (dependencies never cross grids), then the same
+    ctx restricted to half of its VPs (lb_set_owned: the other VPs have no
+    work items, so their columns have no owner in the dependency lists):
+    fields equal the barrier kernel's bit for bit on every owned column."""
+    from paper_1310_4218_gb300 import lb
+    from paper_1310_4218_gb300.sim import Simulation
+    g1 = Grid(64, 48, 96, disk=(10, 10, 1, 1, 9), k_in=7, k_out=1)
+    g2 = Grid(40, 56, 96, -0.5, 0.5, 0.0, disk=(20, 30, 1, 0, 8), k_in=5, k_out=1)
+    q1 = round_to_storage(random_field(g1, 77), "f32")
+    q2 = round_to_storage(random_field(g2, 78), "f32")
+    vps = regular_blocks(64, 48, 16, 8, grid=0) + regular_blocks(40, 56, 8, 14, grid=1)
+
+    def sim(df):
+        o = lb.lb_default_options()
+        o.dataflow = df
+        s = Simulation([g1, g2], [q1, q2], vps, options=o)
+        s.rebalance("queue")
+        return s
+
+    a, b = sim(1), sim(0)
+    assert a.info().dataflow == 1
+    a.step(6)
+    b.step(6)
+    for gi in (0, 1):
+        assert np.array_equal(a.field(gi), b.field(gi))
+    owned = (np.arange(len(vps)) % 2).astype(np.uint8)
+    for s in (a, b):
+        lb.lb_set_owned(s.ctx, owned)
+    assert a.info().dataflow == 1
+    a.step(5)
+    b.step(5)
+    for gi, g in enumerate((g1, g2)):
+        fa, fb = a.field(gi), b.field(gi)
+        for v, (vg, x0, y0, w, h) in enumerate(vps):
+            if vg == gi and owned[v]:
+                assert np.array_equal(fa[:, y0:y0 + h, x0:x0 + w], fb[:, y0:y0 + h, x0:x0 + w])
+    a.close()
+    b.close()
