@@ -27,9 +27,11 @@
 // read it.
 //
 // Ordering: a finished item publishes done[c] = s + 1 with a release (every
-// lane fences after its stores, then lane 0 writes the flag); waiting lanes
-// read the flags with acquire loads, and a warp barrier orders every lane's
-// loads of the item after them.  An item's dependency list (at most
+// lane fences after its stores, then lane 0 writes the flag) at the start of
+// the warp's next iteration, after the next pop and table loads and before
+// any wait (so no warp waits while holding an unpublished flag); waiting
+// lanes read the flags with acquire loads, and a warp barrier orders every
+// lane's loads of the item after them.  An item's dependency list (at most
 // kDfDeps entries, else the CSR) and its table entries load before the
 // waits, so the flags cost one load latency beside the table lookups.  Every wait is bounded by the ctx's time limit
 // (LB_ETIMEOUT; a status set elsewhere ends the wait at once), after which
@@ -162,12 +164,30 @@ lb_step_kernel_df(const __grid_constant__ StepParams<TC> p) {
     unsigned cnt = 0;
     LaneSum<TC> acc;
     bool ok = true;
+    // the warp's last finished item, whose flag is published at the start
+    // of the next iteration -- after the pop and the table loads, so that
+    // the fence finds the item's stores drained -- and before any wait
+    int pend = -1, pend_s = 0;
+    auto publish = [&]() {
+        if (pend >= 0) {
+            __threadfence();                    // every lane's stores before the flag
+            __syncwarp();
+            if (lane == 0) atomicExch(p.df_done + pend, pend_s + 1);
+            pend = -1;
+        }
+    };
     for (;;) {
         unsigned long long i = 0;
         if (lane == 0) i = atomicAdd(&p.df->qhead, 1ull);
         i = __shfl_sync(0xffffffffu, i, 0);
         if (i >= total) break;
         const int s = (int)(i / n), c = (int)(i % n);
+        // the item's tables (never written during a launch) load beside its
+        // dependency list, before the waits
+        const int2 it = p.items[c];
+        const int dl = (p.df_inl && lane < kDfDeps) ? p.df_inl[(size_t)c * kDfDeps + lane] : -1;
+        const VPDev vp = p.vps[it.x];
+        publish();
         if (s != cur_s) {
             if (!df_flush(p, t0, parity0, cur_s, cur_grid, cnt, acc, lane)) { ok = false; break; }
             cur_s = s;
@@ -178,11 +198,6 @@ lb_step_kernel_df(const __grid_constant__ StepParams<TC> p) {
             w = df_wait_ge(reinterpret_cast<const int *>(&p.df->reduced), s - kDfSlots + 1,
                            p.timeout_ns, p.status);
         if (!__shfl_sync(0xffffffffu, w, 0)) { ok = false; break; }
-        // the item's tables (never written during a launch) load beside its
-        // dependency list, before the waits
-        const int2 it = p.items[c];
-        const int dl = (p.df_inl && lane < kDfDeps) ? p.df_inl[(size_t)c * kDfDeps + lane] : -1;
-        const VPDev vp = p.vps[it.x];
         // every item owning a column of c's closed neighbourhood has finished step s - 1
         if (s > 0) {
             bool got = true;
@@ -215,18 +230,21 @@ lb_step_kernel_df(const __grid_constant__ StepParams<TC> p) {
             kc = run_item<TS, TC, NZ, EXACT, NZLO, false, TWIN, false>(p, g, vp, it.y, t, src, lane,
                                                                        do_mass, acc);
         }
-        __threadfence();                        // every lane's stores before the flag
         __syncwarp();
         const long long c1 = clock64();
         const unsigned ksum = __reduce_add_sync(0xffffffffu, (unsigned)kc);
         if (lane == 0) {
-            atomicExch(p.df_done + c, s + 1);
             atomicAdd(&p.vp_cycles[it.x], (unsigned long long)(c1 - c0));
             if (p.sweeps) atomicAdd(p.sweeps, (unsigned long long)ksum * (unsigned)g.nz);
         }
+        pend = c;
+        pend_s = s;
         ++cnt;
     }
-    if (ok) df_flush(p, t0, parity0, cur_s, cur_grid, cnt, acc, lane);
+    if (ok) {
+        publish();
+        df_flush(p, t0, parity0, cur_s, cur_grid, cnt, acc, lane);
+    }
     if (lane == 0) atomicMax(&s_tend, (unsigned long long)clock64());
     __syncthreads();
     if (threadIdx.x == 0) {

@@ -14,7 +14,8 @@ step or runs out of items; the flush that completes a step reduces it, in
 step order, clears the slot and advances `reduced`; a warp starts an item
 of step s >= K only once step s - K is reduced.  The warp that reduces
 the launch's last step advances the device clock once every CTA has read
-it.
+it.  A warp publishes its finished item's flag at the start of its next
+iteration, before any wait (and at its exit).
 
 The model checks, for every interleaving: each read sees the value of the
 step before, no write lands before the previous step's readers are done,
@@ -98,14 +99,22 @@ class Model:
             self.started += 1
             yield True
         cur_s, my_cnt, my_mass = -1, 0, []
+        pend = None                              # finished item, flag not yet published
         while True:
             i = self.qhead
             self.qhead += 1
             yield True
             if i >= self.nsteps * self.n:
+                if pend is not None:
+                    self.done[pend[0]] = pend[1] + 1
+                    yield True
                 yield from self.flush(cur_s, my_cnt, my_mass)
                 return
             s, c = divmod(i, self.n)
+            if pend is not None and self.mistake != "publish_after_waits":
+                self.done[pend[0]] = pend[1] + 1   # before any wait
+                pend = None
+                yield True
             if s != cur_s and self.mistake != "flush_after_waits":
                 yield from self.flush(cur_s, my_cnt, my_mass)
                 cur_s, my_cnt, my_mass = s, 0, []
@@ -123,6 +132,10 @@ class Model:
             if s != cur_s:                       # the late flush of the planted mistake
                 yield from self.flush(cur_s, my_cnt, my_mass)
                 cur_s, my_cnt, my_mass = s, 0, []
+            if pend is not None:                 # the late publication of the planted mistake
+                self.done[pend[0]] = pend[1] + 1
+                pend = None
+                yield True
             # read phase: every read cell holds step s's input, not yet overwritten
             src = s & 1
             for x in self.reads[c]:
@@ -136,7 +149,7 @@ class Model:
                     assert self.pending_reads(s - 1, x) == 0, ("write before read", s, c, x)
                 self.version[dst][x] = s + 1
             yield True
-            self.done[c] = s + 1
+            pend = (c, s)                        # published at the next iteration
             my_cnt += 1
             my_mass.append((s, c))
             yield True
@@ -208,7 +221,8 @@ def test_one_slot_and_long_grids(seed):
 
 
 @pytest.mark.parametrize("mistake", ["no_self_dep", "upwind_only", "no_slot_wait",
-                                     "unordered_reduce", "early_clock", "flush_after_waits"])
+                                     "unordered_reduce", "early_clock", "flush_after_waits",
+                                     "publish_after_waits"])
 def test_planted_protocol_mistakes_are_caught(mistake):
     caught = 0
     shapes = [((9, 7, 4), 2), ((24, 3, 3), 1), ((24, 3, 3), 2)]
